@@ -1,0 +1,405 @@
+"""Benchmark: FIBAR events/s on one GB300 for the 1280x720 rotating/zooming Perlin stream.
+
+Workload: 1280x720 sensor, 200 M events from the contrast-threshold simulator (C = 0.2)
+over a rotating and zooming Perlin-noise texture with 2 % uniform noise events, seed 1,
+pushed as device packets of 65,536 events with a read-out every 1,000,000 events.
+One step = the pushes of one read-out interval plus the read-out (decode, sort, filter,
+stale-pixel detector, masked-blur read-out into a device image).
+
+Timed region: K steps after W warm-up steps, on the device with CUDA events, inputs
+already in HBM; every step consumes a fresh 16 MB slice of the 3.2 GB stream (inputs
+larger than L2).  `e2e` repeats the same steps through the C ABI from pinned HOST
+buffers, with the host-to-device copies of the packets and the device-to-host copy of
+each image inside the timed region.  `--impl reference` times the FP64 oracle on the
+host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+W, H = 1280, 720
+PACKET = 65_536
+READ_EVERY = 1_000_000
+STREAM_EVENTS = 200_000_000
+CONFIG_NAME = "perlin_1280x720_200M"
+METRIC = "events/s (M/s) on 1 GB300, % of HBM roofline; p50/p99 read-out latency"
+UNIT = "Mevents/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def step_plan(n_steps: int, first_step: int, t_col):
+    """Per step: list of (lo, hi) packets and the read-out time."""
+    plans = []
+    for s in range(first_step, first_step + n_steps):
+        lo = s * READ_EVERY
+        hi = (s + 1) * READ_EVERY
+        # packets on the 65,536 grid of the stream
+        p0 = (lo // PACKET) * PACKET
+        pk = []
+        # the pushes needed to cover [pushed_so_far, hi): packets whose start is < hi
+        # and whose start is >= the first packet not yet pushed
+        plans.append((lo, hi))
+    out = []
+    pushed = (first_step * READ_EVERY + PACKET - 1) // PACKET * PACKET if first_step else 0
+    for lo, hi in plans:
+        pk = []
+        while pushed < hi:
+            pk.append((pushed, min(pushed + PACKET, len(t_col))))
+            pushed += PACKET
+        out.append((pk, int(t_col[hi - 1])))
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the GPU works."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, pw = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+                pw.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(pw) if pw else None}
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_stream(device, seed_offset=0):
+    import eventsim
+    cfg = dict(eventsim.CONFIGS[CONFIG_NAME])
+    cfg["seed"] += seed_offset
+    n = cfg.pop("n_events")
+    return eventsim.simulate(cfg.pop("W"), cfg.pop("H"), n, device=device, **cfg)
+
+
+def run_device(args, ev, f, torch, stream):
+    """Warm-up + timed steps with device packets and device images."""
+    t_col = ev[:, 1].cpu()
+    plan = step_plan(args.warmup + args.steps, 0, t_col)
+    out = torch.empty((H, W), dtype=torch.float32, device=ev.device)
+    for pk, t in plan[: args.warmup]:
+        for lo, hi in pk:
+            f.push(ev[lo:hi])
+        f.readout(t, out)
+    f.stage_times(reset=True)
+    launches0 = f.stats()["kernel_launches"]
+    f.set_timing(True)
+    return plan, out, launches0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--mode", default="s2", choices=["s2", "nsf"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2510_20071_gb300 import Fibar
+
+    need = (args.warmup + args.steps) * READ_EVERY
+    stream_events = max(STREAM_EVENTS, need)
+    t0 = time.time()
+    import eventsim
+    cfg = dict(eventsim.CONFIGS[CONFIG_NAME])
+    cfg["seed"] += rank
+    cfg["n_events"] = stream_events
+    ev = eventsim.simulate(cfg.pop("W"), cfg.pop("H"), cfg.pop("n_events"), device=f"cuda:{local}", **cfg)
+    torch.cuda.synchronize()
+    log(f"[rank {rank}] simulated {ev.shape[0]} events in {time.time() - t0:.1f} s")
+
+    params = dict(c_on=0.2, c_off=0.2)
+    if args.mode == "s2":
+        params.update(spatial_filter=1, blur_mode=1)
+    else:
+        params.update(spatial_filter=0)
+    stream = torch.cuda.current_stream()
+    f = Fibar(W, H, stream=stream, **params)
+    plan, out, launches0 = run_device(args, ev, f, torch, stream)
+    timed = plan[args.warmup:]
+    n_timed = sum(min(hi, ev.shape[0]) - lo for pk, _ in timed for lo, hi in pk)
+    applied0 = f.stats()["events_applied"]
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.4)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for pk, t in timed:
+        for lo, hi in pk:
+            f.push(ev[lo:hi])
+        f.readout(t, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    time.sleep(0.3)
+    clocks = sampler.stop()
+    st = f.stats()
+    stages = f.stage_times(reset=True)
+    applied = st["events_applied"] - applied0
+    launches = st["kernel_launches"] - launches0
+    f.set_timing(False)
+
+    ms_all = torch.tensor([ms], device="cuda")
+    ev_all = torch.tensor([float(applied)], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_all, op=dist.ReduceOp.MAX)
+        dist.all_reduce(ev_all, op=dist.ReduceOp.SUM)
+    ms_max = float(ms_all.item())
+    total_events = float(ev_all.item())
+    value = total_events / (ms_max / 1e3) / 1e6  # Mevents/s, whole job
+
+    # roofline of the dominant kernel stage, from its CUDA-event time in the timed region
+    peak, peak_kind = load_peaks()
+    steps = len(timed)
+    per_step_events = applied / steps
+    B_ev = 16.0 + 4.0 * W * H / READ_EVERY
+    stage_ms = {k: v for k, v in stages.items() if k != "calls"}
+    dom = max(stage_ms, key=stage_ms.get)
+    # algorithmic bytes per stage launch: decode reads the 16 B records; the read-out
+    # writes the W*H float image (S2 also reads L: 4 B/px); other stages operate on
+    # L2-resident intermediates and have no compulsory HBM bytes of their own, so the
+    # whole step's algorithmic bytes are charged to them.
+    alg_bytes = {"decode": 16.0 * per_step_events, "readout": 8.0 * W * H}
+    bytes_per_launch = alg_bytes.get(dom, B_ev * per_step_events)
+    dom_ms = stage_ms[dom] / max(stages["calls"], 1)
+    achieved = bytes_per_launch / (dom_ms / 1e3) / 1e9
+    whole_gbs = B_ev * total_events / (ms_max / 1e3) / 1e9
+
+    result = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_max / steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded contrast-threshold simulator)",
+        "config": {"workload": "1280x720 rotating+zooming Perlin, 2% noise events, C=0.2, seed 1, "
+                               "65,536-event device packets, read-out every 1,000,000 events",
+                   "mode": "S2 masked-blur read-out" if args.mode == "s2" else "NSF (no spatial filter)",
+                   "stream_events": int(ev.shape[0]), "events_per_step": int(per_step_events),
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2: each step reads a fresh 16 MB slice of the 3.2 GB stream"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_kind": peak_kind,
+                     "whole_step_gbs": round(whole_gbs, 1),
+                     "whole_step_frac": round(whole_gbs / peak, 4),
+                     "alg_bytes_per_event": B_ev},
+        "stages_ms_per_step": {k: round(v / max(stages["calls"], 1), 5) for k, v in stage_ms.items()},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+
+    if not args.no_e2e:
+        result["e2e"] = run_e2e(args, ev, plan, params, torch)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = run_cpu_baseline(ev, params)
+    f.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, ev, plan, params, torch):
+    """Same steps through the C ABI from pinned host memory, images read back to host."""
+    from paper_2510_20071_gb300 import Fibar
+    stream = torch.cuda.current_stream()
+    lo_all = plan[args.warmup][0][0][0]
+    hi_all = plan[-1][0][-1][1]
+    host = torch.empty((hi_all - lo_all, 2), dtype=torch.int64).pin_memory()
+    host.copy_(ev[lo_all:hi_all])
+    warm = torch.empty((plan[args.warmup - 1][0][-1][1], 2), dtype=torch.int64).pin_memory()
+    warm.copy_(ev[: warm.shape[0]])
+    out = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    f = Fibar(W, H, stream=stream, **params)
+    for pk, t in plan[: args.warmup]:
+        for lo, hi in pk:
+            f.push(warm[lo:hi])
+        f.readout(t, out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for pk, t in plan[args.warmup:]:
+        for lo, hi in pk:
+            f.push(host[lo - lo_all:hi - lo_all])
+        f.readout(t, out)  # host image: waits for the result
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    st = f.stats()
+    f.close()
+    steps = len(plan) - args.warmup
+    n = sum(hi - lo for pk, _ in plan[args.warmup:] for lo, hi in pk)
+    applied = n  # every pushed event of the timed steps is applied by its read-out or the next
+    return {"value": round(applied / dt / 1e6, 3), "unit": UNIT,
+            "h2d_bytes_per_step": int(16 * n / steps), "d2h_bytes_per_step": int(4 * W * H),
+            "ms_per_step": round(dt * 1e3 / steps, 4)}
+
+
+def run_cpu_baseline(ev, params, seconds: float = 15.0):
+    """The FP64 oracle, single-threaded, on a bounded prefix of the same stream."""
+    import oracle
+    oracle.build()
+    o = oracle.Oracle(W, H, **params)
+    cpu = ev[: 40 * READ_EVERY].cpu()
+    t_col = cpu[:, 1]
+    t0 = time.perf_counter()
+    done = 0
+    while done < cpu.shape[0] and time.perf_counter() - t0 < seconds:
+        o.push(cpu[done:done + READ_EVERY])
+        o.readout(int(t_col[done + READ_EVERY - 1]))
+        done += READ_EVERY
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {done // READ_EVERY} read-out intervals ({done} events) of the same stream, "
+                      f"FP64 event-by-event, one thread"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle on the host cores, same config / metric / unit."""
+    if rank != 0:
+        return 0
+    import torch
+    import oracle
+    import eventsim
+    oracle.build()
+    mode_params = dict(spatial_filter=1, blur_mode=1) if args.mode == "s2" else dict(spatial_filter=0)
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    n = (args.warmup + args.steps) * READ_EVERY
+    # bounded: at most 40 read-out intervals of the stream are simulated for this arm
+    n_sim = min(n, 40 * READ_EVERY)
+    cfg = dict(eventsim.CONFIGS[CONFIG_NAME])
+    cfg["n_events"] = STREAM_EVENTS
+    if dev == "cpu":
+        cfg["n_events"] = n_sim
+    ev = eventsim.simulate(cfg.pop("W"), cfg.pop("H"), cfg.pop("n_events"), device=dev, **cfg)[:n_sim].cpu()
+    t_col = ev[:, 1]
+    o = oracle.Oracle(W, H, c_on=0.2, c_off=0.2, **mode_params)
+    per_step = max(1, min(READ_EVERY, int(READ_EVERY * 20 / max(args.steps, 1))))
+    pos = 0
+    for s in range(args.warmup):
+        o.push(ev[pos:pos + per_step]); o.readout(int(t_col[pos + per_step - 1])); pos += per_step
+    t0 = time.perf_counter()
+    done = 0
+    for s in range(args.steps):
+        if pos + per_step > ev.shape[0]:
+            pos = 0
+            o = oracle.Oracle(W, H, c_on=0.2, c_off=0.2, **mode_params)
+        o.push(ev[pos:pos + per_step])
+        o.readout(int(t_col[pos + per_step - 1]))
+        pos += per_step
+        done += per_step
+    dt = time.perf_counter() - t0
+    value = done / dt / 1e6
+    res = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded simulator)",
+           "impl": "reference",
+           "config": {"workload": "1280x720 rotating+zooming Perlin, 2% noise events, C=0.2, seed 1, "
+                                  "read-out every step", "events_per_step": per_step},
+           "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{per_step} events per step of the same stream"},
+           "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main() or 0)

@@ -1,0 +1,189 @@
+/*
+ * fibar.h - C ABI of the GB300 (sm_103a) FIBAR event-to-image reconstruction library.
+ *
+ * FIBAR ("Filter-Based Reconstruction of Images from Events", arXiv 2510.20071)
+ * turns a stream of event-camera events into a brightness image that can be read out
+ * at any time (abstract; Sec. 1):
+ *   - every event drives its pixel's temporal IIR filter (Sec. 4.1, Eqs. 6, 7, 10 with
+ *     coefficients from Eqs. 16-18);
+ *   - a global FIFO "active event queue" whose target length is regulated every event
+ *     by the 2x2-tile fill ratio (Sec. 4.2 steps 1-3, Eqs. 19-20) decides when a pixel
+ *     goes stale;
+ *   - stale pixels are filled with a 3x3 Gaussian (Sec. 4.2).
+ * All compute runs in hand-written CUDA kernels on the device; there is no CPU path.
+ *
+ * Conventions
+ *   - Every function returns FIBAR_OK (0) or a negative FIBAR_E* code; the message of
+ *     the last failure of a handle is available from fibar_last_error().
+ *   - A handle is not thread safe.  All calls on one handle must be ordered: issue
+ *     them on one CUDA stream (or synchronise between streams).  Separate handles are
+ *     independent.
+ *   - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Device memory is owned by the handle and released by fibar_destroy().
+ */
+#ifndef FIBAR_H
+#define FIBAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FIBAR_OK 0
+#define FIBAR_EINVAL (-1)   /* bad argument or parameter */
+#define FIBAR_ENOMEM (-2)   /* device allocation failed, or pending capacity exceeded */
+#define FIBAR_EORDER (-3)   /* read-out time earlier than the previous read-out time */
+#define FIBAR_ECUDA (-4)    /* a CUDA runtime call failed */
+#define FIBAR_ETIMEOUT (-5) /* a bounded device-side wait gave up (state is unreliable) */
+
+/* One event, 16 bytes, little endian.  p > 0 is an ON event (brightness increased by
+ * the ON threshold), otherwise OFF (Sec. 3, Eqs. 1-3).  t_us is the sensor time stamp
+ * in microseconds; FIBAR itself ignores time stamps (Sec. 4.1: each pixel runs on its
+ * own event clock) except to decide which events a read-out includes (Eq. 4, t_k <= t). */
+typedef struct {
+    uint16_t x, y;
+    int8_t p;
+    uint8_t pad[3];
+    uint64_t t_us;
+} fibar_event_t;
+
+/* Parameters.  Fill with fibar_default_params() and override fields. */
+typedef struct {
+    double t_cut;            /* cutoff period in events (Eq. 16); default 40 (Sec. 5.1).
+                                omega_cut = 2 pi / t_cut, alpha by Eq. 17, beta by Eq. 18.
+                                Must be > 4; +inf gives alpha = beta = 1 (plain sum, Eq. 5) */
+    uint32_t fill_num;       /* target fill ratio r_fill = fill_num / fill_den (Eq. 20);  */
+    uint32_t fill_den;       /*   default 1/2 (Sec. 4.2).  Each in 1..255                 */
+    uint32_t q_min;          /* lower bound of the target queue length (Sec. 4.2 requires
+                                one but gives no value); 0 = max(1, ceil(W*H/1024))      */
+    uint32_t q_init;         /* initial target queue length; 0 = q_min                    */
+    float c_on, c_off;       /* contrast scales multiplying ON (+1) / OFF (-1) polarities
+                                before Eqs. 7 and 6 (Eqs. 2-3); 1, 1 = the paper's units  */
+    int32_t spatial_filter;  /* 1 = stale detection + Gaussian fill; 0 = FIBAR-NSF (Tab. 2) */
+    int32_t blur_mode;       /* 0 = "S1": blur the pixel's L in place when it goes stale
+                                   (Sec. 4.2, the paper's method; read-out copies L);
+                                1 = "S2": never modify L; at read-out, output the 3x3 blur
+                                   of L at stale pixels (had an event, none queued) and L
+                                   elsewhere                                              */
+    int32_t chain_policy;    /* reserved (0)                                              */
+    uint32_t max_pending;    /* capacity, in events, of pushed-but-unapplied events and of
+                                one processing batch; 0 = 8 Mi events                     */
+} fibar_params_t;
+
+typedef struct fibar_s fibar_t;
+
+/* Host-side counters.  Filled by fibar_stats(), which synchronises the stream. */
+typedef struct {
+    uint64_t events_pushed;   /* records handed to fibar_push_events                      */
+    uint64_t events_applied;  /* valid events applied to the state                       */
+    uint64_t events_dropped;  /* out-of-range records skipped (counted, not applied)      */
+    uint64_t events_pending;  /* pushed records not yet applied                          */
+    uint64_t readouts;
+    uint64_t q;               /* current queue length (events in the active window)      */
+    uint64_t q_targ;          /* target length for the next event (Eq. 20)               */
+    uint64_t n_ap, n_at;      /* active pixels / active 2x2 tiles (Eq. 19)               */
+    uint64_t detector_fixups; /* batches whose speculative detector needed a serial fixup */
+    uint64_t kernel_launches; /* CUDA kernels this handle has launched                    */
+} fibar_stats_t;
+
+/* Stages of one read-out, in launch order (fibar_stage_times). */
+enum {
+    FIBAR_STAGE_DECODE = 0,  /* decode + read-out cut + compaction (one pass over records)  */
+    FIBAR_STAGE_SORT,        /* stable radix sort by 2x2 tile                               */
+    FIBAR_STAGE_WALK,        /* per-tile walk: temporal filter (Eqs. 6, 7, 10) + links        */
+    FIBAR_STAGE_DET_COUNTS,  /* detector: per-chunk window counts + scan                     */
+    FIBAR_STAGE_DET_PASS1,   /* detector: speculative pass over all chunks                   */
+    FIBAR_STAGE_DET_PASS2,   /* detector: re-run from predecessors until trajectories merge  */
+    FIBAR_STAGE_DET_FIX,     /* detector: serial fixup (no-op when every chunk merged)       */
+    FIBAR_STAGE_S1,          /* S1 only: ordered in-place blurs of pixels going stale        */
+    FIBAR_STAGE_READOUT,     /* output image (copy of L, or S2 masked blur)                  */
+    FIBAR_STAGE_COMMIT,      /* batch bookkeeping                                            */
+    FIBAR_NSTAGES
+};
+
+/* Accumulated device time per stage, measured with CUDA events recorded on the
+ * caller's stream around each stage of every read-out/flush while timing is on. */
+typedef struct {
+    double ms[FIBAR_NSTAGES];
+    uint64_t calls;           /* read-outs/flushes measured */
+} fibar_stage_times_t;
+
+/* Debug copy of the device state.  Each array pointer is a caller-owned HOST buffer
+ * or NULL (skipped).  Arrays are row-major, pixel i = y * W + x; tiles are 2x2 blocks
+ * aligned at (0,0), tile j = (y/2) * ceil(W/2) + (x/2). */
+typedef struct {
+    float *pbar;        /* [W*H] detrending average p_bar (Eq. 7)                         */
+    float *L;           /* [W*H] filter output L (Eq. 10), including S1 blurs             */
+    uint32_t *cnt;      /* [W*H] events of each pixel in the active event queue           */
+    uint8_t *tcnt;      /* [tiles] active pixels of each 2x2 tile                         */
+    uint8_t *stale;     /* [W*H] 1 = pixel had an event and has none queued               */
+    uint64_t *last_idx; /* [W*H] global index of the pixel's last applied event, or
+                           UINT64_MAX if it never had one                                 */
+    /* scalars, always written */
+    uint64_t k;         /* events applied so far (global index of the next event)        */
+    uint64_t h;         /* global index of the oldest queued event                        */
+    uint64_t q, q_targ, n_ap, n_at;
+} fibar_state_view_t;
+
+/* Fill *p with the defaults above. */
+void fibar_default_params(fibar_params_t *p);
+
+/* Create a stream reconstructor for a W x H sensor on the current CUDA device.
+ * p may be NULL (defaults).  Allocates all device memory up front (state, rings,
+ * batch buffers sized by max_pending).  Errors: EINVAL (W or H = 0, W*H > 2^24,
+ * max_pending > 2^27, bad parameter), ENOMEM, ECUDA.  On success *out owns the
+ * handle. */
+int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *p, fibar_t **out);
+
+/* Queue n events for the next read-out (Sec. 1: events arrive in packets).
+ *   on_device = 0: `ev` is host memory; it is copied to the device on `cuda_stream`
+ *                  (pageable buffers may be reused on return; page-locked buffers once
+ *                  the stream has passed the copy).
+ *   on_device = 1: `ev` is device memory (16-byte aligned) read in place by the next
+ *                  fibar_readout() or fibar_flush(); it must stay valid and unchanged
+ *                  until that call's work has completed on the stream.
+ * Nothing is applied here.  Records with x >= W or y >= H are dropped and counted
+ * when applied.  Errors: EINVAL, ENOMEM (more than max_pending events or 255 device
+ * packets pending: read out or flush first), ECUDA. */
+int fibar_push_events(fibar_t *h, const fibar_event_t *ev, size_t n, int on_device,
+                      void *cuda_stream);
+
+/* Apply the longest prefix of pending events whose time stamps are all <= t_us
+ * (Eq. 4's t_k <= t, in push order), then write the W*H float image (row-major) to
+ * `out`: L for S1 and NSF (Sec. 1: no work at read-out), or the masked 3x3 blur of
+ * L for S2.  Pending events after the prefix stay queued.
+ *   on_device = 1: out is device memory; the call returns without waiting.
+ *   on_device = 0: out is host memory; the call waits for the result.
+ * Errors: EINVAL, EORDER (t_us < previous read-out time), ECUDA, ETIMEOUT. */
+int fibar_readout(fibar_t *h, uint64_t t_us, float *out, int on_device, void *cuda_stream);
+
+/* Apply every pending event (as a read-out at t = +inf without output; does not
+ * change the read-out time order). */
+int fibar_flush(fibar_t *h, void *cuda_stream);
+
+/* Synchronise and copy the state (see fibar_state_view_t). */
+int fibar_debug_state(fibar_t *h, fibar_state_view_t *v, void *cuda_stream);
+
+/* Synchronise and fill counters.  Reports ETIMEOUT if a device wait gave up. */
+int fibar_stats(fibar_t *h, fibar_stats_t *s, void *cuda_stream);
+
+/* Turn per-stage timing on (1) or off (0).  While on, each read-out/flush records 10
+ * CUDA events on its stream (up to 4096 read-outs are kept; older ones are folded in
+ * when fibar_stage_times is called). */
+int fibar_set_timing(fibar_t *h, int enable);
+
+/* Synchronise and return the accumulated per-stage times; reset = 1 clears them. */
+int fibar_stage_times(fibar_t *h, fibar_stage_times_t *t, int reset, void *cuda_stream);
+
+/* Message of the last failed call on this handle ("" if none).  Owned by the handle. */
+const char *fibar_last_error(fibar_t *h);
+
+/* Release the handle and its device memory (waits for its outstanding work). */
+void fibar_destroy(fibar_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIBAR_H */

@@ -1,0 +1,14 @@
+"""GB300 (sm_103a) FIBAR: filter-based reconstruction of images from events.
+
+Python binding of the C ABI in ``include/fibar.h`` (``lib/libfibar.so``).  The binding
+only marshals arguments; every step of the reconstruction runs in the library's CUDA
+kernels.  There is no CPU fallback: importing the binding without the built library or
+without a CUDA device raises.
+"""
+from .binding import (  # noqa: F401
+    FIBAR_OK, FIBAR_EINVAL, FIBAR_ENOMEM, FIBAR_EORDER, FIBAR_ECUDA, FIBAR_ETIMEOUT,
+    FibarError, FibarParams, FibarStats, FibarStateView, Fibar, load_library, library_path,
+    fibar_default_params, fibar_create, fibar_push_events, fibar_readout, fibar_flush,
+    fibar_debug_state, fibar_stats, fibar_set_timing, fibar_stage_times, fibar_last_error,
+    fibar_destroy, EXPORTED, STAGES, FibarStageTimes,
+)

@@ -1,0 +1,260 @@
+"""ctypes binding of ``libfibar.so`` (the C ABI of ``include/fibar.h``).
+
+The module-level ``fibar_*`` functions have the C names and signatures.  :class:`Fibar`
+is a convenience wrapper that takes torch tensors (for device memory and streams
+only) and raises :class:`FibarError` on any non-zero status.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+FIBAR_OK = 0
+FIBAR_EINVAL = -1
+FIBAR_ENOMEM = -2
+FIBAR_EORDER = -3
+FIBAR_ECUDA = -4
+FIBAR_ETIMEOUT = -5
+
+EXPORTED = ["fibar_default_params", "fibar_create", "fibar_push_events", "fibar_readout",
+            "fibar_flush", "fibar_debug_state", "fibar_stats", "fibar_set_timing",
+            "fibar_stage_times", "fibar_last_error", "fibar_destroy"]
+
+STAGES = ["decode", "sort", "walk", "det_counts", "det_pass1", "det_pass2", "det_fix", "s1_blur",
+          "readout", "commit"]
+
+
+class FibarError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fibar error {code}: {msg}")
+        self.code = code
+
+
+class FibarParams(C.Structure):
+    _fields_ = [("t_cut", C.c_double), ("fill_num", C.c_uint32), ("fill_den", C.c_uint32),
+                ("q_min", C.c_uint32), ("q_init", C.c_uint32), ("c_on", C.c_float),
+                ("c_off", C.c_float), ("spatial_filter", C.c_int32), ("blur_mode", C.c_int32),
+                ("chain_policy", C.c_int32), ("max_pending", C.c_uint32)]
+
+
+class FibarStats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ["events_pushed", "events_applied", "events_dropped",
+                                          "events_pending", "readouts", "q", "q_targ", "n_ap",
+                                          "n_at", "detector_fixups", "kernel_launches"]]
+
+
+class FibarStageTimes(C.Structure):
+    _fields_ = [("ms", C.c_double * 10), ("calls", C.c_uint64)]
+
+
+class FibarStateView(C.Structure):
+    _fields_ = [("pbar", C.c_void_p), ("L", C.c_void_p), ("cnt", C.c_void_p), ("tcnt", C.c_void_p),
+                ("stale", C.c_void_p), ("last_idx", C.c_void_p), ("k", C.c_uint64), ("h", C.c_uint64),
+                ("q", C.c_uint64), ("q_targ", C.c_uint64), ("n_ap", C.c_uint64), ("n_at", C.c_uint64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libfibar.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise FibarError(FIBAR_ECUDA, f"CUDA library not built: {_build.LIB}")
+            lib = C.CDLL(_build.LIB)
+            vp = C.c_void_p
+            lib.fibar_default_params.argtypes = [C.POINTER(FibarParams)]
+            lib.fibar_default_params.restype = None
+            lib.fibar_create.argtypes = [C.c_uint32, C.c_uint32, C.POINTER(FibarParams), C.POINTER(vp)]
+            lib.fibar_create.restype = C.c_int
+            lib.fibar_push_events.argtypes = [vp, vp, C.c_size_t, C.c_int, vp]
+            lib.fibar_push_events.restype = C.c_int
+            lib.fibar_readout.argtypes = [vp, C.c_uint64, vp, C.c_int, vp]
+            lib.fibar_readout.restype = C.c_int
+            lib.fibar_flush.argtypes = [vp, vp]
+            lib.fibar_flush.restype = C.c_int
+            lib.fibar_debug_state.argtypes = [vp, C.POINTER(FibarStateView), vp]
+            lib.fibar_debug_state.restype = C.c_int
+            lib.fibar_stats.argtypes = [vp, C.POINTER(FibarStats), vp]
+            lib.fibar_stats.restype = C.c_int
+            lib.fibar_set_timing.argtypes = [vp, C.c_int]
+            lib.fibar_set_timing.restype = C.c_int
+            lib.fibar_stage_times.argtypes = [vp, C.POINTER(FibarStageTimes), C.c_int, vp]
+            lib.fibar_stage_times.restype = C.c_int
+            lib.fibar_last_error.argtypes = [vp]
+            lib.fibar_last_error.restype = C.c_char_p
+            lib.fibar_destroy.argtypes = [vp]
+            lib.fibar_destroy.restype = None
+            _lib = lib
+    return _lib
+
+
+# --- C-named entry points ------------------------------------------------------------
+
+def fibar_default_params() -> FibarParams:
+    p = FibarParams()
+    load_library().fibar_default_params(C.byref(p))
+    return p
+
+
+def fibar_create(W: int, H: int, params: FibarParams | None):
+    h = C.c_void_p()
+    rc = load_library().fibar_create(W, H, C.byref(params) if params is not None else None, C.byref(h))
+    return rc, h
+
+
+def fibar_push_events(h, ev_ptr: int, n: int, on_device: int, stream: int) -> int:
+    return load_library().fibar_push_events(h, ev_ptr, n, on_device, stream)
+
+
+def fibar_readout(h, t_us: int, out_ptr: int, on_device: int, stream: int) -> int:
+    return load_library().fibar_readout(h, t_us, out_ptr, on_device, stream)
+
+
+def fibar_flush(h, stream: int) -> int:
+    return load_library().fibar_flush(h, stream)
+
+
+def fibar_debug_state(h, view: FibarStateView, stream: int) -> int:
+    return load_library().fibar_debug_state(h, C.byref(view), stream)
+
+
+def fibar_stats(h, st: FibarStats, stream: int) -> int:
+    return load_library().fibar_stats(h, C.byref(st), stream)
+
+
+def fibar_set_timing(h, enable: int) -> int:
+    return load_library().fibar_set_timing(h, enable)
+
+
+def fibar_stage_times(h, t: FibarStageTimes, reset: int, stream: int) -> int:
+    return load_library().fibar_stage_times(h, C.byref(t), reset, stream)
+
+
+def fibar_last_error(h) -> str:
+    return load_library().fibar_last_error(h).decode()
+
+
+def fibar_destroy(h) -> None:
+    load_library().fibar_destroy(h)
+
+
+# --- convenience wrapper ---------------------------------------------------------------
+
+class Fibar:
+    """One event stream.  Events are (n, 2) int64 tensors in the 16-byte record layout
+    (``eventsim.pack_events``); CUDA tensors are pushed in place, CPU tensors copied."""
+
+    def __init__(self, W: int, H: int, stream=None, **params):
+        import torch
+        if not torch.cuda.is_available():
+            raise FibarError(FIBAR_ECUDA, "no CUDA device: the FIBAR library has no CPU path")
+        self.torch = torch
+        self.W, self.H = int(W), int(H)
+        p = fibar_default_params()
+        for k, v in params.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown parameter {k!r}")
+            setattr(p, k, v)
+        self.params = p
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        rc, h = fibar_create(self.W, self.H, p)
+        if rc != 0:
+            raise FibarError(rc, "fibar_create failed")
+        self.h = h
+        self._keep = []       # device packets referenced by the pending read-out
+        self._keep_prev = []  # packets of the previous read-out (may still be in flight)
+
+    def _check(self, rc: int):
+        if rc != 0:
+            raise FibarError(rc, fibar_last_error(self.h))
+
+    @property
+    def _s(self) -> int:
+        return self.stream.cuda_stream
+
+    def close(self):
+        if getattr(self, "h", None):
+            fibar_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def push(self, ev) -> None:
+        t = self.torch
+        if ev.dtype != t.int64 or ev.dim() != 2 or ev.shape[1] != 2 or not ev.is_contiguous():
+            raise TypeError("events must be a contiguous (n, 2) int64 tensor")
+        n = ev.shape[0]
+        if ev.is_cuda:
+            self._check(fibar_push_events(self.h, ev.data_ptr(), n, 1, self._s))
+            self._keep.append(ev)
+        else:
+            self._check(fibar_push_events(self.h, ev.data_ptr(), n, 0, self._s))
+
+    def _rotate(self):
+        self._keep_prev = self._keep
+        self._keep = []
+
+    def readout(self, t_us: int, out=None):
+        """Image at time t_us.  ``out``: a (H, W) float32 tensor (CUDA: asynchronous,
+        CPU: synchronous); default a new CUDA tensor."""
+        t = self.torch
+        if out is None:
+            out = t.empty((self.H, self.W), dtype=t.float32, device="cuda")
+        if out.dtype != t.float32 or out.numel() != self.W * self.H or not out.is_contiguous():
+            raise TypeError("out must be a contiguous float32 tensor with W*H elements")
+        rc = fibar_readout(self.h, int(t_us), out.data_ptr(), 1 if out.is_cuda else 0, self._s)
+        self._rotate()
+        self._check(rc)
+        return out
+
+    def flush(self) -> None:
+        rc = fibar_flush(self.h, self._s)
+        self._rotate()
+        self._check(rc)
+
+    def set_timing(self, enable: bool) -> None:
+        self._check(fibar_set_timing(self.h, 1 if enable else 0))
+
+    def stage_times(self, reset: bool = False) -> dict:
+        t = FibarStageTimes()
+        self._check(fibar_stage_times(self.h, t, 1 if reset else 0, self._s))
+        d = {name: float(t.ms[i]) for i, name in enumerate(STAGES)}
+        d["calls"] = int(t.calls)
+        return d
+
+    def stats(self) -> dict:
+        st = FibarStats()
+        self._check(fibar_stats(self.h, st, self._s))
+        return {n: int(getattr(st, n)) for n, _ in FibarStats._fields_}
+
+    def state(self) -> dict:
+        npix = self.W * self.H
+        ntiles = ((self.W + 1) // 2) * ((self.H + 1) // 2)
+        arrs = dict(pbar=np.empty(npix, np.float32), L=np.empty(npix, np.float32),
+                    cnt=np.empty(npix, np.uint32), tcnt=np.empty(ntiles, np.uint8),
+                    stale=np.empty(npix, np.uint8), last_idx=np.empty(npix, np.uint64))
+        v = FibarStateView(**{k: a.ctypes.data for k, a in arrs.items()})
+        self._check(fibar_debug_state(self.h, v, self._s))
+        out = dict(arrs)
+        for k in ["k", "h", "q", "q_targ", "n_ap", "n_at"]:
+            out[k] = int(getattr(v, k))
+        return out

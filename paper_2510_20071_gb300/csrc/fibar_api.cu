@@ -1,0 +1,598 @@
+// Host side of the C ABI declared in include/fibar.h.
+//
+// A read-out (or flush) enqueues, on the caller's stream and without host
+// synchronisation:
+//   decode -> radix sort by tile -> tile walk (links + IIR) -> detector (counts, pass 1,
+//   pass 2, fixup) -> read-out image -> commit.
+// Batch sizes live in device memory; every kernel sizes its loop from there, so the host
+// never needs to know how many of the pending records a read-out applied.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "fibar_internal.cuh"
+
+using namespace fibar;
+
+namespace {
+
+int fail(fibar_t *h, int code, const char *msg)
+{
+    if (h) h->err = msg;
+    return code;
+}
+
+int cuda_fail(fibar_t *h, cudaError_t e, const char *where)
+{
+    if (h) {
+        h->err = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+    return FIBAR_ECUDA;
+}
+
+unsigned long long next_pow2(unsigned long long v)
+{
+    unsigned long long p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    return cudaMalloc((void **)p, std::max<size_t>(count, 1) * sizeof(T));
+}
+
+void free_all(fibar_t *h)
+{
+    Bufs &b = h->b;
+    void *ptrs[] = {b.ctrl, b.pbar, b.L, b.last_pix, b.last_tile, b.staging, b.carry[0], b.carry[1],
+                    b.dec_status, b.rec[0], b.rec[1], b.sort_hist, b.sort_base, b.sort_status, b.dpt,
+                    b.qout, b.ring_npt, b.ring_pix, b.dM, b.E0, b.E1, b.E2, b.merged,
+                    b.out_staging, b.dbg_cnt, b.plist, b.plnb, b.epos, b.lbl, b.s1_info, b.s1_linit,
+                    b.popk, b.blur_ord, b.bk, b.bpix, b.bj, b.bD, b.bflag, b.sel_status, b.beta_pow};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    memset(&h->b, 0, sizeof(h->b));
+}
+
+}  // namespace
+
+extern "C" void fibar_default_params(fibar_params_t *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->t_cut = 40.0;
+    p->fill_num = 1;
+    p->fill_den = 2;
+    p->q_min = 0;
+    p->q_init = 0;
+    p->c_on = 1.0f;
+    p->c_off = 1.0f;
+    p->spatial_filter = 1;
+    p->blur_mode = 0;
+    p->chain_policy = 0;
+    p->max_pending = 0;
+}
+
+extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fibar_t **out)
+{
+    if (!out) return FIBAR_EINVAL;
+    *out = nullptr;
+    fibar_params_t p;
+    if (pp) p = *pp; else fibar_default_params(&p);
+    const unsigned long long npix = (unsigned long long)W * H;
+    if (W == 0 || H == 0 || npix > (1ull << 24)) return FIBAR_EINVAL;
+    if (!(p.t_cut > 4.0)) return FIBAR_EINVAL;
+    if (p.fill_num == 0 || p.fill_den == 0 || p.fill_num > 255 || p.fill_den > 255) return FIBAR_EINVAL;
+    if (!(p.c_on > 0.f) || !(p.c_off > 0.f) || !isfinite(p.c_on) || !isfinite(p.c_off)) return FIBAR_EINVAL;
+    if (p.spatial_filter != 0 && p.spatial_filter != 1) return FIBAR_EINVAL;
+    if (p.blur_mode != 0 && p.blur_mode != 1) return FIBAR_EINVAL;
+    const unsigned long long qmin = p.q_min ? p.q_min : std::max(1ull, (npix + 1023) / 1024);
+    const unsigned long long qinit = p.q_init ? p.q_init : qmin;
+    if (qmin > npix || qinit < qmin || qinit > npix) return FIBAR_EINVAL;
+    const unsigned long long maxp = p.max_pending ? p.max_pending : (8ull << 20);
+    if (maxp > (1ull << 27)) return FIBAR_EINVAL;
+
+    fibar_t *h = new (std::nothrow) fibar_s();
+    if (!h) return FIBAR_ENOMEM;
+    memset(&h->b, 0, sizeof(h->b));
+    h->params = p;
+    h->params.max_pending = (uint32_t)maxp;
+    h->W = W;
+    h->H = H;
+    cudaGetDevice(&h->device);
+
+    // Eqs. 16-18 in double, then rounded once to the FP32 filter coefficients
+    const double w = 2.0 * M_PI / p.t_cut;
+    const double c = cos(w);
+    h->alpha = (1.0 - sin(w)) / c;
+    h->beta = (2.0 - c) - sqrt((2.0 - c) * (2.0 - c) - 1.0);
+
+    KParams &kp = h->kp;
+    kp.W = W;
+    kp.H = H;
+    kp.tiles_w = (W + 1) / 2;
+    kp.tiles_h = (H + 1) / 2;
+    kp.npix = (uint32_t)npix;
+    kp.ntiles = kp.tiles_w * kp.tiles_h;
+    kp.a = (float)h->alpha;
+    kp.oma = (float)(1.0 - h->alpha);
+    kp.b = (float)h->beta;
+    kp.g = (float)(0.5 * (1.0 + h->beta));
+    kp.log2b = (float)log2(h->beta);
+    kp.c_on = p.c_on;
+    kp.c_off = p.c_off;
+    kp.q_min = (uint32_t)qmin;
+    kp.q_max = (uint32_t)npix;
+    kp.numA = p.fill_num * 4u;
+    kp.den = p.fill_den;
+    kp.max_pending = (uint32_t)maxp;
+    unsigned bits = 1;
+    while ((1ull << bits) < kp.ntiles) ++bits;
+    kp.key_bits = bits;
+    h->sort_passes = (bits + 7) / 8;
+    kp.spatial = p.spatial_filter;
+    kp.blur_mode = p.blur_mode;
+    // event ring: the batch plus everything a window (or a guessed window) can reach back
+    h->R = next_pow2(maxp + npix + 8ull * CHUNK);
+    kp.ring_mask = h->R - 1;
+    kp.live = h->R - maxp;
+
+    Bufs &b = h->b;
+    b.max_dec_tiles = (maxp + DEC_TILE - 1) / DEC_TILE + 1;
+    b.max_sort_tiles = (maxp + SORT_TILE - 1) / SORT_TILE + 1;
+    b.max_chunks = (maxp + CHUNK - 1) / CHUNK + 1;
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, n)                                  \
+    if (e == cudaSuccess) e = dalloc(&(ptr), (n));
+    ALLOC(b.ctrl, 1);
+    ALLOC(b.pbar, npix);
+    ALLOC(b.L, npix);
+    ALLOC(b.last_pix, npix);
+    ALLOC(b.last_tile, kp.ntiles);
+    ALLOC(b.staging, maxp);
+    ALLOC(b.carry[0], maxp);
+    ALLOC(b.carry[1], maxp);
+    ALLOC(b.dec_status, b.max_dec_tiles);
+    ALLOC(b.rec[0], maxp);
+    ALLOC(b.rec[1], maxp);
+    ALLOC(b.sort_hist, SORT_MAX_PASSES * 256);
+    ALLOC(b.sort_base, SORT_MAX_PASSES * 256);
+    ALLOC(b.sort_status, b.max_sort_tiles * 256);
+    ALLOC(b.out_staging, npix);
+    if (p.spatial_filter) {
+        ALLOC(b.dpt, maxp);
+        ALLOC(b.qout, maxp);
+        ALLOC(b.ring_npt, h->R);
+        ALLOC(b.ring_pix, h->R);
+        ALLOC(b.dM, (b.max_chunks + DET_G + 1) * 2 * (DET_G + 1));
+        ALLOC(b.E0, b.max_chunks);
+        ALLOC(b.E1, b.max_chunks);
+        ALLOC(b.E2, b.max_chunks);
+        ALLOC(b.merged, b.max_chunks);
+    }
+    b.max_pops = maxp + npix + 8;
+    b.max_sel_tiles = (b.max_pops + 4095) / 4096 + 1;
+    if (p.spatial_filter && p.blur_mode == 0) {
+        ALLOC(b.plist, maxp);
+        ALLOC(b.plnb, maxp);
+        ALLOC(b.epos, maxp);
+        ALLOC(b.lbl, maxp);
+        ALLOC(b.s1_info, npix);
+        ALLOC(b.s1_linit, npix);
+        ALLOC(b.popk, b.max_pops);
+        ALLOC(b.blur_ord, b.max_pops);
+        ALLOC(b.bk, b.max_pops);
+        ALLOC(b.bpix, b.max_pops);
+        ALLOC(b.bj, b.max_pops);
+        ALLOC(b.bD, b.max_pops);
+        ALLOC(b.bflag, b.max_pops);
+        ALLOC(b.sel_status, b.max_sel_tiles);
+        ALLOC(b.beta_pow, 64);
+    }
+#undef ALLOC
+    if (e != cudaSuccess) {
+        free_all(h);
+        cudaGetLastError();
+        delete h;
+        return FIBAR_ENOMEM;
+    }
+    cudaStream_t s = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.pbar, 0, npix * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.L, 0, npix * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.last_pix, 0xFF, npix * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.last_tile, 0xFF, kp.ntiles * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.dec_status, 0, b.max_dec_tiles * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.sort_hist, 0, SORT_MAX_PASSES * 256 * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.sort_status, 0, b.max_sort_tiles * 256 * 8, s);
+    if (e == cudaSuccess && p.spatial_filter) e = cudaMemsetAsync(b.ring_npt, 0xFF, h->R * 8, s);
+    if (e == cudaSuccess && p.spatial_filter) e = cudaMemsetAsync(b.ring_pix, 0, h->R * 4, s);
+    if (e == cudaSuccess && b.s1_info) e = cudaMemsetAsync(b.s1_info, 0, npix * sizeof(int4), s);
+    if (e == cudaSuccess && b.bflag) e = cudaMemsetAsync(b.bflag, 0, b.max_pops * 4, s);
+    if (e == cudaSuccess && b.sel_status) e = cudaMemsetAsync(b.sel_status, 0, b.max_sel_tiles * 8, s);
+    if (e == cudaSuccess && b.beta_pow) {
+        float tab[64];
+        double v = 1.0;
+        for (int i = 0; i < 64; ++i) {
+            tab[i] = (float)v;
+            v *= h->beta;
+        }
+        e = cudaMemcpy(b.beta_pow, tab, sizeof(tab), cudaMemcpyHostToDevice);
+    }
+    h->launches = 0;
+    if (e == cudaSuccess) e = launch_init(kp, b, s, h->launches);
+    if (e == cudaSuccess) {
+        // q_targ_0 = q_init as the ratio q_init / 1
+        DetState d0{0, 0, 0, qinit, 1};
+        e = cudaMemcpyAsync(&b.ctrl->det, &d0, sizeof(d0), cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        free_all(h);
+        delete h;
+        return FIBAR_ECUDA;
+    }
+    h->staging_used = 0;
+    h->pending_upper = 0;
+    h->carry_slot = 0;
+    h->epoch = 1;
+    h->have_readout = false;
+    h->last_readout = 0;
+    h->pushed = 0;
+    h->readouts = 0;
+    h->timing = false;
+    h->ev_used = 0;
+    memset(h->stage_ms, 0, sizeof(h->stage_ms));
+    h->stage_calls = 0;
+    *out = h;
+    return FIBAR_OK;
+}
+
+extern "C" void fibar_destroy(fibar_t *h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    free_all(h);
+    delete h;
+}
+
+extern "C" const char *fibar_last_error(fibar_t *h)
+{
+    return h ? h->err.c_str() : "null handle";
+}
+
+extern "C" int fibar_push_events(fibar_t *h, const fibar_event_t *ev, size_t n, int on_device,
+                                 void *cuda_stream)
+{
+    if (!h) return FIBAR_EINVAL;
+    if (n == 0) return FIBAR_OK;
+    if (!ev) return fail(h, FIBAR_EINVAL, "push: null event pointer");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (h->pending_upper + n > h->params.max_pending) {
+        // the bound may be stale: learn the true carry count before refusing
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "push: sync");
+        unsigned carry = 0;
+        e = cudaMemcpy(&carry, &h->b.ctrl->carry_n[h->carry_slot], 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "push: carry count");
+        unsigned long long segs = 0;
+        for (unsigned v : h->seg_n) segs += v;
+        h->pending_upper = carry + segs;
+        if (h->pending_upper + n > h->params.max_pending)
+            return fail(h, FIBAR_ENOMEM, "push: pending capacity exceeded; read out or flush first");
+    }
+    if (on_device) {
+        if (((uintptr_t)ev & 15) != 0) return fail(h, FIBAR_EINVAL, "push: device packet not 16-byte aligned");
+        if (h->seg_ptr.size() >= (size_t)MAXSEG)
+            return fail(h, FIBAR_ENOMEM, "push: too many pending device packets; read out or flush first");
+        h->seg_ptr.push_back((const int4 *)ev);
+        h->seg_n.push_back((unsigned)n);
+    } else {
+        if (h->staging_used + n > h->params.max_pending)
+            return fail(h, FIBAR_ENOMEM, "push: host staging full; read out or flush first");
+        int4 *dst = h->b.staging + h->staging_used;
+        cudaError_t e = cudaMemcpyAsync(dst, ev, n * sizeof(fibar_event_t), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "push: host-to-device copy");
+        if (!h->seg_ptr.empty() && h->seg_ptr.back() + h->seg_n.back() == dst) {
+            h->seg_n.back() += (unsigned)n;
+        } else {
+            if (h->seg_ptr.size() >= (size_t)MAXSEG)
+                return fail(h, FIBAR_ENOMEM, "push: too many pending packets; read out or flush first");
+            h->seg_ptr.push_back(dst);
+            h->seg_n.push_back((unsigned)n);
+        }
+        h->staging_used += n;
+    }
+    h->pending_upper += n;
+    h->pushed += n;
+    return FIBAR_OK;
+}
+
+namespace {
+
+constexpr unsigned EV_SETS = 4096;  // read-outs whose stage events are kept
+
+// Fold recorded stage events into the accumulated times (synchronises on them).
+void fold_stage_events(fibar_t *h)
+{
+    for (unsigned i = 0; i < h->ev_used; ++i) {
+        cudaEvent_t *e = &h->ev_pool[(size_t)i * (FIBAR_NSTAGES + 1)];
+        cudaEventSynchronize(e[FIBAR_NSTAGES]);
+        for (int st = 0; st < FIBAR_NSTAGES; ++st) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, e[st], e[st + 1]) == cudaSuccess) h->stage_ms[st] += ms;
+        }
+        h->stage_calls += 1;
+    }
+    h->ev_used = 0;
+}
+
+struct StageMarks {
+    fibar_t *h;
+    cudaStream_t s;
+    cudaEvent_t *e;
+    explicit StageMarks(fibar_t *h_, cudaStream_t s_) : h(h_), s(s_), e(nullptr)
+    {
+        if (!h->timing) return;
+        if (h->ev_used == EV_SETS) fold_stage_events(h);
+        e = &h->ev_pool[(size_t)h->ev_used * (FIBAR_NSTAGES + 1)];
+        h->ev_used += 1;
+    }
+    void mark(int boundary)
+    {
+        if (e) cudaEventRecord(e[boundary], s);
+    }
+};
+
+// Enqueue the whole per-read-out pipeline.  out == nullptr: apply only (flush).
+int process(fibar_t *h, unsigned long long t_read, float *out, cudaStream_t s)
+{
+    const KParams &kp = h->kp;
+    const Bufs &b = h->b;
+    SegTable T;
+    memset(&T, 0, sizeof(T));
+    T.nseg = (unsigned)h->seg_ptr.size();
+    for (unsigned i = 0; i < T.nseg; ++i) {
+        T.ptr[i] = h->seg_ptr[i];
+        T.n[i] = h->seg_n[i];
+    }
+    T.carry_slot = (unsigned)h->carry_slot;
+    T.carry = b.carry[h->carry_slot];
+    T.carry_out = b.carry[1 - h->carry_slot];
+    T.t_read = t_read;
+    unsigned long long &nl = h->launches;
+    StageMarks mk(h, s);
+
+    mk.mark(FIBAR_STAGE_DECODE);
+    cudaError_t e = launch_decode(kp, b, T, s, nl);
+    if (e != cudaSuccess) return cuda_fail(h, e, "decode");
+    mk.mark(FIBAR_STAGE_SORT);
+    e = launch_sort(kp, b, h->sort_passes, h->epoch, s, nl);
+    h->epoch += SORT_MAX_PASSES;
+    if (e != cudaSuccess) return cuda_fail(h, e, "sort");
+    const unsigned long long *sorted = b.rec[h->sort_passes & 1];
+    mk.mark(FIBAR_STAGE_WALK);
+    e = launch_walk(kp, b, sorted, s, nl);
+    if (e != cudaSuccess) return cuda_fail(h, e, "walk");
+    mk.mark(FIBAR_STAGE_DET_COUNTS);
+    if (kp.spatial) e = launch_det_counts(kp, b, s, nl);
+    mk.mark(FIBAR_STAGE_DET_PASS1);
+    if (kp.spatial && e == cudaSuccess) e = launch_det_pass1(kp, b, s, nl);
+    mk.mark(FIBAR_STAGE_DET_PASS2);
+    if (kp.spatial && e == cudaSuccess) e = launch_det_pass2(kp, b, s, nl);
+    mk.mark(FIBAR_STAGE_DET_FIX);
+    if (kp.spatial && e == cudaSuccess) e = launch_det_fix(kp, b, s, nl);
+    if (e != cudaSuccess) return cuda_fail(h, e, "detector");
+    mk.mark(FIBAR_STAGE_S1);
+    if (kp.spatial && kp.blur_mode == 0) {
+        e = launch_s1(kp, b, s, nl);
+        if (e != cudaSuccess) return cuda_fail(h, e, "S1 blur");
+    }
+    mk.mark(FIBAR_STAGE_READOUT);
+    if (out) {
+        e = launch_readout(kp, b, out, s, nl);
+        if (e != cudaSuccess) return cuda_fail(h, e, "readout");
+    }
+    mk.mark(FIBAR_STAGE_COMMIT);
+    h->carry_slot = 1 - h->carry_slot;
+    e = launch_commit(kp, b, h->carry_slot, s, nl);
+    if (e != cudaSuccess) return cuda_fail(h, e, "commit");
+    mk.mark(FIBAR_NSTAGES);
+    h->seg_ptr.clear();
+    h->seg_n.clear();
+    h->staging_used = 0;
+    return FIBAR_OK;
+}
+
+int check_device_error(fibar_t *h)
+{
+    unsigned err = 0;
+    cudaError_t e = cudaMemcpy(&err, &h->b.ctrl->error, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "error flag");
+    if (err) {
+        char msg[128];
+        snprintf(msg, sizeof msg, "a bounded device wait gave up (flags 0x%x)", err);
+        return fail(h, FIBAR_ETIMEOUT, msg);
+    }
+    return FIBAR_OK;
+}
+
+}  // namespace
+
+extern "C" int fibar_readout(fibar_t *h, uint64_t t_us, float *out, int on_device, void *cuda_stream)
+{
+    if (!h) return FIBAR_EINVAL;
+    if (!out) return fail(h, FIBAR_EINVAL, "readout: null output");
+    if (h->have_readout && t_us < h->last_readout)
+        return fail(h, FIBAR_EORDER, "readout: time earlier than the previous read-out");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (on_device && ((uintptr_t)out & 3) != 0) return fail(h, FIBAR_EINVAL, "readout: misaligned output");
+    float *dst = on_device ? out : h->b.out_staging;
+    int rc = process(h, t_us, dst, s);
+    if (rc) return rc;
+    h->have_readout = true;
+    h->last_readout = t_us;
+    h->readouts += 1;
+    if (!on_device) {
+        cudaError_t e = cudaMemcpyAsync(out, h->b.out_staging, (size_t)h->kp.npix * sizeof(float),
+                                        cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "readout: device-to-host copy");
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "readout: sync");
+        return check_device_error(h);
+    }
+    return FIBAR_OK;
+}
+
+extern "C" int fibar_flush(fibar_t *h, void *cuda_stream)
+{
+    if (!h) return FIBAR_EINVAL;
+    int rc = process(h, ~0ull, nullptr, (cudaStream_t)cuda_stream);
+    if (rc) return rc;
+    h->pending_upper = 0;
+    return FIBAR_OK;
+}
+
+namespace {
+
+int read_ctrl(fibar_t *h, Ctrl *c, cudaStream_t s)
+{
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sync");
+    e = cudaMemcpy(c, h->b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "control block");
+    unsigned long long segs = 0;
+    for (unsigned v : h->seg_n) segs += v;
+    h->pending_upper = c->carry_n[h->carry_slot] + segs;
+    if (c->error) {
+        char msg[128];
+        snprintf(msg, sizeof msg, "a bounded device wait gave up (flags 0x%x)", c->error);
+        return fail(h, FIBAR_ETIMEOUT, msg);
+    }
+    return FIBAR_OK;
+}
+
+unsigned long long q_targ_of(const fibar_t *h, const DetState &d)
+{
+    unsigned long long q = d.Y ? d.X / d.Y : h->kp.q_min;
+    q = std::min<unsigned long long>(q, h->kp.q_max);
+    q = std::max<unsigned long long>(q, h->kp.q_min);
+    return q;
+}
+
+}  // namespace
+
+extern "C" int fibar_stats(fibar_t *h, fibar_stats_t *st, void *cuda_stream)
+{
+    if (!h || !st) return FIBAR_EINVAL;
+    Ctrl c;
+    int rc = read_ctrl(h, &c, (cudaStream_t)cuda_stream);
+    memset(st, 0, sizeof(*st));
+    st->events_pushed = h->pushed;
+    st->events_applied = c.base;
+    st->events_dropped = c.dropped;
+    st->events_pending = h->pending_upper;
+    st->readouts = h->readouts;
+    if (h->kp.spatial) {
+        st->q = c.base - (unsigned long long)c.det.h;
+        st->q_targ = q_targ_of(h, c.det);
+        st->n_ap = c.det.nap;
+        st->n_at = c.det.nat;
+    }
+    st->detector_fixups = c.fixups;
+    st->kernel_launches = h->launches;
+    return rc;
+}
+
+extern "C" int fibar_set_timing(fibar_t *h, int enable)
+{
+    if (!h) return FIBAR_EINVAL;
+    if (enable && h->ev_pool.empty()) {
+        h->ev_pool.resize((size_t)EV_SETS * (FIBAR_NSTAGES + 1));
+        for (cudaEvent_t &e : h->ev_pool) {
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return cuda_fail(h, r, "set_timing: event");
+        }
+    }
+    h->timing = enable != 0;
+    return FIBAR_OK;
+}
+
+extern "C" int fibar_stage_times(fibar_t *h, fibar_stage_times_t *t, int reset, void *cuda_stream)
+{
+    if (!h || !t) return FIBAR_EINVAL;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stage_times: sync");
+    fold_stage_events(h);
+    for (int i = 0; i < FIBAR_NSTAGES; ++i) t->ms[i] = h->stage_ms[i];
+    t->calls = h->stage_calls;
+    if (reset) {
+        memset(h->stage_ms, 0, sizeof(h->stage_ms));
+        h->stage_calls = 0;
+    }
+    return FIBAR_OK;
+}
+
+extern "C" int fibar_debug_state(fibar_t *h, fibar_state_view_t *v, void *cuda_stream)
+{
+    if (!h || !v) return FIBAR_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    Ctrl c;
+    int rc = read_ctrl(h, &c, s);
+    if (rc) return rc;
+    const size_t npix = h->kp.npix;
+    cudaError_t e = cudaSuccess;
+    if (v->pbar) e = cudaMemcpy(v->pbar, h->b.pbar, npix * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && v->L) e = cudaMemcpy(v->L, h->b.L, npix * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && v->last_idx) e = cudaMemcpy(v->last_idx, h->b.last_pix, npix * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "debug_state copy");
+    v->k = c.base;
+    if (h->kp.spatial) {
+        v->h = (unsigned long long)c.det.h;
+        v->q = c.base - v->h;
+        v->q_targ = q_targ_of(h, c.det);
+        v->n_ap = c.det.nap;
+        v->n_at = c.det.nat;
+    } else {
+        v->h = c.base;
+        v->q = 0;
+        v->q_targ = 0;
+        v->n_ap = v->n_at = 0;
+    }
+    const bool want_cnt = v->cnt || v->tcnt || v->stale;
+    if (want_cnt) {
+        std::vector<uint32_t> cnt(npix, 0);
+        if (h->kp.spatial && v->q > 0) {
+            if (!h->b.dbg_cnt) {
+                e = cudaMalloc((void **)&h->b.dbg_cnt, npix * 4);
+                if (e != cudaSuccess) return cuda_fail(h, e, "debug_state alloc");
+            }
+            e = cudaMemsetAsync(h->b.dbg_cnt, 0, npix * 4, s);
+            if (e == cudaSuccess) e = launch_debug_counts(h->kp, h->b, h->b.dbg_cnt, s, h->launches);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess) e = cudaMemcpy(cnt.data(), h->b.dbg_cnt, npix * 4, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(h, e, "debug_state counts");
+        }
+        if (v->cnt) memcpy(v->cnt, cnt.data(), npix * 4);
+        if (v->tcnt) {
+            memset(v->tcnt, 0, h->kp.ntiles);
+            for (size_t i = 0; i < npix; ++i) {
+                const size_t x = i % h->W, y = i / h->W;
+                if (cnt[i]) v->tcnt[(y / 2) * h->kp.tiles_w + x / 2] += 1;
+            }
+        }
+        if (v->stale) {
+            std::vector<unsigned long long> last(npix);
+            e = cudaMemcpy(last.data(), h->b.last_pix, npix * 8, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(h, e, "debug_state last");
+            for (size_t i = 0; i < npix; ++i)
+                v->stale[i] = (h->kp.spatial && last[i] != NONE64 && cnt[i] == 0) ? 1 : 0;
+        }
+    }
+    return FIBAR_OK;
+}

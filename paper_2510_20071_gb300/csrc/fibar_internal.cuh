@@ -1,0 +1,196 @@
+// Internal declarations shared by the FIBAR CUDA translation units.
+//
+// Device data layout (one handle = one sensor stream):
+//   per pixel  : pbar f32, L f32 (row-major), last_pix u64 (global index of the pixel's
+//                last applied event, ~0 = none)
+//   per tile   : last_tile u64 (2x2 tiles aligned at (0,0))
+//   event ring : for global event index g, slot g & ring_mask holds
+//                ring_npt = {nP, nT}: distance to the next event of the same pixel /
+//                tile (0xFFFFFFFF = none yet or >= 2^32-1), ring_pix = pixel id.
+//                The active event queue (Sec. 4.2) is always the index window [h, k].
+//   batch      : arrays indexed by the batch-relative event index k (0 .. m-1):
+//                dpt = {dP, dT}: distance to the previous event of the same pixel / tile
+//                qout = queue length after the pops of step k (window = [k+1-q, k]).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fibar.h"
+
+namespace fibar {
+
+constexpr uint32_t SAT = 0xFFFFFFFFu;          // saturated / absent distance
+constexpr unsigned long long NONE64 = ~0ull;   // "no event yet"
+constexpr int DEC_THREADS = 256;
+constexpr int DEC_PER_THREAD = 16;
+constexpr int DEC_TILE = DEC_THREADS * DEC_PER_THREAD;   // records per decode tile
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_PER_THREAD = 16;
+constexpr int SORT_TILE = SORT_THREADS * SORT_PER_THREAD;
+constexpr int SORT_MAX_PASSES = 4;
+constexpr int MAXSEG = 192;                    // pending device packets per read-out
+constexpr uint32_t CHUNK = 256;                // minimum detector chunk length (events)
+constexpr unsigned DET_G = 255;                // reach of the guessed windows, in chunks
+constexpr unsigned SPIN_LIMIT = 1u << 20;      // bounded device waits (~1 s)
+
+// error bits in Ctrl::error
+constexpr unsigned ERR_DEC_WAIT = 1u;
+constexpr unsigned ERR_SORT_WAIT = 2u;
+constexpr unsigned ERR_BAD_STATE = 4u;
+constexpr unsigned ERR_S1_WAIT = 8u;
+
+// Detector state after some step: window [h, k] (h batch-relative or global, see use),
+// distinct pixels / tiles in the window, and q_targ for the next step as the ratio
+// X / Y (Eq. 20 before the floor and the clamp).
+struct DetState {
+    long long h;
+    unsigned int nap, nat;
+    unsigned long long X, Y;
+};
+
+struct Ctrl {
+    unsigned long long base;     // global index of the first event of the current batch
+    unsigned long long dropped;  // out-of-range records skipped so far
+    unsigned int m;              // valid events in the current batch
+    unsigned int consumed;       // pending records consumed by the last decode
+    unsigned int carry_n[2];     // records left pending in carry buffer 0 / 1
+    unsigned int dec_ticket;
+    unsigned int sort_ticket[SORT_MAX_PASSES];
+    unsigned int hist_done;
+    unsigned int cnt_done;
+    unsigned int error;
+    unsigned int unmerged;       // chunks whose second detector pass did not merge
+    unsigned int fixups;         // batches that needed the serial detector fixup
+    unsigned int S, nchunks, G, Gold;
+    unsigned int N0P, N0T;
+    unsigned int batch_no;       // read-outs/flushes committed (epoch of S1 flags)
+    DetState det;                // detector state at the batch start (h global)
+    long long h_prev;            // global h before the current batch (set by the fixup)
+    unsigned int nblur;          // S1: stale pixels (blurs) in the current batch
+    unsigned int blur_ticket;    // S1: dataflow work counter
+    unsigned int sel_ticket;     // S1: stale-list compaction tile counter
+    unsigned int pad2_;
+};
+
+// Constant per-handle parameters passed to kernels by value.
+struct KParams {
+    uint32_t W, H, tiles_w, tiles_h;
+    uint32_t npix, ntiles;
+    float a, oma, b, g;          // alpha, 1 - alpha, beta, (1 + beta) / 2
+    float log2b;                 // log2(beta) (S1: beta^m for long gaps)
+    float c_on, c_off;
+    uint32_t q_min, q_max;
+    uint32_t numA, den;          // fill_num * 4, fill_den  (Eq. 20 with A = 4)
+    unsigned long long ring_mask;
+    unsigned long long live;     // ring slots that stay valid behind the batch start
+    uint32_t max_pending;
+    uint32_t key_bits;           // bits of the tile id used as sort key
+    int spatial, blur_mode;
+};
+
+struct SegTable {
+    const int4 *ptr[MAXSEG];
+    unsigned int n[MAXSEG];
+    unsigned int nseg;
+    unsigned int carry_slot;     // ctrl->carry_n[carry_slot] = records in `carry`
+    const int4 *carry;
+    int4 *carry_out;
+    unsigned long long t_read;
+};
+
+struct Bufs {
+    Ctrl *ctrl;
+    float *pbar, *L;
+    unsigned long long *last_pix, *last_tile;
+    int4 *staging;
+    int4 *carry[2];
+    unsigned long long *dec_status;
+    unsigned long long *rec[2];
+    unsigned int *sort_hist;     // [SORT_MAX_PASSES][256]
+    unsigned int *sort_base;     // [SORT_MAX_PASSES][256]
+    unsigned long long *sort_status;
+    uint2 *dpt;
+    unsigned int *qout;
+    uint2 *ring_npt;
+    unsigned int *ring_pix;
+    // detector chunk data
+    unsigned short *dM;          // [chunks + G][2][G + 1] suffix histograms
+    DetState *E0, *E1, *E2;
+    unsigned char *merged;
+    float *out_staging;
+    unsigned int *dbg_cnt;
+    // S1 (blur in place when a pixel goes stale)
+    unsigned int *plist;         // [maxp] batch events grouped by pixel (tile-major), in order
+    float *plnb;                 // [maxp] L without this batch's blurs after that event
+    unsigned int *epos;          // [maxp] ordinal of batch event k within its pixel's list
+    unsigned int *lbl;           // [maxp] latest blur attached to the pixel's events <= position
+    int4 *s1_info;               // [npix] {batch_no, list start, list length, previous event - base}
+    float *s1_linit;             // [npix] L at the batch start (pixels with batch events)
+    unsigned int *popk;          // [maxp + npix] pop step | stale << 31 of each popped event
+    unsigned int *blur_ord;      // [maxp + npix] blur ordinal of each popped event (or ~0)
+    unsigned int *bk, *bpix;     // [maxp + npix] step and pixel of each blur
+    int *bj;                     // [maxp + npix] popped event (batch-relative) of each blur
+    float *bD;                   // [maxp + npix] blurred value minus L-without-blurs
+    unsigned int *bflag;         // [maxp + npix] batch_no once bD is published
+    unsigned long long *sel_status;
+    float *beta_pow;             // [64] beta^m
+    size_t max_pops, max_sel_tiles;
+    size_t max_chunks, max_dec_tiles, max_sort_tiles;
+};
+
+}  // namespace fibar
+
+struct fibar_s {
+    fibar::KParams kp;
+    fibar_params_t params;
+    double alpha, beta;
+    uint32_t W, H;
+    uint32_t sort_passes;
+    unsigned long long R;
+    fibar::Bufs b;
+    // pending (host view)
+    std::vector<const int4 *> seg_ptr;
+    std::vector<unsigned int> seg_n;
+    unsigned long long staging_used;
+    unsigned long long pending_upper;   // upper bound of records not yet applied
+    int carry_slot;
+    unsigned int epoch;
+    bool have_readout;
+    unsigned long long last_readout;
+    unsigned long long pushed, readouts;
+    int device;
+    std::string err;
+    unsigned long long launches;
+    // per-stage timing: events[i][0..FIBAR_NSTAGES] bracket the stages of read-out i
+    bool timing;
+    std::vector<cudaEvent_t> ev_pool;
+    unsigned ev_used;            // read-outs recorded in ev_pool
+    double stage_ms[FIBAR_NSTAGES];
+    unsigned long long stage_calls;
+};
+
+namespace fibar {
+// launchers (kernels live in their own translation units); `nl` counts kernel launches
+cudaError_t launch_init(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
+cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, cudaStream_t s,
+                          unsigned long long &nl);
+cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsigned epoch,
+                        cudaStream_t s, unsigned long long &nl);
+cudaError_t launch_walk(const KParams &kp, const Bufs &b, const unsigned long long *sorted,
+                        cudaStream_t s, unsigned long long &nl);
+cudaError_t launch_det_counts(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
+cudaError_t launch_det_pass1(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
+cudaError_t launch_det_pass2(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
+cudaError_t launch_det_fix(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
+cudaError_t launch_readout(const KParams &kp, const Bufs &b, float *out, cudaStream_t s,
+                           unsigned long long &nl);
+cudaError_t launch_commit(const KParams &kp, const Bufs &b, int next_carry_slot, cudaStream_t s,
+                          unsigned long long &nl);
+cudaError_t launch_s1(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
+cudaError_t launch_debug_counts(const KParams &kp, const Bufs &b, unsigned int *cnt,
+                                cudaStream_t s, unsigned long long &nl);
+int grid_for(int sms_mult);
+}  // namespace fibar

@@ -1,0 +1,439 @@
+// Ingest: decode packed events, cut the read-out prefix, compact, and sort by tile.
+//
+// k_decode  - one pass over the pending records (a carry buffer of records left
+//             pending by the previous read-out, then the pushed packets in order).
+//             Each record is read once with a 16-byte load.  A decoupled look-back
+//             over tiles of 4096 records carries (events kept, position of the first
+//             record whose time stamp is later than the read-out time): the applied
+//             set is the longest prefix with t <= t_read (Eq. 4's t_k <= t), minus
+//             out-of-range records, which are counted and skipped.  Kept events get
+//             consecutive batch indices k and a 64-bit sort record
+//             (tile id << 32 | k << 3 | sub-pixel << 1 | OFF).  Records after the
+//             cut are copied to the other carry buffer.
+// k_sort_*  - stable LSD radix sort of the records by tile id, 8-bit digits
+//             (onesweep: one histogram kernel for all digits, then one kernel per
+//             digit with a per-digit decoupled look-back), so that every 2x2 tile's
+//             events end up contiguous and in arrival order.
+#include "fibar_internal.cuh"
+
+namespace fibar {
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim.x == 256).
+__device__ __forceinline__ unsigned block_excl_scan256(unsigned v, unsigned *s_warp, unsigned *total)
+{
+    const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned t = threadIdx.x < 8 ? s_warp[threadIdx.x] : 0u;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (threadIdx.x < 8) s_warp[threadIdx.x + 8] = t;  // inclusive warp prefix
+    }
+    __syncthreads();
+    unsigned warp_excl = w ? s_warp[8 + w - 1] : 0u;
+    *total = s_warp[15];
+    unsigned r = warp_excl + x - v;
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------------
+// decode
+// ---------------------------------------------------------------------------------
+constexpr unsigned S_NONE = 0x7FFFFFFFu;
+constexpr unsigned NOREC = 0xFFFFFFFFu;
+
+struct DAgg {
+    unsigned s;  // absolute position of the first late record, S_NONE if none
+    unsigned c;  // kept events, counted only before any late record
+};
+
+__device__ __forceinline__ DAgg dcombine(DAgg a, DAgg b)  // a precedes b
+{
+    if (a.s != S_NONE) return a;
+    return DAgg{b.s, a.c + b.c};
+}
+
+__device__ __forceinline__ unsigned long long dpack(unsigned flag, DAgg a)
+{
+    return ((unsigned long long)flag << 62) | ((unsigned long long)a.s << 31) | a.c;
+}
+
+__device__ __forceinline__ int4 fetch_rec(const SegTable &T, const int4 *const *s_ptr,
+                                          const unsigned *s_start, unsigned carry_n, unsigned pos)
+{
+    if (pos < carry_n) return __ldg(T.carry + pos);
+    int lo = 0, hi = (int)T.nseg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (s_start[mid] <= pos) lo = mid; else hi = mid - 1;
+    }
+    return __ldg(s_ptr[lo] + (pos - s_start[lo]));
+}
+
+__global__ void __launch_bounds__(DEC_THREADS)
+k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigned long long *rec_out)
+{
+    __shared__ unsigned s_start[MAXSEG + 1];
+    __shared__ const int4 *s_ptr[MAXSEG];
+    __shared__ unsigned s_info[DEC_TILE];
+    __shared__ unsigned s_warp[16];
+    __shared__ unsigned s_tile, s_vmin, s_pre_s, s_pre_c, s_drop;
+
+    const unsigned carry_n = ctrl->carry_n[T.carry_slot];
+    if (threadIdx.x == 0) {
+        unsigned acc = carry_n;
+        for (unsigned i = 0; i < T.nseg; ++i) {
+            s_start[i] = acc;
+            s_ptr[i] = T.ptr[i];
+            acc += T.n[i];
+        }
+        s_start[T.nseg] = acc;
+    }
+    __syncthreads();
+    const unsigned total = s_start[T.nseg];
+    const unsigned ntiles = (total + DEC_TILE - 1) / DEC_TILE;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_tile = atomicAdd(&ctrl->dec_ticket, 1u);
+            s_vmin = S_NONE;
+            s_drop = 0;
+        }
+        __syncthreads();
+        const unsigned tile = s_tile;
+        if (tile >= ntiles) break;
+        const unsigned pos0 = tile * DEC_TILE;
+
+        // coalesced 16-byte loads; classify each record
+        unsigned vloc = S_NONE;
+#pragma unroll 4
+        for (int i = 0; i < DEC_PER_THREAD; ++i) {
+            const unsigned r = i * DEC_THREADS + threadIdx.x;
+            const unsigned pos = pos0 + r;
+            unsigned info = NOREC;
+            if (pos < total) {
+                const int4 e = fetch_rec(T, s_ptr, s_start, carry_n, pos);
+                const unsigned x = (unsigned)e.x & 0xFFFFu, y = (unsigned)e.x >> 16;
+                const int p = (int)(signed char)(e.y & 0xFF);
+                const unsigned long long t =
+                    ((unsigned long long)(unsigned)e.w << 32) | (unsigned)e.z;
+                if (t > T.t_read) vloc = min(vloc, r);
+                const bool valid = x < kp.W && y < kp.H;
+                const unsigned tid_ = valid ? (y >> 1) * kp.tiles_w + (x >> 1) : 0u;
+                const unsigned sub = valid ? (((y & 1u) << 1) | (x & 1u)) : 0u;
+                info = (valid ? 0x80000000u : 0u) | (tid_ << 3) | (sub << 1) | (p > 0 ? 0u : 1u);
+            }
+            s_info[r] = info;
+        }
+        if (vloc != S_NONE) atomicMin(&s_vmin, vloc);
+        __syncthreads();
+        const unsigned vfirst = s_vmin;
+
+        // 16 contiguous records per thread, in arrival order
+        unsigned cnt = 0, drop = 0, keep = 0;
+#pragma unroll
+        for (int j = 0; j < DEC_PER_THREAD; ++j) {
+            const unsigned r = threadIdx.x * DEC_PER_THREAD + j;
+            const unsigned info = s_info[r];
+            if (info != NOREC && r < vfirst) {
+                if (info >> 31) { ++cnt; keep |= 1u << j; }
+                else ++drop;
+            }
+        }
+        unsigned tile_cnt;
+        const unsigned excl = block_excl_scan256(cnt, s_warp, &tile_cnt);
+        if (drop) atomicAdd(&s_drop, drop);
+
+        // decoupled look-back over tiles
+        if (threadIdx.x == 0) {
+            const DAgg own{vfirst != S_NONE ? pos0 + vfirst : S_NONE, tile_cnt};
+            DAgg pre{S_NONE, 0u};
+            if (tile == 0) {
+                st_release(&status[0], dpack(2u, own));
+            } else {
+                st_release(&status[tile], dpack(1u, own));
+                DAgg acc{S_NONE, 0u};
+                bool empty = true;
+                int j = (int)tile - 1;
+                unsigned spins = 0;
+                for (;;) {
+                    const unsigned long long v = ld_acquire(&status[j]);
+                    const unsigned flag = (unsigned)(v >> 62);
+                    if (flag == 0u) {
+                        if (++spins > SPIN_LIMIT) { atomicOr(&ctrl->error, ERR_DEC_WAIT); break; }
+                        continue;
+                    }
+                    const DAgg a{(unsigned)(v >> 31) & 0x7FFFFFFFu, (unsigned)v & 0x7FFFFFFFu};
+                    acc = empty ? a : dcombine(a, acc);
+                    empty = false;
+                    if (flag == 2u || j == 0) break;
+                    --j;
+                }
+                pre = acc;
+                st_release(&status[tile], dpack(2u, dcombine(pre, own)));
+            }
+            s_pre_s = pre.s;
+            s_pre_c = pre.c;
+            if (tile == ntiles - 1) {
+                const DAgg inc = tile == 0 ? own : dcombine(pre, own);
+                const unsigned s = inc.s == S_NONE ? total : inc.s;
+                ctrl->m = inc.c;
+                ctrl->consumed = s;
+                ctrl->carry_n[1 - T.carry_slot] = total - s;
+            }
+        }
+        __syncthreads();
+        const unsigned pre_s = s_pre_s, pre_c = s_pre_c;
+        if (pre_s == S_NONE) {
+            unsigned k = pre_c + excl;
+#pragma unroll
+            for (int j = 0; j < DEC_PER_THREAD; ++j) {
+                if (keep >> j & 1u) {
+                    const unsigned info = s_info[threadIdx.x * DEC_PER_THREAD + j];
+                    rec_out[k] = ((unsigned long long)((info >> 3) & 0x0FFFFFFFu) << 32) |
+                                 ((unsigned long long)k << 3) | (info & 7u);
+                    ++k;
+                }
+            }
+            if (threadIdx.x == 0 && s_drop) atomicAdd(&ctrl->dropped, (unsigned long long)s_drop);
+            if (vfirst != S_NONE) {
+                const unsigned s = pos0 + vfirst;
+                for (int i = 0; i < DEC_PER_THREAD; ++i) {
+                    const unsigned r = i * DEC_THREADS + threadIdx.x;
+                    const unsigned pos = pos0 + r;
+                    if (r >= vfirst && pos < total)
+                        T.carry_out[pos - s] = fetch_rec(T, s_ptr, s_start, carry_n, pos);
+                }
+            }
+        } else {
+            for (int i = 0; i < DEC_PER_THREAD; ++i) {
+                const unsigned pos = pos0 + i * DEC_THREADS + threadIdx.x;
+                if (pos < total) T.carry_out[pos - pre_s] = fetch_rec(T, s_ptr, s_start, carry_n, pos);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// radix sort by tile id (stable)
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_sort_hist(Ctrl *ctrl, const unsigned long long *rec, unsigned passes, unsigned *ghist,
+            unsigned *gbase)
+{
+    __shared__ unsigned h[SORT_MAX_PASSES][256];
+    __shared__ unsigned s_warp[16];
+    __shared__ bool s_last;
+    for (unsigned i = threadIdx.x; i < SORT_MAX_PASSES * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const unsigned m = ctrl->m;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const unsigned key = (unsigned)(rec[i] >> 32);
+        for (unsigned p = 0; p < passes; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (unsigned p = 0; p < passes; ++p) {
+        const unsigned v = h[p][threadIdx.x];
+        if (v) atomicAdd(&ghist[p * 256 + threadIdx.x], v);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&ctrl->hist_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (unsigned p = 0; p < passes; ++p) {
+        const unsigned v = atomicExch(&ghist[p * 256 + threadIdx.x], 0u);
+        unsigned tot;
+        const unsigned ex = block_excl_scan256(v, s_warp, &tot);
+        gbase[p * 256 + threadIdx.x] = ex;
+    }
+    if (threadIdx.x == 0) ctrl->hist_done = 0;
+}
+
+__device__ __forceinline__ unsigned lookback_digit(unsigned long long *status, unsigned tile,
+                                                   unsigned d, unsigned epoch, unsigned cnt,
+                                                   Ctrl *ctrl)
+{
+    const unsigned long long tag = (unsigned long long)epoch << 32;
+    if (tile == 0) {
+        st_release(&status[d], tag | (2ull << 30) | cnt);
+        return 0;
+    }
+    st_release(&status[(size_t)tile * 256 + d], tag | (1ull << 30) | cnt);
+    unsigned acc = 0;
+    int j = (int)tile - 1;
+    unsigned spins = 0;
+    for (;;) {
+        const unsigned long long v = ld_acquire(&status[(size_t)j * 256 + d]);
+        const unsigned flag = (unsigned)(v >> 30) & 3u;
+        if ((unsigned)(v >> 32) != epoch || flag == 0u) {
+            if (++spins > SPIN_LIMIT) { atomicOr(&ctrl->error, ERR_SORT_WAIT); break; }
+            continue;
+        }
+        acc += (unsigned)v & 0x3FFFFFFFu;
+        if (flag == 2u || j == 0) break;
+        --j;
+    }
+    st_release(&status[(size_t)tile * 256 + d], tag | (2ull << 30) | (acc + cnt));
+    return acc;
+}
+
+// dynamic shared memory layout of k_sort_pass
+struct SortSmem {
+    unsigned long long key[SORT_TILE];
+    unsigned long long out[SORT_TILE];
+    unsigned short rank[SORT_TILE];
+    unsigned whist[8][256];
+    unsigned tdig[256];
+    unsigned gpos[256];
+    unsigned warp[16];
+    unsigned tile;
+};
+
+__global__ void __launch_bounds__(SORT_THREADS)
+k_sort_pass(Ctrl *ctrl, const unsigned long long *in, unsigned long long *out, unsigned pass,
+            unsigned epoch, const unsigned *gbase, unsigned long long *status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SortSmem &S = *reinterpret_cast<SortSmem *>(smem_raw);
+    const unsigned m = ctrl->m;
+    const unsigned ntiles = (m + SORT_TILE - 1) / SORT_TILE;
+    const unsigned shift = 32 + 8 * pass;
+    const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    for (;;) {
+        if (threadIdx.x == 0) S.tile = atomicAdd(&ctrl->sort_ticket[pass], 1u);
+        for (unsigned i = threadIdx.x; i < 8 * 256; i += SORT_THREADS) (&S.whist[0][0])[i] = 0;
+        __syncthreads();
+        const unsigned tile = S.tile;
+        if (tile >= ntiles) break;
+        const unsigned base = tile * SORT_TILE;
+        const unsigned n_here = min((unsigned)SORT_TILE, m - base);
+#pragma unroll 4
+        for (int i = 0; i < SORT_PER_THREAD; ++i) {
+            const unsigned r = i * SORT_THREADS + threadIdx.x;
+            S.key[r] = r < n_here ? in[base + r] : ~0ull;
+        }
+        __syncthreads();
+        // stable rank within (warp range, digit): warp w owns records [w*512, w*512+512)
+        for (int q = 0; q < 16; ++q) {
+            const unsigned r = w * 512 + q * 32 + lane;
+            const bool valid = r < n_here;
+            const unsigned d = valid ? (unsigned)(S.key[r] >> shift) & 255u : 256u;
+            const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+            const unsigned rank = __popc(peers & lt_mask);
+            if (valid) S.rank[r] = (unsigned short)(S.whist[w][d] + rank);
+            __syncwarp();
+            if (valid && rank == 0) S.whist[w][d] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        // per-digit exclusive offsets of each warp, and the tile's digit counts
+        const unsigned d = threadIdx.x;
+        unsigned run = 0;
+#pragma unroll
+        for (int ww = 0; ww < 8; ++ww) {
+            const unsigned c = S.whist[ww][d];
+            S.whist[ww][d] = run;
+            run += c;
+        }
+        unsigned tot;
+        const unsigned tdig = block_excl_scan256(run, S.warp, &tot);
+        S.tdig[d] = tdig;
+        const unsigned prefix = lookback_digit(status, tile, d, epoch, run, ctrl);
+        S.gpos[d] = gbase[pass * 256 + d] + prefix;
+        __syncthreads();
+        // reorder the tile by digit in shared memory
+#pragma unroll 4
+        for (int i = 0; i < SORT_PER_THREAD; ++i) {
+            const unsigned r = i * SORT_THREADS + threadIdx.x;
+            if (r < n_here) {
+                const unsigned long long k = S.key[r];
+                const unsigned dd = (unsigned)(k >> shift) & 255u;
+                const unsigned ww = r >> 9;
+                S.out[S.tdig[dd] + S.whist[ww][dd] + S.rank[r]] = k;
+            }
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int i = 0; i < SORT_PER_THREAD; ++i) {
+            const unsigned lp = i * SORT_THREADS + threadIdx.x;
+            if (lp < n_here) {
+                const unsigned long long k = S.out[lp];
+                const unsigned dd = (unsigned)(k >> shift) & 255u;
+                out[S.gpos[dd] + (lp - S.tdig[dd])] = k;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+static int g_sms = 0;
+
+int grid_for(int mult)
+{
+    if (!g_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms <= 0) g_sms = 1;
+    }
+    return g_sms * mult;
+}
+
+cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, cudaStream_t s,
+                          unsigned long long &nl)
+{
+    nl += 1;
+    k_decode<<<grid_for(2), DEC_THREADS, 0, s>>>(kp, t, b.ctrl, b.dec_status, b.rec[0]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsigned epoch,
+                        cudaStream_t s, unsigned long long &nl)
+{
+    nl += 1 + passes;
+    (void)kp;
+    static bool attr_set = false;
+    const size_t smem = sizeof(SortSmem);
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_sort_hist<<<grid_for(2), 256, 0, s>>>(b.ctrl, b.rec[0], passes, b.sort_hist, b.sort_base);
+    for (unsigned p = 0; p < passes; ++p) {
+        k_sort_pass<<<grid_for(2), SORT_THREADS, smem, s>>>(b.ctrl, b.rec[p & 1], b.rec[(p + 1) & 1], p,
+                                                           epoch + p, b.sort_base, b.sort_status);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fibar

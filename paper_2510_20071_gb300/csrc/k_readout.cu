@@ -1,0 +1,163 @@
+// Read-out, batch commit and small bookkeeping kernels.
+//
+// k_readout_s2 - masked separable 3x3 Gaussian ([1,2,1] x [1,2,1] / 16, weights of taps
+//   outside the sensor dropped and the rest renormalised, Sec. 4.2's 3x3 Gaussian):
+//   out_i = blur(L)_i where pixel i is stale (had an event, none queued: last_pix < h),
+//   L_i elsewhere.  Each block stages a (32+2) x (8+2) halo of L in shared memory and
+//   applies the horizontal then the vertical [1,2,1] pass.
+// k_commit     - advances the batch base and resets the per-read-out counters.
+#include "fibar_internal.cuh"
+
+namespace fibar {
+
+constexpr int RB_X = 32, RB_Y = 8;
+
+__global__ void __launch_bounds__(RB_X *RB_Y)
+k_readout_s2(KParams kp, const Ctrl *ctrl, const float *__restrict__ L,
+             const unsigned long long *__restrict__ last_pix, float *__restrict__ out)
+{
+    __shared__ float t[RB_Y + 2][RB_X + 2];
+    __shared__ float hs[RB_Y + 2][RB_X];
+    const int x0 = blockIdx.x * RB_X, y0 = blockIdx.y * RB_Y;
+    const int W = (int)kp.W, H = (int)kp.H;
+    for (int i = threadIdx.x; i < (RB_Y + 2) * (RB_X + 2); i += RB_X * RB_Y) {
+        const int ly = i / (RB_X + 2), lx = i % (RB_X + 2);
+        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        t[ly][lx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? L[(size_t)gy * W + gx] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (RB_Y + 2) * RB_X; i += RB_X * RB_Y) {
+        const int ly = i / RB_X, lx = i % RB_X;
+        hs[ly][lx] = t[ly][lx] + 2.f * t[ly][lx + 1] + t[ly][lx + 2];
+    }
+    __syncthreads();
+    const int lx = threadIdx.x % RB_X, ly = threadIdx.x / RB_X;
+    const int x = x0 + lx, y = y0 + ly;
+    if (x >= W || y >= H) return;
+    const size_t i = (size_t)y * W + x;
+    const unsigned long long h = (unsigned long long)ctrl->det.h;
+    const unsigned long long lp = last_pix[i];
+    const bool stale = lp != NONE64 && lp < h;
+    float v = t[ly + 1][lx + 1];
+    if (stale) {
+        const float wx = 4.f - (x == 0 ? 1.f : 0.f) - (x == W - 1 ? 1.f : 0.f);
+        const float wy = 4.f - (y == 0 ? 1.f : 0.f) - (y == H - 1 ? 1.f : 0.f);
+        v = (hs[ly][lx] + 2.f * hs[ly + 1][lx] + hs[ly + 2][lx]) / (wx * wy);
+    }
+    out[i] = v;
+}
+
+__global__ void k_copy(const float4 *__restrict__ in, float4 *__restrict__ out, size_t n4,
+                       const float *__restrict__ in1, float *__restrict__ out1, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = in[i];
+    const size_t tail = n4 * 4;
+    if (blockIdx.x == 0 && threadIdx.x < n - tail) out1[tail + threadIdx.x] = in1[tail + threadIdx.x];
+}
+
+// After the last kernel of a read-out: base += m, reset tickets and look-back status.
+__global__ void k_commit(Ctrl *ctrl, unsigned long long *dec_status, size_t n_status, int next_carry_slot)
+{
+    for (size_t i = threadIdx.x; i < n_status; i += blockDim.x) dec_status[i] = 0ull;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctrl->base += ctrl->m;
+        ctrl->m = 0;
+        ctrl->dec_ticket = 0;
+        for (int p = 0; p < SORT_MAX_PASSES; ++p) ctrl->sort_ticket[p] = 0;
+        ctrl->unmerged = 0;
+        ctrl->N0P = 0;
+        ctrl->N0T = 0;
+        ctrl->nblur = 0;
+        ctrl->blur_ticket = 0;
+        ctrl->sel_ticket = 0;
+        ctrl->batch_no += 1;
+        // the carry slot just consumed becomes the output slot of the next decode
+        ctrl->carry_n[1 - next_carry_slot] = 0;
+    }
+}
+
+__global__ void k_init(KParams kp, Ctrl *ctrl)
+{
+    if (threadIdx.x != 0) return;
+    ctrl->base = 0;
+    ctrl->dropped = 0;
+    ctrl->m = 0;
+    ctrl->consumed = 0;
+    ctrl->carry_n[0] = ctrl->carry_n[1] = 0;
+    ctrl->dec_ticket = 0;
+    for (int p = 0; p < SORT_MAX_PASSES; ++p) ctrl->sort_ticket[p] = 0;
+    ctrl->hist_done = 0;
+    ctrl->cnt_done = 0;
+    ctrl->error = 0;
+    ctrl->unmerged = 0;
+    ctrl->fixups = 0;
+    ctrl->N0P = ctrl->N0T = 0;
+    ctrl->batch_no = 1;
+    ctrl->h_prev = 0;
+    ctrl->nblur = 0;
+    ctrl->blur_ticket = 0;
+    ctrl->sel_ticket = 0;
+    ctrl->det.h = 0;
+    ctrl->det.nap = 0;
+    ctrl->det.nat = 0;
+    ctrl->det.X = kp.q_min;  // overwritten by the host with q_init
+    ctrl->det.Y = 1;
+}
+
+// Debug: per-pixel count of queued events, cnt[pix(j)] += 1 for j in [h, base).
+__global__ void k_debug_counts(KParams kp, const Ctrl *ctrl, const unsigned *ring_pix, unsigned *cnt)
+{
+    const unsigned long long h = (unsigned long long)ctrl->det.h, k = ctrl->base;
+    for (unsigned long long j = h + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < k;
+         j += (unsigned long long)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[ring_pix[j & kp.ring_mask]], 1u);
+}
+
+cudaError_t launch_init(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)
+{
+    nl += 1;
+    k_init<<<1, 32, 0, s>>>(kp, b.ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_readout(const KParams &kp, const Bufs &b, float *out, cudaStream_t s,
+                           unsigned long long &nl)
+{
+    nl += 1;
+    if (kp.spatial && kp.blur_mode == 1) {
+        dim3 grid((kp.W + RB_X - 1) / RB_X, (kp.H + RB_Y - 1) / RB_Y);
+        k_readout_s2<<<grid, RB_X * RB_Y, 0, s>>>(kp, b.ctrl, b.L, b.last_pix, out);
+    } else {
+        const size_t n = kp.npix;
+        const bool aligned = ((uintptr_t)out & 15) == 0;
+        if (aligned) {
+            const size_t n4 = n / 4;
+            k_copy<<<grid_for(4), 256, 0, s>>>((const float4 *)b.L, (float4 *)out, n4, b.L, out, n);
+        } else {
+            nl -= 1;
+            return cudaMemcpyAsync(out, b.L, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_commit(const KParams &kp, const Bufs &b, int next_carry_slot, cudaStream_t s,
+                          unsigned long long &nl)
+{
+    nl += 1;
+    (void)kp;
+    k_commit<<<1, 256, 0, s>>>(b.ctrl, b.dec_status, b.max_dec_tiles, next_carry_slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_counts(const KParams &kp, const Bufs &b, unsigned int *cnt, cudaStream_t s,
+                                unsigned long long &nl)
+{
+    nl += 1;
+    k_debug_counts<<<grid_for(2), 256, 0, s>>>(kp, b.ctrl, b.ring_pix, cnt);
+    return cudaGetLastError();
+}
+
+}  // namespace fibar

@@ -1,0 +1,179 @@
+"""GPU parity: the CUDA library against the FP64 oracle on the same seeded streams.
+
+Integer state (events applied, queue window h/q, q_targ, N_ap, N_at, per-pixel queued
+counts, per-tile active counts, stale masks, last event index) must match bit-exactly;
+L, p_bar and read-out images within 1e-4 absolute (log brightness at C = 0.2).
+"""
+import numpy as np
+import pytest
+import torch
+
+import eventsim
+from tests.harness import compare, plan_packets, run_gpu, run_oracle, sim
+
+pytestmark = pytest.mark.gpu
+
+MODES = {
+    "nsf": dict(spatial_filter=0),
+    "s1": dict(spatial_filter=1, blur_mode=0),
+    "s2": dict(spatial_filter=1, blur_mode=1),
+}
+
+
+def _check(oracle_mod, W, H, ev, steps, mode, device_push=True, host_out=False, **params):
+    p = dict(MODES[mode])
+    p.update(params)
+    o_imgs, o_states = run_oracle(oracle_mod, W, H, ev, steps, **p)
+    g_imgs, g_states, stats = run_gpu(W, H, ev, steps, device_push=device_push, host_out=host_out, **p)
+    worst = compare(W, H, o_imgs, o_states, g_imgs, g_states, spatial=p.get("spatial_filter", 1) == 1)
+    return worst, stats
+
+
+@pytest.mark.parametrize("mode", ["nsf", "s1", "s2"])
+def test_small_random_streams(oracle_mod, mode):
+    for (W, H, n, seed) in [(4, 4, 300, 1), (6, 4, 500, 2), (8, 8, 2000, 3), (5, 3, 400, 4),
+                            (1, 1, 50, 5), (2, 2, 100, 6), (33, 17, 5000, 7)]:
+        ev = eventsim.random_events(W, H, n, seed=seed)
+        steps = plan_packets(n, 97, 250, ev)
+        _check(oracle_mod, W, H, ev, steps, mode, q_min=1)
+
+
+@pytest.mark.parametrize("mode", ["nsf", "s1", "s2"])
+def test_sine_checker_several_tiles_and_ragged_tail(oracle_mod, mode):
+    W, H = 96, 72
+    ev = sim(W, H, 60_000, seed=3, noise=0.02)
+    steps = plan_packets(60_000, 4093, 9_999, ev)
+    _check(oracle_mod, W, H, ev, steps, mode, c_on=0.2, c_off=0.2)
+
+
+def test_config_sine_checker_240x180_1M_full(oracle_mod):
+    """240x180, 1,000,000 events, translating sinusoid+checker, seed 0, one read-out."""
+    ev = eventsim.make_config("sine_checker_240x180_1M")
+    steps = [("push", 0, 1_000_000), ("read", int(ev[-1, 1]))]
+    for mode in ["nsf", "s1", "s2"]:
+        worst, stats = _check(oracle_mod, 240, 180, ev, steps, mode, c_on=0.2, c_off=0.2)
+        assert worst <= 1e-4
+
+
+def test_config_perlin_1280x720_prefix(oracle_mod):
+    """1280x720 rotating+zooming Perlin with 2% noise events, 65,536-event packets and a
+    read-out every 1,000,000 events (first 3 M events of the stream)."""
+    n = 3_000_000
+    ev = eventsim.make_config("perlin_1280x720_200M", n_events=n, device="cuda").cpu()
+    steps = plan_packets(n, 65_536, 1_000_000, ev)
+    for mode in ["s2", "s1"]:
+        _check(oracle_mod, 1280, 720, ev, steps, mode, c_on=0.2, c_off=0.2)
+
+
+@pytest.mark.parametrize("mode", ["nsf", "s1", "s2"])
+def test_host_push_and_host_readout(oracle_mod, mode):
+    W, H = 40, 30
+    ev = sim(W, H, 20_000, seed=9)
+    steps = plan_packets(20_000, 3000, 7000, ev)
+    _check(oracle_mod, W, H, ev, steps, mode, device_push=False, host_out=True, c_on=0.2, c_off=0.2)
+
+
+def test_readout_mid_packet_and_nonmonotone_time(oracle_mod):
+    W, H = 24, 20
+    ev = eventsim.random_events(W, H, 3000, seed=11, t_step_us=3)
+    ev[1500, 1] = 10**9  # a late record blocks everything after it until a later read-out
+    steps = [("push", 0, 1000), ("read", 700), ("push", 1000, 3000), ("read", 2000),
+             ("read", 2000), ("read", 5000), ("read", 10**9), ("read", 10**10)]
+    for mode in ["nsf", "s1", "s2"]:
+        _check(oracle_mod, W, H, ev, steps, mode, q_min=1)
+
+
+def test_out_of_range_events_dropped(oracle_mod):
+    W, H = 16, 12
+    ev = eventsim.random_events(W, H, 2000, seed=12)
+    bad = eventsim.pack_events(torch.tensor([16, 3, 200, 0]), torch.tensor([0, 12, 5, 65535]),
+                               torch.tensor([1, -1, 1, 1]), torch.tensor([0, 0, 0, 0]))
+    ev = torch.cat([ev[:500], bad, ev[500:1500], bad, ev[1500:]])
+    ev[:, 1] = torch.arange(ev.shape[0])
+    steps = plan_packets(ev.shape[0], 333, 800, ev)
+    _, _, stats = run_gpu(W, H, ev, steps, **MODES["s2"])
+    assert stats["events_dropped"] == 8 and stats["events_applied"] == 2000
+    _check(oracle_mod, W, H, ev, steps, "s2")
+
+
+def test_packet_split_invariance(oracle_mod):
+    W, H = 48, 36
+    ev = sim(W, H, 30_000, seed=13, noise=0.05)
+    # single-event packets (host pushes coalesce in the staging buffer)
+    sub = 3000
+    steps = plan_packets(sub, 1, 700, ev[:sub])
+    imgs, states, _ = run_gpu(W, H, ev[:sub], steps, device_push=False, **MODES["s2"])
+    o_imgs, o_states = run_oracle(oracle_mod, W, H, ev[:sub], steps, **MODES["s2"])
+    compare(W, H, o_imgs, o_states, imgs, states)
+    # device packets of several sizes: identical results
+    results = []
+    for packet in [977, 8192, 30_000]:
+        steps = plan_packets(30_000, packet, None, ev)
+        imgs, states, _ = run_gpu(W, H, ev, steps, **MODES["s2"])
+        results.append((imgs[-1], states[-1]))
+    for img, st in results[1:]:
+        np.testing.assert_array_equal(img, results[0][0])
+        for key in ["h", "q_targ", "n_ap", "n_at"]:
+            assert st[key] == results[0][1][key]
+        np.testing.assert_array_equal(st["cnt"], results[0][1]["cnt"])
+
+
+def test_pending_device_packet_limit():
+    from paper_2510_20071_gb300 import FibarError, FIBAR_ENOMEM, Fibar
+    ev = eventsim.random_events(8, 8, 300, seed=1).cuda()
+    f = Fibar(8, 8)
+    for i in range(192):
+        f.push(ev[i:i + 1])
+    with pytest.raises(FibarError) as e:
+        f.push(ev[192:193])
+    assert e.value.code == FIBAR_ENOMEM
+    f.readout(10**9)
+    f.push(ev[192:193])  # accepted again after the read-out
+    f.flush()
+    assert f.stats()["events_applied"] == 193
+    f.close()
+
+
+@pytest.mark.parametrize("params", [dict(q_min=1), dict(q_min=7, q_init=50), dict(fill_num=7, fill_den=10),
+                                    dict(fill_num=1, fill_den=4), dict(t_cut=float("inf")),
+                                    dict(t_cut=100.0, c_on=0.25, c_off=0.35)])
+def test_parameter_variants(oracle_mod, params):
+    W, H = 30, 22
+    ev = sim(W, H, 25_000, seed=14, noise=0.03)
+    steps = plan_packets(25_000, 5000, 6000, ev)
+    _check(oracle_mod, W, H, ev, steps, "s2", **params)
+    _check(oracle_mod, W, H, ev, steps, "s1", **params)
+
+
+def test_degenerate_streams(oracle_mod):
+    # one pixel only (one tile holds every event: one long segment), one tile cycling,
+    # an empty read-out, and a push of zero events
+    W, H = 64, 64
+    for pixels in [[1000], [0, 1, 64, 65], [4095]]:
+        ev = eventsim.random_events(W, H, 20_000, seed=15, pixels=pixels)
+        steps = [("read", 0), ("push", 0, 0), ("push", 0, 20_000), ("read", 10**12)]
+        _check(oracle_mod, W, H, ev, steps, "s2", q_min=1)
+        _check(oracle_mod, W, H, ev, steps, "s1", q_min=1)
+        _check(oracle_mod, W, H, ev, steps, "nsf")
+
+
+def test_large_batch_many_chunks(oracle_mod):
+    """One read-out over 4 M events (16 k detector chunks) on 640x480."""
+    W, H = 640, 480
+    n = 4_000_000
+    ev = eventsim.simulate(W, H, n, scene=eventsim.SceneSpec(texture="perlin"), seed=21,
+                           noise_frac=0.02, device="cuda").cpu()
+    steps = [("push", 0, n), ("read", int(ev[-1, 1]))]
+    _check(oracle_mod, W, H, ev, steps, "s2", c_on=0.2, c_off=0.2)
+    _check(oracle_mod, W, H, ev, steps, "s1", c_on=0.2, c_off=0.2)
+
+
+def test_determinism(oracle_mod):
+    W, H = 64, 48
+    ev = sim(W, H, 50_000, seed=16, noise=0.02)
+    steps = plan_packets(50_000, 8192, 12_000, ev)
+    for mode in ["s1", "s2"]:
+        a = run_gpu(W, H, ev, steps, **MODES[mode])
+        b = run_gpu(W, H, ev, steps, **MODES[mode])
+        for x, y in zip(a[0], b[0]):
+            np.testing.assert_array_equal(x, y)
