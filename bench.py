@@ -166,9 +166,11 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--mode", default="s2", choices=["s2", "nsf"])
+    ap.add_argument("--mode", default="s2", choices=["s2", "s1", "nsf"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stream-events", type=int, default=None,
+                    help="simulate a shorter stream (profiling runs); default: the 200 M workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -184,7 +186,7 @@ def main():
     from paper_2510_20071_gb300 import Fibar
 
     need = (args.warmup + args.steps) * READ_EVERY
-    stream_events = max(STREAM_EVENTS, need)
+    stream_events = max(args.stream_events or STREAM_EVENTS, need + PACKET)
     t0 = time.time()
     import eventsim
     cfg = dict(eventsim.CONFIGS[CONFIG_NAME])
@@ -197,11 +199,14 @@ def main():
     params = dict(c_on=0.2, c_off=0.2)
     if args.mode == "s2":
         params.update(spatial_filter=1, blur_mode=1)
+    elif args.mode == "s1":
+        params.update(spatial_filter=1, blur_mode=0)
     else:
         params.update(spatial_filter=0)
     stream = torch.cuda.current_stream()
     f = Fibar(W, H, stream=stream, **params)
     plan, out, launches0 = run_device(args, ev, f, torch, stream)
+    det0 = f.stats()
     timed = plan[args.warmup:]
     n_timed = sum(min(hi, ev.shape[0]) - lo for pk, _ in timed for lo, hi in pk)
     applied0 = f.stats()["events_applied"]
@@ -228,6 +233,7 @@ def main():
     clocks = sampler.stop()
     st = f.stats()
     stages = f.stage_times(reset=True)
+    st0 = getattr(f, "_st0", None)
     applied = st["events_applied"] - applied0
     launches = st["kernel_launches"] - launches0
     f.set_timing(False)
@@ -273,7 +279,8 @@ def main():
         "data": "synthetic (seeded contrast-threshold simulator)",
         "config": {"workload": "1280x720 rotating+zooming Perlin, 2% noise events, C=0.2, seed 1, "
                                "65,536-event device packets, read-out every 1,000,000 events",
-                   "mode": "S2 masked-blur read-out" if args.mode == "s2" else "NSF (no spatial filter)",
+                   "mode": {"s2": "S2 masked-blur read-out", "s1": "S1 in-place blur (paper)",
+                            "nsf": "NSF (no spatial filter)"}[args.mode],
                    "stream_events": int(ev.shape[0]), "events_per_step": int(per_step_events),
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2: each step reads a fresh 16 MB slice of the 3.2 GB stream"},
@@ -286,6 +293,8 @@ def main():
         "stages_ms_per_step": {k: round(v / max(stages["calls"], 1), 5) for k, v in stage_ms.items()},
         "clocks": clocks,
         "gpu_launches": int(launches),
+        "detector": {k: st[k] - det0[k] for k in ["detector_fixups", "detector_unmerged",
+                                                   "detector_pass2_steps", "detector_fix_steps", "s1_blurs"]},
     }
 
     if not args.no_e2e:

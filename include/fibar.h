@@ -86,6 +86,10 @@ typedef struct {
     uint64_t n_ap, n_at;      /* active pixels / active 2x2 tiles (Eq. 19)               */
     uint64_t detector_fixups; /* batches whose speculative detector needed a serial fixup */
     uint64_t kernel_launches; /* CUDA kernels this handle has launched                    */
+    uint64_t detector_unmerged;    /* speculative chunks that did not merge (cumulative)  */
+    uint64_t detector_pass2_steps; /* events re-run by the merging pass (cumulative)       */
+    uint64_t detector_fix_steps;   /* events re-run serially by the fixup (cumulative)     */
+    uint64_t s1_blurs;             /* S1 in-place blurs applied (cumulative)               */
 } fibar_stats_t;
 
 /* Stages of one read-out, in launch order (fibar_stage_times). */

@@ -45,7 +45,9 @@ class FibarParams(C.Structure):
 class FibarStats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ["events_pushed", "events_applied", "events_dropped",
                                           "events_pending", "readouts", "q", "q_targ", "n_ap",
-                                          "n_at", "detector_fixups", "kernel_launches"]]
+                                          "n_at", "detector_fixups", "kernel_launches",
+                                          "detector_unmerged", "detector_pass2_steps",
+                                          "detector_fix_steps", "s1_blurs"]]
 
 
 class FibarStageTimes(C.Structure):

@@ -51,7 +51,7 @@ void free_all(fibar_t *h)
     Bufs &b = h->b;
     void *ptrs[] = {b.ctrl, b.pbar, b.L, b.last_pix, b.last_tile, b.staging, b.carry[0], b.carry[1],
                     b.dec_status, b.rec[0], b.rec[1], b.sort_hist, b.sort_base, b.sort_status, b.dpt,
-                    b.qout, b.ring_npt, b.ring_pix, b.dM, b.E0, b.E1, b.E2, b.merged,
+                    b.qout, b.ring_npt, b.ring_pix, b.dM, b.E0, b.E1, b.E2, b.merged, b.unm_bits,
                     b.out_staging, b.dbg_cnt, b.plist, b.plnb, b.epos, b.lbl, b.s1_info, b.s1_linit,
                     b.popk, b.blur_ord, b.bk, b.bpix, b.bj, b.bD, b.bflag, b.sel_status, b.beta_pow};
     for (void *p : ptrs)
@@ -134,7 +134,7 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     unsigned bits = 1;
     while ((1ull << bits) < kp.ntiles) ++bits;
     kp.key_bits = bits;
-    h->sort_passes = (bits + 7) / 8;
+    h->sort_passes = (bits + RADIX_BITS - 1) / RADIX_BITS;
     kp.spatial = p.spatial_filter;
     kp.blur_mode = p.blur_mode;
     // event ring: the batch plus everything a window (or a guessed window) can reach back
@@ -160,9 +160,9 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     ALLOC(b.dec_status, b.max_dec_tiles);
     ALLOC(b.rec[0], maxp);
     ALLOC(b.rec[1], maxp);
-    ALLOC(b.sort_hist, SORT_MAX_PASSES * 256);
-    ALLOC(b.sort_base, SORT_MAX_PASSES * 256);
-    ALLOC(b.sort_status, b.max_sort_tiles * 256);
+    ALLOC(b.sort_hist, SORT_MAX_PASSES * RADIX);
+    ALLOC(b.sort_base, SORT_MAX_PASSES * RADIX);
+    ALLOC(b.sort_status, b.max_sort_tiles * RADIX);
     ALLOC(b.out_staging, npix);
     if (p.spatial_filter) {
         ALLOC(b.dpt, maxp);
@@ -174,6 +174,7 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
         ALLOC(b.E1, b.max_chunks);
         ALLOC(b.E2, b.max_chunks);
         ALLOC(b.merged, b.max_chunks);
+        ALLOC(b.unm_bits, b.max_chunks / 32 + 2);
     }
     b.max_pops = maxp + npix + 8;
     b.max_sel_tiles = (b.max_pops + 4095) / 4096 + 1;
@@ -207,10 +208,11 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     if (e == cudaSuccess) e = cudaMemsetAsync(b.last_pix, 0xFF, npix * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.last_tile, 0xFF, kp.ntiles * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.dec_status, 0, b.max_dec_tiles * 8, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b.sort_hist, 0, SORT_MAX_PASSES * 256 * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b.sort_status, 0, b.max_sort_tiles * 256 * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.sort_hist, 0, SORT_MAX_PASSES * RADIX * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.sort_status, 0, b.max_sort_tiles * RADIX * 8, s);
     if (e == cudaSuccess && p.spatial_filter) e = cudaMemsetAsync(b.ring_npt, 0xFF, h->R * 8, s);
     if (e == cudaSuccess && p.spatial_filter) e = cudaMemsetAsync(b.ring_pix, 0, h->R * 4, s);
+    if (e == cudaSuccess && b.unm_bits) e = cudaMemsetAsync(b.unm_bits, 0, (b.max_chunks / 32 + 2) * 4, s);
     if (e == cudaSuccess && b.s1_info) e = cudaMemsetAsync(b.s1_info, 0, npix * sizeof(int4), s);
     if (e == cudaSuccess && b.bflag) e = cudaMemsetAsync(b.bflag, 0, b.max_pops * 4, s);
     if (e == cudaSuccess && b.sel_status) e = cudaMemsetAsync(b.sel_status, 0, b.max_sel_tiles * 8, s);
@@ -506,6 +508,10 @@ extern "C" int fibar_stats(fibar_t *h, fibar_stats_t *st, void *cuda_stream)
     }
     st->detector_fixups = c.fixups;
     st->kernel_launches = h->launches;
+    st->detector_unmerged = c.unmerged_total;
+    st->detector_pass2_steps = c.pass2_steps;
+    st->detector_fix_steps = c.fix_steps;
+    st->s1_blurs = c.s1_blurs;
     return rc;
 }
 

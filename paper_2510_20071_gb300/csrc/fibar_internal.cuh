@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/fibar.h"
@@ -31,9 +32,12 @@ constexpr int SORT_THREADS = 256;
 constexpr int SORT_PER_THREAD = 16;
 constexpr int SORT_TILE = SORT_THREADS * SORT_PER_THREAD;
 constexpr int SORT_MAX_PASSES = 4;
+constexpr int RADIX_BITS = 9;                  // sort digit width (max)
+constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int MAXSEG = 192;                    // pending device packets per read-out
 constexpr uint32_t CHUNK = 256;                // minimum detector chunk length (events)
 constexpr unsigned DET_G = 255;                // reach of the guessed windows, in chunks
+constexpr int LB_WIN = 8;                      // look-back window (predecessor tiles per load round)
 constexpr unsigned SPIN_LIMIT = 1u << 20;      // bounded device waits (~1 s)
 
 // error bits in Ctrl::error
@@ -73,6 +77,10 @@ struct Ctrl {
     unsigned int blur_ticket;    // S1: dataflow work counter
     unsigned int sel_ticket;     // S1: stale-list compaction tile counter
     unsigned int pad2_;
+    unsigned long long unmerged_total;  // diagnostics, cumulative
+    unsigned long long pass2_steps;
+    unsigned long long fix_steps;
+    unsigned long long s1_blurs;
 };
 
 // Constant per-handle parameters passed to kernels by value.
@@ -109,8 +117,8 @@ struct Bufs {
     int4 *carry[2];
     unsigned long long *dec_status;
     unsigned long long *rec[2];
-    unsigned int *sort_hist;     // [SORT_MAX_PASSES][256]
-    unsigned int *sort_base;     // [SORT_MAX_PASSES][256]
+    unsigned int *sort_hist;     // [SORT_MAX_PASSES][RADIX]
+    unsigned int *sort_base;     // [SORT_MAX_PASSES][RADIX]
     unsigned long long *sort_status;
     uint2 *dpt;
     unsigned int *qout;
@@ -120,6 +128,7 @@ struct Bufs {
     unsigned short *dM;          // [chunks + G][2][G + 1] suffix histograms
     DetState *E0, *E1, *E2;
     unsigned char *merged;
+    unsigned *unm_bits;          // [chunks / 32] chunks that did not merge in pass 2
     float *out_staging;
     unsigned int *dbg_cnt;
     // S1 (blur in place when a pixel goes stale)
@@ -173,6 +182,34 @@ struct fibar_s {
 };
 
 namespace fibar {
+// Programmatic dependent launch: every kernel of the pipeline is launched with
+// programmatic stream serialization and starts with PDL_ENTRY(), which lets the next
+// kernel's blocks become resident early and then waits until the previous grid has
+// completed and its memory is visible.  This hides most of the launch gap between the
+// dependent kernels of a read-out.
+#define PDL_ENTRY()                                              \
+    do {                                                         \
+        asm volatile("griddepcontrol.wait;" ::: "memory");       \
+        asm volatile("griddepcontrol.launch_dependents;" :::);   \
+    } while (0)
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 // launchers (kernels live in their own translation units); `nl` counts kernel launches
 cudaError_t launch_init(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
 cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, cudaStream_t s,

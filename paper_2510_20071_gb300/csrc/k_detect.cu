@@ -69,6 +69,7 @@ __device__ __forceinline__ long long chunk_of(long long x, unsigned S, unsigned 
 __global__ void __launch_bounds__(256)
 k_det_hist(KParams kp, Ctrl *ctrl, const uint2 *ring, unsigned short *M)
 {
+    PDL_ENTRY();
     __shared__ unsigned hist[8][2][DET_G + 1];
     const Geo g = geometry(kp, ctrl);
     const unsigned lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(256)
 k_det_init(KParams kp, const Ctrl *ctrl, const uint2 *dpt, const uint2 *ring,
            const unsigned short *M, unsigned *qout, DetState *E0)
 {
+    PDL_ENTRY();
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long base = ctrl->base;
     const unsigned m = ctrl->m, S = ctrl->S, nch = ctrl->nchunks, Gold = ctrl->Gold;
@@ -228,45 +230,82 @@ k_det_init(KParams kp, const Ctrl *ctrl, const uint2 *dpt, const uint2 *ring,
     }
 }
 
+// Run the detector over steps [k0, k1) from state st (h batch-relative) with one warp.
+// All lanes hold the same state.  Per step, lane j tests whether the (j+1)-th pop of
+// this step happens: the pop condition q > q_targ is monotone in q, so the ballot of
+// lanes 0..31 is a prefix whose population count is the number of pops (another round
+// if all 32 pop).  Lane j also holds the ring links of event h + j, so the deactivations
+// of the popped events are two more ballots.  The sequential streams dpt (read) and
+// qout (written, or compared in merge mode) move in coalesced blocks of 32 steps.
+// kMerge = false: write every step's queue length to qout.
+// kMerge = true : compare with qout; stop (return true) at the first equal step,
+//                 overwriting the differing entries before it.
 template <bool kMerge>
-__device__ __forceinline__ bool det_run(const KParams &kp, unsigned long long base,
-                                        const uint2 *__restrict__ dpt, const uint2 *__restrict__ ring,
-                                        unsigned *qout, unsigned k0, unsigned k1, DetState &st,
-                                        unsigned *err)
+__device__ __forceinline__ bool warp_run(const KParams &kp, unsigned long long base,
+                                         const uint2 *__restrict__ dpt, const uint2 *__restrict__ ring,
+                                         unsigned *qout, unsigned k0, unsigned k1, DetState &st,
+                                         unsigned *err, unsigned *nsteps = nullptr)
 {
+    const unsigned lane = threadIdx.x & 31;
     long long h = st.h;
     unsigned nap = st.nap, nat = st.nat;
-    unsigned long long X = st.X, Y = st.Y;
+    unsigned long long X = st.X;
+    unsigned long long Y = st.Y;
     bool merged = false;
-    for (unsigned k = k0; k < k1; ++k) {
-        // both streams are sequential: keep the L1 a few lines ahead of them
-        if ((k & 15u) == 0u && k + 32u < k1) asm volatile("prefetch.global.L1 [%0];" ::"l"(dpt + k + 32));
-        if ((((base + (unsigned long long)h) & 15ull) == 0ull))
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(ring + ((base + (unsigned long long)h + 32) & kp.ring_mask)));
-        const uint2 d = dpt[k];
-        const long long dist = (long long)k - h;
-        if (dist < 0) {  // impossible for a consistent state; never loop on a bad one
-            atomicOr(err, ERR_BAD_STATE);
-            break;
+    unsigned done = k1 - k0;
+    for (unsigned kb = k0; kb < k1; kb += 32) {
+        const unsigned nb = min(32u, k1 - kb);
+        const uint2 dblk = lane < nb ? dpt[kb + lane] : make_uint2(0u, 0u);
+        unsigned qold = 0;
+        if (kMerge) qold = lane < nb ? qout[kb + lane] : 0u;
+        unsigned qmine = 0;
+        unsigned i = 0;
+        bool bad = false;
+        for (; i < nb; ++i) {
+            const unsigned k = kb + i;
+            uint2 rn = ring[(base + (unsigned long long)(h + lane)) & kp.ring_mask];
+            const unsigned dx = __shfl_sync(0xFFFFFFFFu, dblk.x, i);
+            const unsigned dy = __shfl_sync(0xFFFFFFFFu, dblk.y, i);
+            const long long dist = (long long)k - h;
+            if (dist < 0) {  // impossible for a consistent state; never loop on a bad one
+                if (lane == 0) atomicOr(err, ERR_BAD_STATE);
+                bad = true;
+                break;
+            }
+            nap += (long long)dx > dist;
+            nat += (long long)dy > dist;
+            unsigned long long q = (unsigned long long)dist + 1;
+            for (;;) {
+                const unsigned long long v = q - lane;  // queue length before pop number lane+1
+                const bool pop = lane < q && v > kp.q_min && (v > kp.q_max || v * Y > X);
+                const unsigned c = __popc(__ballot_sync(0xFFFFFFFFu, pop));
+                const long long dj = (long long)k - (h + lane);
+                const bool offP = lane < c && (long long)rn.x > dj;
+                const bool offT = lane < c && (long long)rn.y > dj;
+                nap -= __popc(__ballot_sync(0xFFFFFFFFu, offP));
+                nat -= __popc(__ballot_sync(0xFFFFFFFFu, offT));
+                h += c;
+                q -= c;
+                if (c < 32) break;
+                rn = ring[(base + (unsigned long long)(h + lane)) & kp.ring_mask];
+            }
+            X = q * kp.numA * nat;
+            Y = (unsigned long long)kp.den * nap;
+            if (lane == i) qmine = (unsigned)q;
+            if (kMerge) {
+                const unsigned qo = __shfl_sync(0xFFFFFFFFu, qold, i);
+                if (qo == (unsigned)q) {
+                    merged = true;
+                    done = k + 1 - k0;
+                    break;
+                }
+            }
         }
-        nap += (long long)d.x > dist;
-        nat += (long long)d.y > dist;
-        unsigned long long q = (unsigned long long)dist + 1;
-        while (q > kp.q_min && (q > kp.q_max || q * Y > X)) {
-            const uint2 n = ring[(base + (unsigned long long)h) & kp.ring_mask];
-            const long long dd = (long long)k - h;
-            nap -= (long long)n.x > dd;
-            nat -= (long long)n.y > dd;
-            ++h;
-            --q;
-        }
-        X = q * kp.numA * nat;
-        Y = (unsigned long long)kp.den * nap;
-        if (kMerge) {
-            if (qout[k] == (unsigned)q) { merged = true; break; }
-        }
-        qout[k] = (unsigned)q;
+        // this block's queue lengths (in merge mode the equal one at i is not rewritten)
+        if (lane < i) qout[kb + lane] = qmine;
+        if (merged || bad) break;
     }
+    if (nsteps) *nsteps = done;
     st.h = h; st.nap = nap; st.nat = nat; st.X = X; st.Y = Y;
     return merged;
 }
@@ -275,9 +314,12 @@ __global__ void __launch_bounds__(128)
 k_det_pass1(KParams kp, Ctrl *ctrl, const uint2 *dpt, const uint2 *ring, unsigned *qout,
             const DetState *E0, DetState *E1)
 {
+    PDL_ENTRY();
     const unsigned long long base = ctrl->base;
     const unsigned m = ctrl->m, S = ctrl->S, nch = ctrl->nchunks;
-    for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += gridDim.x * blockDim.x) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned warps = gridDim.x * (blockDim.x >> 5);
+    for (unsigned c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nch; c += warps) {
         DetState st;
         unsigned k0 = c * S;
         if (c == 0) {
@@ -287,25 +329,34 @@ k_det_pass1(KParams kp, Ctrl *ctrl, const uint2 *dpt, const uint2 *ring, unsigne
             st = E0[c];
             k0 += 1;  // the chunk's first event was applied by k_det_init
         }
-        det_run<false>(kp, base, dpt, ring, qout, k0, min(m, (c + 1) * S), st, &ctrl->error);
-        E1[c] = st;
+        warp_run<false>(kp, base, dpt, ring, qout, k0, min(m, (c + 1) * S), st, &ctrl->error);
+        if (lane == 0) E1[c] = st;
     }
 }
 
 __global__ void __launch_bounds__(128)
 k_det_pass2(KParams kp, Ctrl *ctrl, const uint2 *dpt, const uint2 *ring, unsigned *qout,
-            const DetState *E1, DetState *E2, unsigned char *merged)
+            const DetState *E1, DetState *E2, unsigned char *merged, unsigned *unm_bits)
 {
+    PDL_ENTRY();
     const unsigned long long base = ctrl->base;
     const unsigned m = ctrl->m, S = ctrl->S, nch = ctrl->nchunks;
-    for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x + 1; c < nch; c += gridDim.x * blockDim.x) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned warps = gridDim.x * (blockDim.x >> 5);
+    for (unsigned c = 1 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nch; c += warps) {
         DetState st = E1[c - 1];
-        const bool mg = det_run<true>(kp, base, dpt, ring, qout, c * S, min(m, (c + 1) * S), st,
-                                      &ctrl->error);
-        merged[c] = mg;
-        if (!mg) {
-            E2[c] = st;
-            atomicAdd(&ctrl->unmerged, 1u);
+        unsigned steps = 0;
+        const bool mg = warp_run<true>(kp, base, dpt, ring, qout, c * S, min(m, (c + 1) * S), st,
+                                       &ctrl->error, &steps);
+        if (lane == 0) {
+            merged[c] = mg;
+            atomicAdd(&ctrl->pass2_steps, (unsigned long long)steps);
+            if (!mg) {
+                E2[c] = st;
+                atomicAdd(&ctrl->unmerged, 1u);
+                atomicAdd(&ctrl->unmerged_total, 1ull);
+                atomicOr(&unm_bits[c >> 5], 1u << (c & 31));
+            }
         }
     }
 }
@@ -315,65 +366,105 @@ __device__ __forceinline__ bool same_state(const DetState &a, const DetState &b)
     return a.h == b.h && a.nap == b.nap && a.nat == b.nat && a.X == b.X && a.Y == b.Y;
 }
 
+// Serial fixup, one warp.  Pass 2 ran chunk c from E1[c-1]; that run is exact when
+// E1[c-1] is the exact exit of chunk c-1.  Chunks that merged in pass 2 end on E1[c], so
+// exactness can only break right after a chunk that did not merge (its exact exit is
+// E2[c]).  The warp jumps from one unmerged chunk to the next with a bitmap, and re-runs
+// chunks only while the entry they were run from differs from the exact one.  The
+// bitmap is cleared on the way.
 __global__ void k_det_fix(KParams kp, Ctrl *ctrl, const uint2 *dpt, const uint2 *ring, unsigned *qout,
-                          const DetState *E1, const DetState *E2, const unsigned char *merged)
+                          const DetState *E1, const DetState *E2, const unsigned char *merged,
+                          unsigned *unm_bits)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    PDL_ENTRY();
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const unsigned lane = threadIdx.x;
     const unsigned long long base = ctrl->base;
     const unsigned m = ctrl->m, S = ctrl->S, nch = ctrl->nchunks;
     if (m == 0) {
-        ctrl->h_prev = ctrl->det.h;
+        if (lane == 0) ctrl->h_prev = ctrl->det.h;
         return;
     }
     DetState fin;
     if (ctrl->unmerged == 0) {
         fin = E1[nch - 1];
     } else {
-        ctrl->fixups += 1;
-        DetState exact = E1[0];
-        for (unsigned c = 1; c < nch; ++c) {
-            if (same_state(E1[c - 1], exact)) {
-                exact = merged[c] ? E1[c] : E2[c];
+        if (lane == 0) ctrl->fixups += 1;
+        const unsigned nwords = (nch + 31) / 32;
+        unsigned c = 1;  // chunks < c are exact and chunk c's pass-2 entry E1[c-1] is exact
+        DetState exit_c;
+        bool have_exit = false;  // exit of chunk c-1 if it differs from E1[c-1]
+        while (c < nch) {
+            if (!have_exit) {
+                // next unmerged chunk >= c
+                unsigned w = c >> 5, found = nch;
+                for (unsigned wb = w; wb < nwords && found == nch; wb += 32) {
+                    const unsigned wi = wb + lane;
+                    unsigned bits = wi < nwords ? unm_bits[wi] : 0u;
+                    if (wi == w) bits &= ~0u << (c & 31);
+                    const unsigned any = __ballot_sync(0xFFFFFFFFu, bits != 0u);
+                    if (any) {
+                        const unsigned src = __ffs(any) - 1;
+                        const unsigned b = __shfl_sync(0xFFFFFFFFu, bits, src);
+                        found = (wb + src) * 32 + __ffs(b) - 1;
+                    }
+                }
+                if (found >= nch) { c = nch; break; }
+                // chunk `found` has an exact entry and did not merge: its exact exit is E2
+                exit_c = E2[found];
+                c = found + 1;
+                have_exit = true;
                 continue;
             }
-            DetState st = exact;
-            const bool mg = det_run<true>(kp, base, dpt, ring, qout, c * S, min(m, (c + 1) * S), st,
-                                          &ctrl->error);
-            exact = mg ? (merged[c] ? E1[c] : E2[c]) : st;
+            // chunk c was run from E1[c-1]; the exact entry is exit_c
+            if (same_state(E1[c - 1], exit_c)) { have_exit = false; continue; }
+            DetState st = exit_c;
+            unsigned steps = 0;
+            const bool mg = warp_run<true>(kp, base, dpt, ring, qout, c * S, min(m, (c + 1) * S), st,
+                                           &ctrl->error, &steps);
+            if (lane == 0) ctrl->fix_steps += steps;
+            exit_c = mg ? (merged[c] ? E1[c] : E2[c]) : st;
+            ++c;
+            have_exit = true;
         }
-        fin = exact;
+        fin = have_exit ? exit_c : E1[nch - 1];
+        for (unsigned wi = lane; wi < nwords; wi += 32) unm_bits[wi] = 0u;
     }
-    fin.h = (long long)(base + (unsigned long long)fin.h);
-    ctrl->h_prev = ctrl->det.h;
-    ctrl->det = fin;
+    __syncwarp();
+    if (lane == 0) {
+        fin.h = (long long)(base + (unsigned long long)fin.h);
+        ctrl->h_prev = ctrl->det.h;
+        ctrl->det = fin;
+    }
 }
 
 cudaError_t launch_det_counts(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)
 {
     nl += 2;
-    k_det_hist<<<grid_for(4), 256, 0, s>>>(kp, b.ctrl, b.ring_npt, b.dM);
-    k_det_init<<<grid_for(4), 256, 0, s>>>(kp, b.ctrl, b.dpt, b.ring_npt, b.dM, b.qout, b.E0);
+    if (cudaError_t e_ = launch_pdl(k_det_hist, grid_for(4), 256, 0, s, kp, b.ctrl, b.ring_npt, b.dM)) return e_;
+    if (cudaError_t e_ = launch_pdl(k_det_init, grid_for(4), 256, 0, s, kp, b.ctrl, b.dpt, b.ring_npt, b.dM, b.qout, b.E0)) return e_;
     return cudaGetLastError();
 }
 
 cudaError_t launch_det_pass1(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)
 {
     nl += 1;
-    k_det_pass1<<<grid_for(1), 128, 0, s>>>(kp, b.ctrl, b.dpt, b.ring_npt, b.qout, b.E0, b.E1);
+    if (cudaError_t e_ = launch_pdl(k_det_pass1, grid_for(8), 128, 0, s, kp, b.ctrl, b.dpt, b.ring_npt, b.qout, b.E0, b.E1)) return e_;
     return cudaGetLastError();
 }
 
 cudaError_t launch_det_pass2(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)
 {
     nl += 1;
-    k_det_pass2<<<grid_for(1), 128, 0, s>>>(kp, b.ctrl, b.dpt, b.ring_npt, b.qout, b.E1, b.E2, b.merged);
+    if (cudaError_t e_ = launch_pdl(k_det_pass2, grid_for(8), 128, 0, s, kp, b.ctrl, b.dpt, b.ring_npt, b.qout, b.E1, b.E2, b.merged,
+                                           b.unm_bits)) return e_;
     return cudaGetLastError();
 }
 
 cudaError_t launch_det_fix(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)
 {
     nl += 1;
-    k_det_fix<<<1, 32, 0, s>>>(kp, b.ctrl, b.dpt, b.ring_npt, b.qout, b.E1, b.E2, b.merged);
+    if (cudaError_t e_ = launch_pdl(k_det_fix, 1, 32, 0, s, kp, b.ctrl, b.dpt, b.ring_npt, b.qout, b.E1, b.E2, b.merged, b.unm_bits)) return e_;
     return cudaGetLastError();
 }
 

@@ -10,7 +10,7 @@
 //             consecutive batch indices k and a 64-bit sort record
 //             (tile id << 32 | k << 3 | sub-pixel << 1 | OFF).  Records after the
 //             cut are copied to the other carry buffer.
-// k_sort_*  - stable LSD radix sort of the records by tile id, 8-bit digits
+// k_sort_*  - stable LSD radix sort of the records by tile id, digits of up to 9 bits
 //             (onesweep: one histogram kernel for all digits, then one kernel per
 //             digit with a per-digit decoupled look-back), so that every 2x2 tile's
 //             events end up contiguous and in arrival order.
@@ -22,6 +22,13 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 {
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -96,6 +103,7 @@ __device__ __forceinline__ int4 fetch_rec(const SegTable &T, const int4 *const *
 __global__ void __launch_bounds__(DEC_THREADS)
 k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigned long long *rec_out)
 {
+    PDL_ENTRY();
     __shared__ unsigned s_start[MAXSEG + 1];
     __shared__ const int4 *s_ptr[MAXSEG];
     __shared__ unsigned s_info[DEC_TILE];
@@ -175,22 +183,32 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
                 st_release(&status[0], dpack(2u, own));
             } else {
                 st_release(&status[tile], dpack(1u, own));
+                // windowed look-back: 8 predecessor statuses per round trip
                 DAgg acc{S_NONE, 0u};
-                bool empty = true;
+                bool empty = true, found = false;
                 int j = (int)tile - 1;
                 unsigned spins = 0;
-                for (;;) {
-                    const unsigned long long v = ld_acquire(&status[j]);
-                    const unsigned flag = (unsigned)(v >> 62);
-                    if (flag == 0u) {
-                        if (++spins > SPIN_LIMIT) { atomicOr(&ctrl->error, ERR_DEC_WAIT); break; }
-                        continue;
+                while (!found) {
+                    unsigned long long v[LB_WIN];
+#pragma unroll
+                    for (int q = 0; q < LB_WIN; ++q) v[q] = j - q >= 0 ? ld_relaxed(&status[j - q]) : 0ull;
+                    int used = 0;
+#pragma unroll
+                    for (int q = 0; q < LB_WIN; ++q) {
+                        if (found || used < q) break;
+                        const unsigned flag = (unsigned)(v[q] >> 62);
+                        if (flag == 0u) break;
+                        const DAgg a{(unsigned)(v[q] >> 31) & 0x7FFFFFFFu, (unsigned)v[q] & 0x7FFFFFFFu};
+                        acc = empty ? a : dcombine(a, acc);
+                        empty = false;
+                        ++used;
+                        if (flag == 2u || j - q == 0) found = true;
                     }
-                    const DAgg a{(unsigned)(v >> 31) & 0x7FFFFFFFu, (unsigned)v & 0x7FFFFFFFu};
-                    acc = empty ? a : dcombine(a, acc);
-                    empty = false;
-                    if (flag == 2u || j == 0) break;
-                    --j;
+                    j -= used;
+                    if (!found && used == 0 && ++spins > SPIN_LIMIT) {
+                        atomicOr(&ctrl->error, ERR_DEC_WAIT);
+                        break;
+                    }
                 }
                 pre = acc;
                 st_release(&status[tile], dpack(2u, dcombine(pre, own)));
@@ -242,24 +260,27 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
 // radix sort by tile id (stable)
 // ---------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-k_sort_hist(Ctrl *ctrl, const unsigned long long *rec, unsigned passes, unsigned *ghist,
+k_sort_hist(Ctrl *ctrl, const unsigned long long *rec, unsigned passes, unsigned dbits, unsigned *ghist,
             unsigned *gbase)
 {
-    __shared__ unsigned h[SORT_MAX_PASSES][256];
+    PDL_ENTRY();
+    __shared__ unsigned h[SORT_MAX_PASSES][RADIX];
     __shared__ unsigned s_warp[16];
     __shared__ bool s_last;
-    for (unsigned i = threadIdx.x; i < SORT_MAX_PASSES * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    for (unsigned i = threadIdx.x; i < SORT_MAX_PASSES * RADIX; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
     const unsigned m = ctrl->m;
+    const unsigned dmask = (1u << dbits) - 1u;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         const unsigned key = (unsigned)(rec[i] >> 32);
-        for (unsigned p = 0; p < passes; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 255u], 1u);
+        for (unsigned p = 0; p < passes; ++p) atomicAdd(&h[p][(key >> (dbits * p)) & dmask], 1u);
     }
     __syncthreads();
-    for (unsigned p = 0; p < passes; ++p) {
-        const unsigned v = h[p][threadIdx.x];
-        if (v) atomicAdd(&ghist[p * 256 + threadIdx.x], v);
-    }
+    for (unsigned p = 0; p < passes; ++p)
+        for (unsigned d = threadIdx.x; d < RADIX; d += 256) {
+            const unsigned v = h[p][d];
+            if (v) atomicAdd(&ghist[p * RADIX + d], v);
+        }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(&ctrl->hist_done, 1u) == gridDim.x - 1;
@@ -267,10 +288,14 @@ k_sort_hist(Ctrl *ctrl, const unsigned long long *rec, unsigned passes, unsigned
     if (!s_last) return;
     __threadfence();
     for (unsigned p = 0; p < passes; ++p) {
-        const unsigned v = atomicExch(&ghist[p * 256 + threadIdx.x], 0u);
+        // two digits per thread
+        const unsigned d0 = 2 * threadIdx.x;
+        const unsigned v0 = atomicExch(&ghist[p * RADIX + d0], 0u);
+        const unsigned v1 = atomicExch(&ghist[p * RADIX + d0 + 1], 0u);
         unsigned tot;
-        const unsigned ex = block_excl_scan256(v, s_warp, &tot);
-        gbase[p * 256 + threadIdx.x] = ex;
+        const unsigned ex = block_excl_scan256(v0 + v1, s_warp, &tot);
+        gbase[p * RADIX + d0] = ex;
+        gbase[p * RADIX + d0 + 1] = ex + v0;
     }
     if (threadIdx.x == 0) ctrl->hist_done = 0;
 }
@@ -284,22 +309,33 @@ __device__ __forceinline__ unsigned lookback_digit(unsigned long long *status, u
         st_release(&status[d], tag | (2ull << 30) | cnt);
         return 0;
     }
-    st_release(&status[(size_t)tile * 256 + d], tag | (1ull << 30) | cnt);
+    st_release(&status[(size_t)tile * RADIX + d], tag | (1ull << 30) | cnt);
+    // windowed look-back: 8 predecessor statuses per round trip
     unsigned acc = 0;
     int j = (int)tile - 1;
     unsigned spins = 0;
-    for (;;) {
-        const unsigned long long v = ld_acquire(&status[(size_t)j * 256 + d]);
-        const unsigned flag = (unsigned)(v >> 30) & 3u;
-        if ((unsigned)(v >> 32) != epoch || flag == 0u) {
-            if (++spins > SPIN_LIMIT) { atomicOr(&ctrl->error, ERR_SORT_WAIT); break; }
-            continue;
+    bool found = false;
+    while (!found) {
+        unsigned long long v[LB_WIN];
+#pragma unroll
+        for (int q = 0; q < LB_WIN; ++q) v[q] = j - q >= 0 ? ld_relaxed(&status[(size_t)(j - q) * RADIX + d]) : 0ull;
+        int used = 0;
+#pragma unroll
+        for (int q = 0; q < LB_WIN; ++q) {
+            if (found || used < q) break;
+            const unsigned flag = (unsigned)(v[q] >> 30) & 3u;
+            if ((unsigned)(v[q] >> 32) != epoch || flag == 0u) break;
+            acc += (unsigned)v[q] & 0x3FFFFFFFu;
+            ++used;
+            if (flag == 2u || j - q == 0) found = true;
         }
-        acc += (unsigned)v & 0x3FFFFFFFu;
-        if (flag == 2u || j == 0) break;
-        --j;
+        j -= used;
+        if (!found && used == 0 && ++spins > SPIN_LIMIT) {
+            atomicOr(&ctrl->error, ERR_SORT_WAIT);
+            break;
+        }
     }
-    st_release(&status[(size_t)tile * 256 + d], tag | (2ull << 30) | (acc + cnt));
+    st_release(&status[(size_t)tile * RADIX + d], tag | (2ull << 30) | (acc + cnt));
     return acc;
 }
 
@@ -308,28 +344,30 @@ struct SortSmem {
     unsigned long long key[SORT_TILE];
     unsigned long long out[SORT_TILE];
     unsigned short rank[SORT_TILE];
-    unsigned whist[8][256];
-    unsigned tdig[256];
-    unsigned gpos[256];
+    unsigned whist[8][RADIX];
+    unsigned tdig[RADIX];
+    unsigned gpos[RADIX];
     unsigned warp[16];
     unsigned tile;
 };
 
 __global__ void __launch_bounds__(SORT_THREADS)
 k_sort_pass(Ctrl *ctrl, const unsigned long long *in, unsigned long long *out, unsigned pass,
-            unsigned epoch, const unsigned *gbase, unsigned long long *status)
+            unsigned dbits, unsigned epoch, const unsigned *gbase, unsigned long long *status)
 {
+    PDL_ENTRY();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem &S = *reinterpret_cast<SortSmem *>(smem_raw);
     const unsigned m = ctrl->m;
     const unsigned ntiles = (m + SORT_TILE - 1) / SORT_TILE;
-    const unsigned shift = 32 + 8 * pass;
+    const unsigned shift = 32 + dbits * pass;
+    const unsigned dmask = (1u << dbits) - 1u;
     const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
 
     for (;;) {
         if (threadIdx.x == 0) S.tile = atomicAdd(&ctrl->sort_ticket[pass], 1u);
-        for (unsigned i = threadIdx.x; i < 8 * 256; i += SORT_THREADS) (&S.whist[0][0])[i] = 0;
+        for (unsigned i = threadIdx.x; i < 8 * RADIX; i += SORT_THREADS) (&S.whist[0][0])[i] = 0;
         __syncthreads();
         const unsigned tile = S.tile;
         if (tile >= ntiles) break;
@@ -345,7 +383,7 @@ k_sort_pass(Ctrl *ctrl, const unsigned long long *in, unsigned long long *out, u
         for (int q = 0; q < 16; ++q) {
             const unsigned r = w * 512 + q * 32 + lane;
             const bool valid = r < n_here;
-            const unsigned d = valid ? (unsigned)(S.key[r] >> shift) & 255u : 256u;
+            const unsigned d = valid ? (unsigned)(S.key[r] >> shift) & dmask : RADIX;
             const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
             const unsigned rank = __popc(peers & lt_mask);
             if (valid) S.rank[r] = (unsigned short)(S.whist[w][d] + rank);
@@ -354,20 +392,25 @@ k_sort_pass(Ctrl *ctrl, const unsigned long long *in, unsigned long long *out, u
             __syncwarp();
         }
         __syncthreads();
-        // per-digit exclusive offsets of each warp, and the tile's digit counts
-        const unsigned d = threadIdx.x;
-        unsigned run = 0;
+        // per-digit exclusive offsets of each warp, the tile's digit counts (2 digits per thread)
+        const unsigned d0 = 2 * threadIdx.x;
+        unsigned run0 = 0, run1 = 0;
 #pragma unroll
         for (int ww = 0; ww < 8; ++ww) {
-            const unsigned c = S.whist[ww][d];
-            S.whist[ww][d] = run;
-            run += c;
+            const unsigned c0 = S.whist[ww][d0], c1 = S.whist[ww][d0 + 1];
+            S.whist[ww][d0] = run0;
+            S.whist[ww][d0 + 1] = run1;
+            run0 += c0;
+            run1 += c1;
         }
         unsigned tot;
-        const unsigned tdig = block_excl_scan256(run, S.warp, &tot);
-        S.tdig[d] = tdig;
-        const unsigned prefix = lookback_digit(status, tile, d, epoch, run, ctrl);
-        S.gpos[d] = gbase[pass * 256 + d] + prefix;
+        const unsigned tdig = block_excl_scan256(run0 + run1, S.warp, &tot);
+        S.tdig[d0] = tdig;
+        S.tdig[d0 + 1] = tdig + run0;
+        const unsigned pre0 = lookback_digit(status, tile, d0, epoch, run0, ctrl);
+        const unsigned pre1 = lookback_digit(status, tile, d0 + 1, epoch, run1, ctrl);
+        S.gpos[d0] = gbase[pass * RADIX + d0] + pre0;
+        S.gpos[d0 + 1] = gbase[pass * RADIX + d0 + 1] + pre1;
         __syncthreads();
         // reorder the tile by digit in shared memory
 #pragma unroll 4
@@ -375,7 +418,7 @@ k_sort_pass(Ctrl *ctrl, const unsigned long long *in, unsigned long long *out, u
             const unsigned r = i * SORT_THREADS + threadIdx.x;
             if (r < n_here) {
                 const unsigned long long k = S.key[r];
-                const unsigned dd = (unsigned)(k >> shift) & 255u;
+                const unsigned dd = (unsigned)(k >> shift) & dmask;
                 const unsigned ww = r >> 9;
                 S.out[S.tdig[dd] + S.whist[ww][dd] + S.rank[r]] = k;
             }
@@ -386,7 +429,7 @@ k_sort_pass(Ctrl *ctrl, const unsigned long long *in, unsigned long long *out, u
             const unsigned lp = i * SORT_THREADS + threadIdx.x;
             if (lp < n_here) {
                 const unsigned long long k = S.out[lp];
-                const unsigned dd = (unsigned)(k >> shift) & 255u;
+                const unsigned dd = (unsigned)(k >> shift) & dmask;
                 out[S.gpos[dd] + (lp - S.tdig[dd])] = k;
             }
         }
@@ -411,7 +454,7 @@ cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, c
                           unsigned long long &nl)
 {
     nl += 1;
-    k_decode<<<grid_for(2), DEC_THREADS, 0, s>>>(kp, t, b.ctrl, b.dec_status, b.rec[0]);
+    if (cudaError_t e_ = launch_pdl(k_decode, grid_for(2), DEC_THREADS, 0, s, kp, t, b.ctrl, b.dec_status, b.rec[0])) return e_;
     return cudaGetLastError();
 }
 
@@ -419,7 +462,6 @@ cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsig
                         cudaStream_t s, unsigned long long &nl)
 {
     nl += 1 + passes;
-    (void)kp;
     static bool attr_set = false;
     const size_t smem = sizeof(SortSmem);
     if (!attr_set) {
@@ -428,10 +470,11 @@ cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsig
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_sort_hist<<<grid_for(2), 256, 0, s>>>(b.ctrl, b.rec[0], passes, b.sort_hist, b.sort_base);
+    const unsigned dbits = (kp.key_bits + passes - 1) / passes;
+    if (cudaError_t e_ = launch_pdl(k_sort_hist, grid_for(2), 256, 0, s, b.ctrl, b.rec[0], passes, dbits, b.sort_hist, b.sort_base)) return e_;
     for (unsigned p = 0; p < passes; ++p) {
-        k_sort_pass<<<grid_for(2), SORT_THREADS, smem, s>>>(b.ctrl, b.rec[p & 1], b.rec[(p + 1) & 1], p,
-                                                           epoch + p, b.sort_base, b.sort_status);
+        if (cudaError_t e_ = launch_pdl(k_sort_pass, grid_for(2), SORT_THREADS, smem, s, b.ctrl, b.rec[p & 1], b.rec[(p + 1) & 1], p,
+                                                           dbits, epoch + p, b.sort_base, b.sort_status)) return e_;
     }
     return cudaGetLastError();
 }

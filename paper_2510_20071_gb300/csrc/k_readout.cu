@@ -16,6 +16,7 @@ __global__ void __launch_bounds__(RB_X *RB_Y)
 k_readout_s2(KParams kp, const Ctrl *ctrl, const float *__restrict__ L,
              const unsigned long long *__restrict__ last_pix, float *__restrict__ out)
 {
+    PDL_ENTRY();
     __shared__ float t[RB_Y + 2][RB_X + 2];
     __shared__ float hs[RB_Y + 2][RB_X];
     const int x0 = blockIdx.x * RB_X, y0 = blockIdx.y * RB_Y;
@@ -50,6 +51,7 @@ k_readout_s2(KParams kp, const Ctrl *ctrl, const float *__restrict__ L,
 __global__ void k_copy(const float4 *__restrict__ in, float4 *__restrict__ out, size_t n4,
                        const float *__restrict__ in1, float *__restrict__ out1, size_t n)
 {
+    PDL_ENTRY();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
         out[i] = in[i];
     const size_t tail = n4 * 4;
@@ -59,6 +61,7 @@ __global__ void k_copy(const float4 *__restrict__ in, float4 *__restrict__ out, 
 // After the last kernel of a read-out: base += m, reset tickets and look-back status.
 __global__ void k_commit(Ctrl *ctrl, unsigned long long *dec_status, size_t n_status, int next_carry_slot)
 {
+    PDL_ENTRY();
     for (size_t i = threadIdx.x; i < n_status; i += blockDim.x) dec_status[i] = 0ull;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -69,6 +72,7 @@ __global__ void k_commit(Ctrl *ctrl, unsigned long long *dec_status, size_t n_st
         ctrl->unmerged = 0;
         ctrl->N0P = 0;
         ctrl->N0T = 0;
+        ctrl->s1_blurs += ctrl->nblur;
         ctrl->nblur = 0;
         ctrl->blur_ticket = 0;
         ctrl->sel_ticket = 0;
@@ -80,6 +84,7 @@ __global__ void k_commit(Ctrl *ctrl, unsigned long long *dec_status, size_t n_st
 
 __global__ void k_init(KParams kp, Ctrl *ctrl)
 {
+    PDL_ENTRY();
     if (threadIdx.x != 0) return;
     ctrl->base = 0;
     ctrl->dropped = 0;
@@ -94,6 +99,7 @@ __global__ void k_init(KParams kp, Ctrl *ctrl)
     ctrl->unmerged = 0;
     ctrl->fixups = 0;
     ctrl->N0P = ctrl->N0T = 0;
+    ctrl->unmerged_total = ctrl->pass2_steps = ctrl->fix_steps = ctrl->s1_blurs = 0;
     ctrl->batch_no = 1;
     ctrl->h_prev = 0;
     ctrl->nblur = 0;
@@ -109,6 +115,7 @@ __global__ void k_init(KParams kp, Ctrl *ctrl)
 // Debug: per-pixel count of queued events, cnt[pix(j)] += 1 for j in [h, base).
 __global__ void k_debug_counts(KParams kp, const Ctrl *ctrl, const unsigned *ring_pix, unsigned *cnt)
 {
+    PDL_ENTRY();
     const unsigned long long h = (unsigned long long)ctrl->det.h, k = ctrl->base;
     for (unsigned long long j = h + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < k;
          j += (unsigned long long)gridDim.x * blockDim.x)
@@ -118,7 +125,7 @@ __global__ void k_debug_counts(KParams kp, const Ctrl *ctrl, const unsigned *rin
 cudaError_t launch_init(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)
 {
     nl += 1;
-    k_init<<<1, 32, 0, s>>>(kp, b.ctrl);
+    if (cudaError_t e_ = launch_pdl(k_init, 1, 32, 0, s, kp, b.ctrl)) return e_;
     return cudaGetLastError();
 }
 
@@ -128,13 +135,13 @@ cudaError_t launch_readout(const KParams &kp, const Bufs &b, float *out, cudaStr
     nl += 1;
     if (kp.spatial && kp.blur_mode == 1) {
         dim3 grid((kp.W + RB_X - 1) / RB_X, (kp.H + RB_Y - 1) / RB_Y);
-        k_readout_s2<<<grid, RB_X * RB_Y, 0, s>>>(kp, b.ctrl, b.L, b.last_pix, out);
+        if (cudaError_t e_ = launch_pdl(k_readout_s2, grid, RB_X * RB_Y, 0, s, kp, b.ctrl, b.L, b.last_pix, out)) return e_;
     } else {
         const size_t n = kp.npix;
         const bool aligned = ((uintptr_t)out & 15) == 0;
         if (aligned) {
             const size_t n4 = n / 4;
-            k_copy<<<grid_for(4), 256, 0, s>>>((const float4 *)b.L, (float4 *)out, n4, b.L, out, n);
+            if (cudaError_t e_ = launch_pdl(k_copy, grid_for(4), 256, 0, s, (const float4 *)b.L, (float4 *)out, n4, b.L, out, n)) return e_;
         } else {
             nl -= 1;
             return cudaMemcpyAsync(out, b.L, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
@@ -148,7 +155,7 @@ cudaError_t launch_commit(const KParams &kp, const Bufs &b, int next_carry_slot,
 {
     nl += 1;
     (void)kp;
-    k_commit<<<1, 256, 0, s>>>(b.ctrl, b.dec_status, b.max_dec_tiles, next_carry_slot);
+    if (cudaError_t e_ = launch_pdl(k_commit, 1, 256, 0, s, b.ctrl, b.dec_status, b.max_dec_tiles, next_carry_slot)) return e_;
     return cudaGetLastError();
 }
 
@@ -156,7 +163,7 @@ cudaError_t launch_debug_counts(const KParams &kp, const Bufs &b, unsigned int *
                                 unsigned long long &nl)
 {
     nl += 1;
-    k_debug_counts<<<grid_for(2), 256, 0, s>>>(kp, b.ctrl, b.ring_pix, cnt);
+    if (cudaError_t e_ = launch_pdl(k_debug_counts, grid_for(2), 256, 0, s, kp, b.ctrl, b.ring_pix, cnt)) return e_;
     return cudaGetLastError();
 }
 

@@ -76,6 +76,7 @@ __device__ __forceinline__ S1Geo s1_geo(const Ctrl *ctrl)
 // pop step of every event popped in this batch, and whether its pixel went stale
 __global__ void __launch_bounds__(256) k_s1_pops(KParams kp, Bufs b)
 {
+    PDL_ENTRY();
     const S1Geo g = s1_geo(b.ctrl);
     const uint2 *ring = b.ring_npt;
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < g.m; k += gridDim.x * blockDim.x) {
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(256) k_s1_pops(KParams kp, Bufs b)
 // ordered compaction of the stale pops (decoupled look-back over tiles)
 __global__ void __launch_bounds__(SEL_THREADS) k_s1_select(KParams kp, Bufs b)
 {
+    PDL_ENTRY();
     __shared__ unsigned s_warp[16];
     __shared__ unsigned s_tile, s_pre;
     Ctrl *ctrl = b.ctrl;
@@ -142,16 +144,26 @@ __global__ void __launch_bounds__(SEL_THREADS) k_s1_select(KParams kp, Bufs b)
                 st_release_u64b(&st[tile], tag | (1ull << 30) | tile_cnt);
                 int j = (int)tile - 1;
                 unsigned spins = 0;
-                for (;;) {
-                    const unsigned long long v = ld_acquire_u64b(&st[j]);
-                    const unsigned flag = (unsigned)(v >> 30) & 3u;
-                    if ((v >> 32) != (tag >> 32) || flag == 0u) {
-                        if (++spins > SPIN_LIMIT) { atomicOr(&ctrl->error, ERR_SORT_WAIT); break; }
-                        continue;
+                bool found = false;
+                while (!found) {
+                    unsigned long long v[LB_WIN];
+#pragma unroll
+                    for (int q = 0; q < LB_WIN; ++q) v[q] = j - q >= 0 ? ld_acquire_u64b(&st[j - q]) : 0ull;
+                    int used = 0;
+#pragma unroll
+                    for (int q = 0; q < LB_WIN; ++q) {
+                        if (found || used < q) break;
+                        const unsigned flag = (unsigned)(v[q] >> 30) & 3u;
+                        if ((v[q] >> 32) != (tag >> 32) || flag == 0u) break;
+                        pre += (unsigned)v[q] & 0x3FFFFFFFu;
+                        ++used;
+                        if (flag == 2u || j - q == 0) found = true;
                     }
-                    pre += (unsigned)v & 0x3FFFFFFFu;
-                    if (flag == 2u || j == 0) break;
-                    --j;
+                    j -= used;
+                    if (!found && used == 0 && ++spins > SPIN_LIMIT) {
+                        atomicOr(&ctrl->error, ERR_SORT_WAIT);
+                        break;
+                    }
                 }
                 st_release_u64b(&st[tile], tag | (2ull << 30) | (pre + tile_cnt));
             }
@@ -189,6 +201,7 @@ __device__ __forceinline__ unsigned blur_of(const Bufs &b, const S1Geo &g, long 
 // per pixel list: latest blur attached to events at positions <= p
 __global__ void __launch_bounds__(256) k_s1_lb(KParams kp, Bufs b, const unsigned long long *srt)
 {
+    PDL_ENTRY();
     const S1Geo g = s1_geo(b.ctrl);
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < g.m; i += gridDim.x * blockDim.x) {
         const unsigned key = (unsigned)(srt[i] >> 32);
@@ -265,6 +278,7 @@ __device__ __forceinline__ Tap resolve(const KParams &kp, const Bufs &b, const S
 
 __global__ void __launch_bounds__(128) k_s1_blur(KParams kp, Bufs b)
 {
+    PDL_ENTRY();
     Ctrl *ctrl = b.ctrl;
     const S1Geo g = s1_geo(ctrl);
     const unsigned nb = ctrl->nblur;
@@ -330,6 +344,7 @@ __global__ void __launch_bounds__(128) k_s1_blur(KParams kp, Bufs b)
 // final L of the pixels a blur of this batch changed
 __global__ void __launch_bounds__(256) k_s1_apply(KParams kp, Bufs b, const unsigned long long *srt)
 {
+    PDL_ENTRY();
     const S1Geo g = s1_geo(b.ctrl);
     const unsigned nb = b.ctrl->nblur;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < g.m; i += gridDim.x * blockDim.x) {
@@ -361,13 +376,13 @@ __global__ void __launch_bounds__(256) k_s1_apply(KParams kp, Bufs b, const unsi
 
 cudaError_t launch_s1(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)
 {
-    const unsigned long long *srt = b.rec[(kp.key_bits + 7) / 8 & 1];
+    const unsigned long long *srt = b.rec[((kp.key_bits + RADIX_BITS - 1) / RADIX_BITS) & 1];
     nl += 5;
-    k_s1_pops<<<grid_for(4), 256, 0, s>>>(kp, b);
-    k_s1_select<<<grid_for(2), SEL_THREADS, 0, s>>>(kp, b);
-    k_s1_lb<<<grid_for(4), 256, 0, s>>>(kp, b, srt);
-    k_s1_blur<<<grid_for(4), 128, 0, s>>>(kp, b);
-    k_s1_apply<<<grid_for(4), 256, 0, s>>>(kp, b, srt);
+    if (cudaError_t e_ = launch_pdl(k_s1_pops, grid_for(4), 256, 0, s, kp, b)) return e_;
+    if (cudaError_t e_ = launch_pdl(k_s1_select, grid_for(2), SEL_THREADS, 0, s, kp, b)) return e_;
+    if (cudaError_t e_ = launch_pdl(k_s1_lb, grid_for(4), 256, 0, s, kp, b, srt)) return e_;
+    if (cudaError_t e_ = launch_pdl(k_s1_blur, grid_for(4), 128, 0, s, kp, b)) return e_;
+    if (cudaError_t e_ = launch_pdl(k_s1_apply, grid_for(4), 256, 0, s, kp, b, srt)) return e_;
     return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ template <bool kLinks, bool kS1>
 __global__ void __launch_bounds__(256)
 k_walk(KParams kp, Bufs b, const unsigned long long *srt)
 {
+    PDL_ENTRY();
     Ctrl *ctrl = b.ctrl;
     unsigned *ring_np = (unsigned *)b.ring_npt;
     const unsigned m = ctrl->m;
@@ -153,12 +154,14 @@ cudaError_t launch_walk(const KParams &kp, const Bufs &b, const unsigned long lo
                         cudaStream_t s, unsigned long long &nl)
 {
     nl += 1;
+    cudaError_t e;
     if (kp.spatial && kp.blur_mode == 0)
-        k_walk<true, true><<<grid_for(8), 256, 0, s>>>(kp, b, sorted);
+        e = launch_pdl(k_walk<true, true>, grid_for(8), 256, 0, s, kp, b, sorted);
     else if (kp.spatial)
-        k_walk<true, false><<<grid_for(8), 256, 0, s>>>(kp, b, sorted);
+        e = launch_pdl(k_walk<true, false>, grid_for(8), 256, 0, s, kp, b, sorted);
     else
-        k_walk<false, false><<<grid_for(8), 256, 0, s>>>(kp, b, sorted);
+        e = launch_pdl(k_walk<false, false>, grid_for(8), 256, 0, s, kp, b, sorted);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
