@@ -50,8 +50,8 @@ void free_all(fibar_t *h)
 {
     Bufs &b = h->b;
     void *ptrs[] = {b.ctrl, b.pbar, b.L, b.last_pix, b.last_tile, b.staging, b.carry[0], b.carry[1],
-                    b.dec_status, b.rec[0], b.rec[1], b.sort_hist, b.sort_base, b.sort_status, b.dpt,
-                    b.qout, b.ring_npt, b.ring_pix, b.dM, b.E0, b.E1, b.E2, b.merged, b.unm_bits,
+                    b.dec_status, b.rec[0], b.rec[1], b.sort_hist, b.sort_base, b.sort_rows, b.sort_rowflag, b.sort_gtot, b.sort_gflag, b.sort_gcount,
+                    b.qout, b.ring4, b.ring_pix, b.bucket_start, b.bucket_cnt, b.cA, b.cB, b.cE, b.cinit, b.E0, b.E1, b.E2, b.merged, b.unm_bits,
                     b.out_staging, b.dbg_cnt, b.plist, b.plnb, b.epos, b.lbl, b.s1_info, b.s1_linit,
                     b.popk, b.blur_ord, b.bk, b.bpix, b.bj, b.bD, b.bflag, b.sel_status, b.beta_pow};
     for (void *p : ptrs)
@@ -134,18 +134,23 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     unsigned bits = 1;
     while ((1ull << bits) < kp.ntiles) ++bits;
     kp.key_bits = bits;
-    h->sort_passes = (bits + RADIX_BITS - 1) / RADIX_BITS;
+    // buckets of 2^lb consecutive tiles: the radix sort orders by bucket only, the bucket
+    // walk sorts each bucket by the low lb bits in shared memory
+    kp.lb = std::min<unsigned>(9u, bits);
+    kp.nbuckets = (kp.ntiles + (1u << kp.lb) - 1) >> kp.lb;
+    h->sort_passes = (bits - kp.lb + RADIX_BITS - 1) / RADIX_BITS;
     kp.spatial = p.spatial_filter;
     kp.blur_mode = p.blur_mode;
     // event ring: the batch plus everything a window (or a guessed window) can reach back
-    h->R = next_pow2(maxp + npix + 8ull * CHUNK);
+    h->R = next_pow2(maxp + npix + 8ull * 256);
     kp.ring_mask = h->R - 1;
     kp.live = h->R - maxp;
 
     Bufs &b = h->b;
     b.max_dec_tiles = (maxp + DEC_TILE - 1) / DEC_TILE + 1;
     b.max_sort_tiles = (maxp + SORT_TILE - 1) / SORT_TILE + 1;
-    b.max_chunks = (maxp + CHUNK - 1) / CHUNK + 1;
+    b.max_chunks = std::min<unsigned long long>((maxp + CHUNK - 1) / CHUNK, DET_MAX_CHUNKS) + 1;
+    b.max_echunks = b.max_chunks + (npix + CHUNK - 1) / CHUNK + 2;
     cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, n)                                  \
     if (e == cudaSuccess) e = dalloc(&(ptr), (n));
@@ -162,14 +167,22 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     ALLOC(b.rec[1], maxp);
     ALLOC(b.sort_hist, SORT_MAX_PASSES * RADIX);
     ALLOC(b.sort_base, SORT_MAX_PASSES * RADIX);
-    ALLOC(b.sort_status, b.max_sort_tiles * RADIX);
+    ALLOC(b.sort_rows, b.max_sort_tiles * RADIX);
+    ALLOC(b.sort_rowflag, b.max_sort_tiles);
+    ALLOC(b.sort_gtot, (b.max_sort_tiles / LB_GROUP + 1) * RADIX);
+    ALLOC(b.sort_gflag, b.max_sort_tiles / LB_GROUP + 1);
+    ALLOC(b.sort_gcount, b.max_sort_tiles / LB_GROUP + 1);
     ALLOC(b.out_staging, npix);
+    ALLOC(b.bucket_start, kp.nbuckets);
+    ALLOC(b.bucket_cnt, kp.nbuckets);
     if (p.spatial_filter) {
-        ALLOC(b.dpt, maxp);
         ALLOC(b.qout, maxp);
-        ALLOC(b.ring_npt, h->R);
+        ALLOC(b.ring4, h->R);
         ALLOC(b.ring_pix, h->R);
-        ALLOC(b.dM, (b.max_chunks + DET_G + 1) * 2 * (DET_G + 1));
+        ALLOC(b.cA, 2 * b.max_chunks);
+        ALLOC(b.cB, 2 * NCAND * b.max_chunks);
+        ALLOC(b.cE, 2 * NCAND * b.max_echunks);
+        ALLOC(b.cinit, NCAND * b.max_chunks);
         ALLOC(b.E0, b.max_chunks);
         ALLOC(b.E1, b.max_chunks);
         ALLOC(b.E2, b.max_chunks);
@@ -209,8 +222,12 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     if (e == cudaSuccess) e = cudaMemsetAsync(b.last_tile, 0xFF, kp.ntiles * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.dec_status, 0, b.max_dec_tiles * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.sort_hist, 0, SORT_MAX_PASSES * RADIX * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b.sort_status, 0, b.max_sort_tiles * RADIX * 8, s);
-    if (e == cudaSuccess && p.spatial_filter) e = cudaMemsetAsync(b.ring_npt, 0xFF, h->R * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.sort_rowflag, 0, b.max_sort_tiles * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.sort_gflag, 0, (b.max_sort_tiles / LB_GROUP + 1) * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.sort_gcount, 0, (b.max_sort_tiles / LB_GROUP + 1) * 4, s);
+    if (e == cudaSuccess && p.spatial_filter) e = cudaMemsetAsync(b.ring4, 0xFF, h->R * 16, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.bucket_start, 0, (size_t)kp.nbuckets * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.bucket_cnt, 0, (size_t)kp.nbuckets * 4, s);
     if (e == cudaSuccess && p.spatial_filter) e = cudaMemsetAsync(b.ring_pix, 0, h->R * 4, s);
     if (e == cudaSuccess && b.unm_bits) e = cudaMemsetAsync(b.unm_bits, 0, (b.max_chunks / 32 + 2) * 4, s);
     if (e == cudaSuccess && b.s1_info) e = cudaMemsetAsync(b.s1_info, 0, npix * sizeof(int4), s);

@@ -5,12 +5,12 @@
 //                last applied event, ~0 = none)
 //   per tile   : last_tile u64 (2x2 tiles aligned at (0,0))
 //   event ring : for global event index g, slot g & ring_mask holds
-//                ring_npt = {nP, nT}: distance to the next event of the same pixel /
-//                tile (0xFFFFFFFF = none yet or >= 2^32-1), ring_pix = pixel id.
+//                ring4 = {dP, dT, nP, nT}: distance to the previous / next event of the
+//                same pixel and of the same tile (0xFFFFFFFF = none, or >= 2^32-1), and
+//                ring_pix = pixel id.
 //                The active event queue (Sec. 4.2) is always the index window [h, k].
-//   batch      : arrays indexed by the batch-relative event index k (0 .. m-1):
-//                dpt = {dP, dT}: distance to the previous event of the same pixel / tile
-//                qout = queue length after the pops of step k (window = [k+1-q, k]).
+//   batch      : qout[k] = queue length after the pops of step k (window [k+1-q, k]),
+//                k the batch-relative event index (0 .. m-1).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -34,10 +34,13 @@ constexpr int SORT_TILE = SORT_THREADS * SORT_PER_THREAD;
 constexpr int SORT_MAX_PASSES = 4;
 constexpr int RADIX_BITS = 9;                  // sort digit width (max)
 constexpr int RADIX = 1 << RADIX_BITS;
+constexpr int MAX_BUCKETS = 8192;              // buckets of <= 512 tiles (W*H <= 2^24)
 constexpr int MAXSEG = 192;                    // pending device packets per read-out
-constexpr uint32_t CHUNK = 256;                // minimum detector chunk length (events)
-constexpr unsigned DET_G = 255;                // reach of the guessed windows, in chunks
+constexpr uint32_t CHUNK = 64;                 // minimum detector chunk length (events)
+constexpr int NCAND = 8;                       // candidate window lengths of the detector's guesses
+constexpr unsigned DET_MAX_CHUNKS = 32768;     // chunks per batch at most (S grows beyond)
 constexpr int LB_WIN = 8;                      // look-back window (predecessor tiles per load round)
+constexpr int LB_GROUP = 32;                   // sort tiles per published group total
 constexpr unsigned SPIN_LIMIT = 1u << 20;      // bounded device waits (~1 s)
 
 // error bits in Ctrl::error
@@ -69,14 +72,14 @@ struct Ctrl {
     unsigned int unmerged;       // chunks whose second detector pass did not merge
     unsigned int fixups;         // batches that needed the serial detector fixup
     unsigned int S, nchunks, G, Gold;
-    unsigned int N0P, N0T;
+    unsigned int N0[NCAND][2];   // distinct pixels / tiles of the candidate windows of chunk 0
     unsigned int batch_no;       // read-outs/flushes committed (epoch of S1 flags)
     DetState det;                // detector state at the batch start (h global)
     long long h_prev;            // global h before the current batch (set by the fixup)
     unsigned int nblur;          // S1: stale pixels (blurs) in the current batch
     unsigned int blur_ticket;    // S1: dataflow work counter
     unsigned int sel_ticket;     // S1: stale-list compaction tile counter
-    unsigned int pad2_;
+    unsigned int walk_ticket;    // bucket walk work counter
     unsigned long long unmerged_total;  // diagnostics, cumulative
     unsigned long long pass2_steps;
     unsigned long long fix_steps;
@@ -95,7 +98,9 @@ struct KParams {
     unsigned long long ring_mask;
     unsigned long long live;     // ring slots that stay valid behind the batch start
     uint32_t max_pending;
-    uint32_t key_bits;           // bits of the tile id used as sort key
+    uint32_t key_bits;           // bits of the tile id
+    uint32_t lb;                 // low tile-id bits handled inside a bucket (<= 9)
+    uint32_t nbuckets;           // buckets of 2^lb consecutive tiles
     int spatial, blur_mode;
 };
 
@@ -119,13 +124,15 @@ struct Bufs {
     unsigned long long *rec[2];
     unsigned int *sort_hist;     // [SORT_MAX_PASSES][RADIX]
     unsigned int *sort_base;     // [SORT_MAX_PASSES][RADIX]
-    unsigned long long *sort_status;
-    uint2 *dpt;
+    unsigned *sort_rows, *sort_rowflag, *sort_gtot, *sort_gflag, *sort_gcount;
     unsigned int *qout;
-    uint2 *ring_npt;
+    uint4 *ring4;                // {dP, dT, nP, nT} per global event index (ring)
     unsigned int *ring_pix;
+    unsigned int *bucket_start;  // [nbuckets] first sorted position of each bucket
+    unsigned int *bucket_cnt;    // [nbuckets] scratch histogram
     // detector chunk data
-    unsigned short *dM;          // [chunks + G][2][G + 1] suffix histograms
+    unsigned *cA, *cB, *cE;      // detector per-chunk counts (see k_det_counts)
+    uint2 *cinit;                // [chunks][NCAND] distinct counts of the candidate windows
     DetState *E0, *E1, *E2;
     unsigned char *merged;
     unsigned *unm_bits;          // [chunks / 32] chunks that did not merge in pass 2
@@ -147,7 +154,7 @@ struct Bufs {
     unsigned long long *sel_status;
     float *beta_pow;             // [64] beta^m
     size_t max_pops, max_sel_tiles;
-    size_t max_chunks, max_dec_tiles, max_sort_tiles;
+    size_t max_chunks, max_echunks, max_dec_tiles, max_sort_tiles;
 };
 
 }  // namespace fibar

@@ -2,18 +2,20 @@
 //
 // k_decode  - one pass over the pending records (a carry buffer of records left
 //             pending by the previous read-out, then the pushed packets in order).
-//             Each record is read once with a 16-byte load.  A decoupled look-back
-//             over tiles of 4096 records carries (events kept, position of the first
-//             record whose time stamp is later than the read-out time): the applied
+//             Each record is read once with a 16-byte load.  Tiles of 4096 records
+//             publish (events kept, position of the first record whose time stamp is
+//             later than the read-out time); each tile reduces its predecessors' values
+//             in order to find its output offset and whether it lies past the cut: the applied
 //             set is the longest prefix with t <= t_read (Eq. 4's t_k <= t), minus
 //             out-of-range records, which are counted and skipped.  Kept events get
 //             consecutive batch indices k and a 64-bit sort record
 //             (tile id << 32 | k << 3 | sub-pixel << 1 | OFF).  Records after the
 //             cut are copied to the other carry buffer.
 // k_sort_*  - stable LSD radix sort of the records by tile id, digits of up to 9 bits
-//             (onesweep: one histogram kernel for all digits, then one kernel per
-//             digit with a per-digit decoupled look-back), so that every 2x2 tile's
-//             events end up contiguous and in arrival order.
+//             (one histogram kernel for all digits, then one kernel per digit whose tiles
+//             publish their digit counts; tile prefixes come from group totals of 32
+//             tiles plus the earlier tiles of the own group, with no look-back chains),
+//             so that every 2x2 tile's events end up contiguous and in arrival order.
 #include "fibar_internal.cuh"
 
 namespace fibar {
@@ -101,14 +103,17 @@ __device__ __forceinline__ int4 fetch_rec(const SegTable &T, const int4 *const *
 }
 
 __global__ void __launch_bounds__(DEC_THREADS)
-k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigned long long *rec_out)
+k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigned long long *rec_out,
+         unsigned *ring_pix)
 {
     PDL_ENTRY();
     __shared__ unsigned s_start[MAXSEG + 1];
     __shared__ const int4 *s_ptr[MAXSEG];
     __shared__ unsigned s_info[DEC_TILE];
+    __shared__ unsigned s_pix[DEC_TILE];
     __shared__ unsigned s_warp[16];
     __shared__ unsigned s_tile, s_vmin, s_pre_s, s_pre_c, s_drop;
+    __shared__ unsigned s_red_s[DEC_THREADS / 32], s_red_c[DEC_THREADS / 32];
 
     const unsigned carry_n = ctrl->carry_n[T.carry_slot];
     if (threadIdx.x == 0) {
@@ -153,6 +158,7 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
                 const unsigned tid_ = valid ? (y >> 1) * kp.tiles_w + (x >> 1) : 0u;
                 const unsigned sub = valid ? (((y & 1u) << 1) | (x & 1u)) : 0u;
                 info = (valid ? 0x80000000u : 0u) | (tid_ << 3) | (sub << 1) | (p > 0 ? 0u : 1u);
+                s_pix[r] = valid ? y * kp.W + x : 0u;
             }
             s_info[r] = info;
         }
@@ -175,57 +181,53 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
         const unsigned excl = block_excl_scan256(cnt, s_warp, &tile_cnt);
         if (drop) atomicAdd(&s_drop, drop);
 
-        // decoupled look-back over tiles
-        if (threadIdx.x == 0) {
-            const DAgg own{vfirst != S_NONE ? pos0 + vfirst : S_NONE, tile_cnt};
-            DAgg pre{S_NONE, 0u};
-            if (tile == 0) {
-                st_release(&status[0], dpack(2u, own));
-            } else {
-                st_release(&status[tile], dpack(1u, own));
-                // windowed look-back: 8 predecessor statuses per round trip
-                DAgg acc{S_NONE, 0u};
-                bool empty = true, found = false;
-                int j = (int)tile - 1;
+        // publish this tile's aggregate, then reduce all predecessors' aggregates in
+        // order (each thread a contiguous range, then an ordered tree): no chains
+        const DAgg own{vfirst != S_NONE ? pos0 + vfirst : S_NONE, tile_cnt};
+        if (threadIdx.x == 0) st_release(&status[tile], dpack(1u, own));
+        DAgg acc{S_NONE, 0u};
+        {
+            const unsigned per = (tile + DEC_THREADS - 1) / DEC_THREADS;
+            const unsigned t0 = threadIdx.x * per, t1 = min(tile, t0 + per);
+            for (unsigned tp = t0; tp < t1; ++tp) {
+                unsigned long long v = ld_relaxed(&status[tp]);
                 unsigned spins = 0;
-                while (!found) {
-                    unsigned long long v[LB_WIN];
-#pragma unroll
-                    for (int q = 0; q < LB_WIN; ++q) v[q] = j - q >= 0 ? ld_relaxed(&status[j - q]) : 0ull;
-                    int used = 0;
-#pragma unroll
-                    for (int q = 0; q < LB_WIN; ++q) {
-                        if (found || used < q) break;
-                        const unsigned flag = (unsigned)(v[q] >> 62);
-                        if (flag == 0u) break;
-                        const DAgg a{(unsigned)(v[q] >> 31) & 0x7FFFFFFFu, (unsigned)v[q] & 0x7FFFFFFFu};
-                        acc = empty ? a : dcombine(a, acc);
-                        empty = false;
-                        ++used;
-                        if (flag == 2u || j - q == 0) found = true;
-                    }
-                    j -= used;
-                    if (!found && used == 0 && ++spins > SPIN_LIMIT) {
-                        atomicOr(&ctrl->error, ERR_DEC_WAIT);
-                        break;
-                    }
+                while ((v >> 62) == 0ull) {
+                    if (++spins > SPIN_LIMIT) { atomicOr(&ctrl->error, ERR_DEC_WAIT); break; }
+                    v = ld_relaxed(&status[tp]);
                 }
-                pre = acc;
-                st_release(&status[tile], dpack(2u, dcombine(pre, own)));
+                acc = dcombine(acc, DAgg{(unsigned)(v >> 31) & 0x7FFFFFFFu, (unsigned)v & 0x7FFFFFFFu});
             }
-            s_pre_s = pre.s;
-            s_pre_c = pre.c;
-            if (tile == ntiles - 1) {
-                const DAgg inc = tile == 0 ? own : dcombine(pre, own);
-                const unsigned s = inc.s == S_NONE ? total : inc.s;
-                ctrl->m = inc.c;
-                ctrl->consumed = s;
-                ctrl->carry_n[1 - T.carry_slot] = total - s;
+        }
+        // ordered reduction across the block
+        {
+            const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned os = __shfl_down_sync(0xFFFFFFFFu, acc.s, o);
+                const unsigned oc = __shfl_down_sync(0xFFFFFFFFu, acc.c, o);
+                if (lane + o < 32 && (lane & (2 * o - 1)) == 0) acc = dcombine(acc, DAgg{os, oc});
+            }
+            if (lane == 0) { s_red_s[w] = acc.s; s_red_c[w] = acc.c; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                DAgg pre{S_NONE, 0u};
+                for (int i = 0; i < DEC_THREADS / 32; ++i) pre = dcombine(pre, DAgg{s_red_s[i], s_red_c[i]});
+                s_pre_s = pre.s;
+                s_pre_c = pre.c;
+                if (tile == ntiles - 1) {
+                    const DAgg inc = dcombine(pre, own);
+                    const unsigned s = inc.s == S_NONE ? total : inc.s;
+                    ctrl->m = inc.c;
+                    ctrl->consumed = s;
+                    ctrl->carry_n[1 - T.carry_slot] = total - s;
+                }
             }
         }
         __syncthreads();
         const unsigned pre_s = s_pre_s, pre_c = s_pre_c;
         if (pre_s == S_NONE) {
+            const unsigned long long base = ctrl->base;
             unsigned k = pre_c + excl;
 #pragma unroll
             for (int j = 0; j < DEC_PER_THREAD; ++j) {
@@ -233,6 +235,7 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
                     const unsigned info = s_info[threadIdx.x * DEC_PER_THREAD + j];
                     rec_out[k] = ((unsigned long long)((info >> 3) & 0x0FFFFFFFu) << 32) |
                                  ((unsigned long long)k << 3) | (info & 7u);
+                    if (ring_pix) ring_pix[(base + k) & kp.ring_mask] = s_pix[threadIdx.x * DEC_PER_THREAD + j];
                     ++k;
                 }
             }
@@ -260,20 +263,23 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
 // radix sort by tile id (stable)
 // ---------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-k_sort_hist(Ctrl *ctrl, const unsigned long long *rec, unsigned passes, unsigned dbits, unsigned *ghist,
-            unsigned *gbase)
+k_sort_hist(Ctrl *ctrl, const unsigned long long *rec, unsigned passes, unsigned dbits, unsigned lb,
+            unsigned nbuckets, unsigned *ghist, unsigned *gbase, unsigned *bcnt, unsigned *bucket_start)
 {
     PDL_ENTRY();
     __shared__ unsigned h[SORT_MAX_PASSES][RADIX];
+    __shared__ unsigned hb[MAX_BUCKETS];
     __shared__ unsigned s_warp[16];
     __shared__ bool s_last;
     for (unsigned i = threadIdx.x; i < SORT_MAX_PASSES * RADIX; i += blockDim.x) (&h[0][0])[i] = 0;
+    for (unsigned i = threadIdx.x; i < nbuckets; i += blockDim.x) hb[i] = 0;
     __syncthreads();
     const unsigned m = ctrl->m;
     const unsigned dmask = (1u << dbits) - 1u;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        const unsigned key = (unsigned)(rec[i] >> 32);
+        const unsigned key = (unsigned)(rec[i] >> 32) >> lb;
         for (unsigned p = 0; p < passes; ++p) atomicAdd(&h[p][(key >> (dbits * p)) & dmask], 1u);
+        atomicAdd(&hb[key], 1u);
     }
     __syncthreads();
     for (unsigned p = 0; p < passes; ++p)
@@ -281,6 +287,10 @@ k_sort_hist(Ctrl *ctrl, const unsigned long long *rec, unsigned passes, unsigned
             const unsigned v = h[p][d];
             if (v) atomicAdd(&ghist[p * RADIX + d], v);
         }
+    for (unsigned d = threadIdx.x; d < nbuckets; d += 256) {
+        const unsigned v = hb[d];
+        if (v) atomicAdd(&bcnt[d], v);
+    }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(&ctrl->hist_done, 1u) == gridDim.x - 1;
@@ -297,51 +307,48 @@ k_sort_hist(Ctrl *ctrl, const unsigned long long *rec, unsigned passes, unsigned
         gbase[p * RADIX + d0] = ex;
         gbase[p * RADIX + d0 + 1] = ex + v0;
     }
+    // bucket starts: each thread a contiguous run of buckets
+    {
+        const unsigned per = (nbuckets + 255) / 256;
+        const unsigned b0 = threadIdx.x * per, b1 = min(nbuckets, b0 + per);
+        unsigned sum = 0;
+        for (unsigned bb = b0; bb < b1; ++bb) sum += __ldcg(&bcnt[bb]);
+        unsigned tot;
+        unsigned run = block_excl_scan256(sum, s_warp, &tot);
+        for (unsigned bb = b0; bb < b1; ++bb) {
+            const unsigned v = atomicExch(&bcnt[bb], 0u);
+            bucket_start[bb] = run;
+            run += v;
+        }
+    }
     if (threadIdx.x == 0) ctrl->hist_done = 0;
 }
 
-__device__ __forceinline__ unsigned lookback_digit(unsigned long long *status, unsigned tile,
-                                                   unsigned d, unsigned epoch, unsigned cnt,
-                                                   Ctrl *ctrl)
+__device__ __forceinline__ unsigned ld_acq_u32(const unsigned *p)
 {
-    const unsigned long long tag = (unsigned long long)epoch << 32;
-    if (tile == 0) {
-        st_release(&status[d], tag | (2ull << 30) | cnt);
-        return 0;
-    }
-    st_release(&status[(size_t)tile * RADIX + d], tag | (1ull << 30) | cnt);
-    // windowed look-back: 8 predecessor statuses per round trip
-    unsigned acc = 0;
-    int j = (int)tile - 1;
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_rel_u32(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// wait (bounded) until *flag == epoch
+__device__ __forceinline__ void wait_flag(const unsigned *flag, unsigned epoch, Ctrl *ctrl)
+{
     unsigned spins = 0;
-    bool found = false;
-    while (!found) {
-        unsigned long long v[LB_WIN];
-#pragma unroll
-        for (int q = 0; q < LB_WIN; ++q) v[q] = j - q >= 0 ? ld_relaxed(&status[(size_t)(j - q) * RADIX + d]) : 0ull;
-        int used = 0;
-#pragma unroll
-        for (int q = 0; q < LB_WIN; ++q) {
-            if (found || used < q) break;
-            const unsigned flag = (unsigned)(v[q] >> 30) & 3u;
-            if ((unsigned)(v[q] >> 32) != epoch || flag == 0u) break;
-            acc += (unsigned)v[q] & 0x3FFFFFFFu;
-            ++used;
-            if (flag == 2u || j - q == 0) found = true;
-        }
-        j -= used;
-        if (!found && used == 0 && ++spins > SPIN_LIMIT) {
-            atomicOr(&ctrl->error, ERR_SORT_WAIT);
-            break;
-        }
+    while (ld_acq_u32(flag) != epoch) {
+        if (++spins > SPIN_LIMIT) { atomicOr(&ctrl->error, ERR_SORT_WAIT); return; }
     }
-    st_release(&status[(size_t)tile * RADIX + d], tag | (2ull << 30) | (acc + cnt));
-    return acc;
 }
 
 // dynamic shared memory layout of k_sort_pass
 struct SortSmem {
     unsigned long long key[SORT_TILE];
+    unsigned glast;
     unsigned long long out[SORT_TILE];
     unsigned short rank[SORT_TILE];
     unsigned whist[8][RADIX];
@@ -353,14 +360,15 @@ struct SortSmem {
 
 __global__ void __launch_bounds__(SORT_THREADS)
 k_sort_pass(Ctrl *ctrl, const unsigned long long *in, unsigned long long *out, unsigned pass,
-            unsigned dbits, unsigned epoch, const unsigned *gbase, unsigned long long *status)
+            unsigned dbits, unsigned lb, unsigned epoch, const unsigned *gbase, unsigned *rows, unsigned *rowflag,
+            unsigned *gtot, unsigned *gflag, unsigned *gcount)
 {
     PDL_ENTRY();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem &S = *reinterpret_cast<SortSmem *>(smem_raw);
     const unsigned m = ctrl->m;
     const unsigned ntiles = (m + SORT_TILE - 1) / SORT_TILE;
-    const unsigned shift = 32 + dbits * pass;
+    const unsigned shift = 32 + lb + dbits * pass;
     const unsigned dmask = (1u << dbits) - 1u;
     const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -407,8 +415,68 @@ k_sort_pass(Ctrl *ctrl, const unsigned long long *in, unsigned long long *out, u
         const unsigned tdig = block_excl_scan256(run0 + run1, S.warp, &tot);
         S.tdig[d0] = tdig;
         S.tdig[d0 + 1] = tdig + run0;
-        const unsigned pre0 = lookback_digit(status, tile, d0, epoch, run0, ctrl);
-        const unsigned pre1 = lookback_digit(status, tile, d0 + 1, epoch, run1, ctrl);
+        // tile prefix per digit: publish this tile's digit counts; the last tile of each
+        // group of LB_GROUP tiles to arrive publishes the group's totals; a tile adds the
+        // totals of earlier groups and the counts of earlier tiles of its own group
+        unsigned *row = rows + (size_t)tile * RADIX;
+        row[d0] = run0;
+        row[d0 + 1] = run1;
+        __syncthreads();
+        const unsigned g = tile / LB_GROUP;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_rel_u32(&rowflag[tile], epoch);
+            const unsigned gsize = min((unsigned)LB_GROUP, ntiles - g * LB_GROUP);
+            const unsigned old = atomicAdd(&gcount[g], 1u);
+            S.glast = old == gsize - 1;
+            if (S.glast) gcount[g] = 0;
+        }
+        __syncthreads();
+        if (S.glast) {
+            // every member has published (it counted itself in after publishing)
+            const unsigned gsize = min((unsigned)LB_GROUP, ntiles - g * LB_GROUP);
+            unsigned a0 = 0, a1 = 0;
+#pragma unroll 8
+            for (unsigned t = g * LB_GROUP; t < g * LB_GROUP + gsize; ++t) {
+                a0 += __ldcg(&rows[(size_t)t * RADIX + d0]);
+                a1 += __ldcg(&rows[(size_t)t * RADIX + d0 + 1]);
+            }
+            gtot[(size_t)g * RADIX + d0] = a0;
+            gtot[(size_t)g * RADIX + d0 + 1] = a1;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                st_rel_u32(&gflag[g], epoch);
+            }
+        }
+        // wait until the earlier groups' totals and the earlier tiles of this group are
+        // published: thread i watches one flag, the block polls them together
+        {
+            const unsigned nt = tile - g * LB_GROUP;  // earlier tiles of this group (< 32)
+            const unsigned *flag = nullptr;
+            if (threadIdx.x < nt) flag = &rowflag[g * LB_GROUP + threadIdx.x];
+            else if (threadIdx.x >= 32 && threadIdx.x - 32 < g) flag = &gflag[threadIdx.x - 32];
+            unsigned spins = 0;
+            bool ok = flag == nullptr || ld_acq_u32(flag) == epoch;
+            while (!__syncthreads_and(ok)) {
+                if (++spins > SPIN_LIMIT) {
+                    if (threadIdx.x == 0) atomicOr(&ctrl->error, ERR_SORT_WAIT);
+                    break;
+                }
+                if (!ok) ok = ld_acq_u32(flag) == epoch;
+            }
+        }
+        unsigned pre0 = 0, pre1 = 0;
+#pragma unroll 8
+        for (unsigned gg = 0; gg < g; ++gg) {
+            pre0 += __ldcg(&gtot[(size_t)gg * RADIX + d0]);
+            pre1 += __ldcg(&gtot[(size_t)gg * RADIX + d0 + 1]);
+        }
+#pragma unroll 8
+        for (unsigned t = g * LB_GROUP; t < tile; ++t) {
+            pre0 += __ldcg(&rows[(size_t)t * RADIX + d0]);
+            pre1 += __ldcg(&rows[(size_t)t * RADIX + d0 + 1]);
+        }
         S.gpos[d0] = gbase[pass * RADIX + d0] + pre0;
         S.gpos[d0 + 1] = gbase[pass * RADIX + d0 + 1] + pre1;
         __syncthreads();
@@ -454,14 +522,15 @@ cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, c
                           unsigned long long &nl)
 {
     nl += 1;
-    if (cudaError_t e_ = launch_pdl(k_decode, grid_for(2), DEC_THREADS, 0, s, kp, t, b.ctrl, b.dec_status, b.rec[0])) return e_;
+    if (cudaError_t e_ = launch_pdl(k_decode, grid_for(2), DEC_THREADS, 0, s, kp, t, b.ctrl, b.dec_status, b.rec[0],
+                                    kp.spatial ? b.ring_pix : nullptr)) return e_;
     return cudaGetLastError();
 }
 
 cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsigned epoch,
                         cudaStream_t s, unsigned long long &nl)
 {
-    nl += 1 + passes;
+    nl += 1 + passes;  // the histogram kernel also produces the bucket starts
     static bool attr_set = false;
     const size_t smem = sizeof(SortSmem);
     if (!attr_set) {
@@ -470,11 +539,16 @@ cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsig
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const unsigned dbits = (kp.key_bits + passes - 1) / passes;
-    if (cudaError_t e_ = launch_pdl(k_sort_hist, grid_for(2), 256, 0, s, b.ctrl, b.rec[0], passes, dbits, b.sort_hist, b.sort_base)) return e_;
+    const unsigned bucket_bits = kp.key_bits - kp.lb;
+    const unsigned dbits = passes ? (bucket_bits + passes - 1) / passes : 1u;
+    if (cudaError_t e_ = launch_pdl(k_sort_hist, grid_for(2), 256, 0, s, b.ctrl, b.rec[0], passes, dbits, kp.lb,
+                                    kp.nbuckets, b.sort_hist, b.sort_base, b.bucket_cnt, b.bucket_start))
+        return e_;
     for (unsigned p = 0; p < passes; ++p) {
-        if (cudaError_t e_ = launch_pdl(k_sort_pass, grid_for(2), SORT_THREADS, smem, s, b.ctrl, b.rec[p & 1], b.rec[(p + 1) & 1], p,
-                                                           dbits, epoch + p, b.sort_base, b.sort_status)) return e_;
+        if (cudaError_t e_ = launch_pdl(k_sort_pass, grid_for(2), SORT_THREADS, smem, s, b.ctrl, b.rec[p & 1],
+                                        b.rec[(p + 1) & 1], p, dbits, kp.lb, epoch + p, b.sort_base, b.sort_rows,
+                                        b.sort_rowflag, b.sort_gtot, b.sort_gflag, b.sort_gcount))
+            return e_;
     }
     return cudaGetLastError();
 }

@@ -78,12 +78,12 @@ __global__ void __launch_bounds__(256) k_s1_pops(KParams kp, Bufs b)
 {
     PDL_ENTRY();
     const S1Geo g = s1_geo(b.ctrl);
-    const uint2 *ring = b.ring_npt;
+    const unsigned *ring_u = reinterpret_cast<const unsigned *>(b.ring4);
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < g.m; k += gridDim.x * blockDim.x) {
         const long long h0 = k == 0 ? g.hs : (long long)k - (long long)b.qout[k - 1];
         const long long h1 = (long long)k + 1 - (long long)b.qout[k];
         for (long long j = h0; j < h1; ++j) {
-            const unsigned np = ring[(g.base + (unsigned long long)j) & kp.ring_mask].x;
+            const unsigned np = ring_u[4 * ((g.base + (unsigned long long)j) & kp.ring_mask) + 2];
             const bool stale = (long long)np > (long long)k - j;
             b.popk[j - g.hs] = k | (stale ? 0x80000000u : 0u);
         }
@@ -135,38 +135,26 @@ __global__ void __launch_bounds__(SEL_THREADS) k_s1_select(KParams kp, Bufs b)
         __syncthreads();
         const unsigned excl = (w ? s_warp[8 + w - 1] : 0u) + x - cnt;
         const unsigned tile_cnt = s_warp[15];
+        // publish this tile's count; sum all predecessors' counts (no look-back chain)
+        unsigned long long *st = b.sel_status;
+        if (threadIdx.x == 0) st_release_u64b(&st[tile], tag | (1ull << 30) | tile_cnt);
+        unsigned part = 0;
+        for (unsigned tp = threadIdx.x; tp < tile; tp += SEL_THREADS) {
+            unsigned long long v = ld_acquire_u64b(&st[tp]);
+            unsigned spins = 0;
+            while ((v >> 32) != (tag >> 32) || ((v >> 30) & 3ull) == 0ull) {
+                if (++spins > SPIN_LIMIT) { atomicOr(&ctrl->error, ERR_SORT_WAIT); break; }
+                v = ld_acquire_u64b(&st[tp]);
+            }
+            part += (unsigned)v & 0x3FFFFFFFu;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+        if (lane == 0) s_warp[w] = part;
+        __syncthreads();
         if (threadIdx.x == 0) {
             unsigned pre = 0;
-            unsigned long long *st = b.sel_status;
-            if (tile == 0) {
-                st_release_u64b(&st[0], tag | (2ull << 30) | tile_cnt);
-            } else {
-                st_release_u64b(&st[tile], tag | (1ull << 30) | tile_cnt);
-                int j = (int)tile - 1;
-                unsigned spins = 0;
-                bool found = false;
-                while (!found) {
-                    unsigned long long v[LB_WIN];
-#pragma unroll
-                    for (int q = 0; q < LB_WIN; ++q) v[q] = j - q >= 0 ? ld_acquire_u64b(&st[j - q]) : 0ull;
-                    int used = 0;
-#pragma unroll
-                    for (int q = 0; q < LB_WIN; ++q) {
-                        if (found || used < q) break;
-                        const unsigned flag = (unsigned)(v[q] >> 30) & 3u;
-                        if ((v[q] >> 32) != (tag >> 32) || flag == 0u) break;
-                        pre += (unsigned)v[q] & 0x3FFFFFFFu;
-                        ++used;
-                        if (flag == 2u || j - q == 0) found = true;
-                    }
-                    j -= used;
-                    if (!found && used == 0 && ++spins > SPIN_LIMIT) {
-                        atomicOr(&ctrl->error, ERR_SORT_WAIT);
-                        break;
-                    }
-                }
-                st_release_u64b(&st[tile], tag | (2ull << 30) | (pre + tile_cnt));
-            }
+            for (int i = 0; i < SEL_THREADS / 32; ++i) pre += s_warp[i];
             s_pre = pre;
             if (tile == ntiles - 1) ctrl->nblur = pre + tile_cnt;
         }
@@ -198,26 +186,22 @@ __device__ __forceinline__ unsigned blur_of(const Bufs &b, const S1Geo &g, long 
     return b.blur_ord[j - g.hs];
 }
 
-// per pixel list: latest blur attached to events at positions <= p
-__global__ void __launch_bounds__(256) k_s1_lb(KParams kp, Bufs b, const unsigned long long *srt)
+// per pixel list: latest blur attached to events at positions <= p.  Each pixel with
+// batch events owns the list plist[info.y .. info.y + info.z); a thread starting at the
+// list's first position walks it.
+__global__ void __launch_bounds__(256) k_s1_lb(KParams kp, Bufs b)
 {
     PDL_ENTRY();
     const S1Geo g = s1_geo(b.ctrl);
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < g.m; i += gridDim.x * blockDim.x) {
-        const unsigned key = (unsigned)(srt[i] >> 32);
-        if (i > 0 && (unsigned)(srt[i - 1] >> 32) == key) continue;
-        const unsigned tx = key % kp.tiles_w, ty = key / kp.tiles_w;
-        for (int s = 0; s < 4; ++s) {
-            const unsigned x = 2 * tx + (s & 1), y = 2 * ty + (s >> 1);
-            if (x >= kp.W || y >= kp.H) continue;
-            const int4 info = b.s1_info[y * kp.W + x];
-            if ((unsigned)info.x != g.batch_no) continue;
-            unsigned run = info.w > -0x40000000 ? blur_of(b, g, info.w) : NOBLUR;
-            for (int p = info.y; p < info.y + info.z; ++p) {
-                const unsigned bo = blur_of(b, g, (long long)b.plist[p]);
-                if (bo != NOBLUR) run = bo;
-                b.lbl[p] = run;
-            }
+    for (unsigned p = blockIdx.x * blockDim.x + threadIdx.x; p < g.m; p += gridDim.x * blockDim.x) {
+        const unsigned pix = b.ring_pix[(g.base + b.plist[p]) & kp.ring_mask];
+        const int4 info = b.s1_info[pix];
+        if ((unsigned)info.y != p) continue;
+        unsigned run = info.w > -0x40000000 ? blur_of(b, g, info.w) : NOBLUR;
+        for (int q = info.y; q < info.y + info.z; ++q) {
+            const unsigned bo = blur_of(b, g, (long long)b.plist[q]);
+            if (bo != NOBLUR) run = bo;
+            b.lbl[q] = run;
         }
     }
 }
@@ -342,28 +326,21 @@ __global__ void __launch_bounds__(128) k_s1_blur(KParams kp, Bufs b)
 }
 
 // final L of the pixels a blur of this batch changed
-__global__ void __launch_bounds__(256) k_s1_apply(KParams kp, Bufs b, const unsigned long long *srt)
+__global__ void __launch_bounds__(256) k_s1_apply(KParams kp, Bufs b)
 {
     PDL_ENTRY();
     const S1Geo g = s1_geo(b.ctrl);
     const unsigned nb = b.ctrl->nblur;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < g.m; i += gridDim.x * blockDim.x) {
-        const unsigned key = (unsigned)(srt[i] >> 32);
-        if (i > 0 && (unsigned)(srt[i - 1] >> 32) == key) continue;
-        const unsigned tx = key % kp.tiles_w, ty = key / kp.tiles_w;
-        for (int s = 0; s < 4; ++s) {
-            const unsigned x = 2 * tx + (s & 1), y = 2 * ty + (s >> 1);
-            if (x >= kp.W || y >= kp.H) continue;
-            const unsigned pix = y * kp.W + x;
-            const int4 info = b.s1_info[pix];
-            if ((unsigned)info.x != g.batch_no) continue;
-            const int last = info.y + info.z - 1;
-            const unsigned bl = b.lbl[last];
-            if (bl == NOBLUR) continue;
-            const int jb = b.bj[bl];
-            const int ord_b = jb >= 0 ? (int)b.epos[jb] : -1;
-            b.L[pix] = b.plnb[last] + beta_pow(kp, b.beta_pow, info.z - 1 - ord_b) * __ldcg(&b.bD[bl]);
-        }
+    for (unsigned p = blockIdx.x * blockDim.x + threadIdx.x; p < g.m; p += gridDim.x * blockDim.x) {
+        const unsigned pix = b.ring_pix[(g.base + b.plist[p]) & kp.ring_mask];
+        const int4 info = b.s1_info[pix];
+        if ((unsigned)info.y != p) continue;
+        const int last = info.y + info.z - 1;
+        const unsigned bl = b.lbl[last];
+        if (bl == NOBLUR) continue;
+        const int jb = b.bj[bl];
+        const int ord_b = jb >= 0 ? (int)b.epos[jb] : -1;
+        b.L[pix] = b.plnb[last] + beta_pow(kp, b.beta_pow, info.z - 1 - ord_b) * __ldcg(&b.bD[bl]);
     }
     // pixels without events in this batch whose previous event was popped (and blurred) now
     for (unsigned s = blockIdx.x * blockDim.x + threadIdx.x; s < nb; s += gridDim.x * blockDim.x) {
@@ -376,13 +353,12 @@ __global__ void __launch_bounds__(256) k_s1_apply(KParams kp, Bufs b, const unsi
 
 cudaError_t launch_s1(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)
 {
-    const unsigned long long *srt = b.rec[((kp.key_bits + RADIX_BITS - 1) / RADIX_BITS) & 1];
     nl += 5;
     if (cudaError_t e_ = launch_pdl(k_s1_pops, grid_for(4), 256, 0, s, kp, b)) return e_;
     if (cudaError_t e_ = launch_pdl(k_s1_select, grid_for(2), SEL_THREADS, 0, s, kp, b)) return e_;
-    if (cudaError_t e_ = launch_pdl(k_s1_lb, grid_for(4), 256, 0, s, kp, b, srt)) return e_;
+    if (cudaError_t e_ = launch_pdl(k_s1_lb, grid_for(4), 256, 0, s, kp, b)) return e_;
     if (cudaError_t e_ = launch_pdl(k_s1_blur, grid_for(4), 128, 0, s, kp, b)) return e_;
-    if (cudaError_t e_ = launch_pdl(k_s1_apply, grid_for(4), 256, 0, s, kp, b, srt)) return e_;
+    if (cudaError_t e_ = launch_pdl(k_s1_apply, grid_for(4), 256, 0, s, kp, b)) return e_;
     return cudaGetLastError();
 }
 
