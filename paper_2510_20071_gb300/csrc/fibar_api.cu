@@ -51,7 +51,7 @@ void free_all(fibar_t *h)
     Bufs &b = h->b;
     void *ptrs[] = {b.ctrl, b.pbar, b.L, b.last_pix, b.last_tile, b.staging, b.carry[0], b.carry[1],
                     b.dec_status, b.rec[0], b.rec[1], b.sort_hist, b.sort_base, b.sort_rows, b.sort_rowflag, b.sort_gtot, b.sort_gflag, b.sort_gcount,
-                    b.qout, b.ring4, b.ring_pix, b.bucket_start, b.bucket_cnt, b.cA, b.cB, b.cE, b.cinit, b.E0, b.E1, b.E2, b.merged, b.unm_bits,
+                    b.qout, b.ring4, b.ring_pix, b.bucket_start, b.bucket_cnt, b.dMt, b.E0, b.E1, b.E2, b.merged, b.unm_bits,
                     b.out_staging, b.dbg_cnt, b.plist, b.plnb, b.epos, b.lbl, b.s1_info, b.s1_linit,
                     b.popk, b.blur_ord, b.bk, b.bpix, b.bj, b.bD, b.bflag, b.sel_status, b.beta_pow};
     for (void *p : ptrs)
@@ -150,7 +150,7 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     b.max_dec_tiles = (maxp + DEC_TILE - 1) / DEC_TILE + 1;
     b.max_sort_tiles = (maxp + SORT_TILE - 1) / SORT_TILE + 1;
     b.max_chunks = std::min<unsigned long long>((maxp + CHUNK - 1) / CHUNK, DET_MAX_CHUNKS) + 1;
-    b.max_echunks = b.max_chunks + (npix + CHUNK - 1) / CHUNK + 2;
+    b.mt_stride = (b.max_chunks + DET_G + 1 + 31) / 32 * 32;
     cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, n)                                  \
     if (e == cudaSuccess) e = dalloc(&(ptr), (n));
@@ -179,10 +179,7 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
         ALLOC(b.qout, maxp);
         ALLOC(b.ring4, h->R);
         ALLOC(b.ring_pix, h->R);
-        ALLOC(b.cA, 2 * b.max_chunks);
-        ALLOC(b.cB, 2 * NCAND * b.max_chunks);
-        ALLOC(b.cE, 2 * NCAND * b.max_echunks);
-        ALLOC(b.cinit, NCAND * b.max_chunks);
+        ALLOC(b.dMt, 2 * (DET_G + 1) * b.mt_stride);
         ALLOC(b.E0, b.max_chunks);
         ALLOC(b.E1, b.max_chunks);
         ALLOC(b.E2, b.max_chunks);

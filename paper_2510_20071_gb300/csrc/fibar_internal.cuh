@@ -37,7 +37,8 @@ constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int MAX_BUCKETS = 8192;              // buckets of <= 512 tiles (W*H <= 2^24)
 constexpr int MAXSEG = 192;                    // pending device packets per read-out
 constexpr uint32_t CHUNK = 64;                 // minimum detector chunk length (events)
-constexpr int NCAND = 8;                       // candidate window lengths of the detector's guesses
+constexpr unsigned DET_G = 1023;               // reach of the guessed windows, in chunks
+constexpr unsigned DET_MARGIN = 2;             // extra chunks added to the equilibrium window
 constexpr unsigned DET_MAX_CHUNKS = 32768;     // chunks per batch at most (S grows beyond)
 constexpr int LB_WIN = 8;                      // look-back window (predecessor tiles per load round)
 constexpr int LB_GROUP = 32;                   // sort tiles per published group total
@@ -72,7 +73,6 @@ struct Ctrl {
     unsigned int unmerged;       // chunks whose second detector pass did not merge
     unsigned int fixups;         // batches that needed the serial detector fixup
     unsigned int S, nchunks, G, Gold;
-    unsigned int N0[NCAND][2];   // distinct pixels / tiles of the candidate windows of chunk 0
     unsigned int batch_no;       // read-outs/flushes committed (epoch of S1 flags)
     DetState det;                // detector state at the batch start (h global)
     long long h_prev;            // global h before the current batch (set by the fixup)
@@ -131,8 +131,8 @@ struct Bufs {
     unsigned int *bucket_start;  // [nbuckets] first sorted position of each bucket
     unsigned int *bucket_cnt;    // [nbuckets] scratch histogram
     // detector chunk data
-    unsigned *cA, *cB, *cE;      // detector per-chunk counts (see k_det_counts)
-    uint2 *cinit;                // [chunks][NCAND] distinct counts of the candidate windows
+    unsigned short *dMt;         // [2][DET_G + 1][mt_stride] transposed suffix histograms
+    size_t mt_stride;            // chunks (old + batch) per row of dMt
     DetState *E0, *E1, *E2;
     unsigned char *merged;
     unsigned *unm_bits;          // [chunks / 32] chunks that did not merge in pass 2
@@ -154,7 +154,7 @@ struct Bufs {
     unsigned long long *sel_status;
     float *beta_pow;             // [64] beta^m
     size_t max_pops, max_sel_tiles;
-    size_t max_chunks, max_echunks, max_dec_tiles, max_sort_tiles;
+    size_t max_chunks, max_dec_tiles, max_sort_tiles;
 };
 
 }  // namespace fibar

@@ -12,11 +12,11 @@
 //            (q > q_max or q * Y > X), which needs no division.
 //
 // Pass 1: chunk c starts from a guessed window slightly longer than the true one: the
-//         shortest of 8 candidate window lengths (ratio sqrt 2) that the regulator would
-//         shrink (k_det_counts, k_det_init); the exact distinct counts of the candidate
-//         windows of every chunk come from sliding-window recurrences over per-chunk
-//         counts.  A too-long window pops down to its target in the first steps and then
-//         coincides with the true trajectory.
+//         shortest chunk-aligned window that the regulator would shrink, plus a margin
+//         (k_det_hist, k_det_init); its exact distinct counts come from per-chunk suffix
+//         histograms.  A too-long window pops down to its target in the first steps and
+//         then coincides with the true trajectory; each chunk also warms up over the
+//         previous chunk.
 // Pass 2: chunk c restarts from pass 1's exit state of chunk c-1 and runs until its
 //         queue length equals pass 1's at the same step (the trajectories merged).
 // Fixup:  if some chunk did not merge, one thread walks the chunks in order and re-runs
@@ -28,38 +28,24 @@ namespace fibar {
 struct Geo {
     unsigned long long base;
     unsigned m, S, nchunks, Gold;
-    unsigned gtop;              // reach of the longest candidate window, in chunks
 };
 
-// Chunk length S (the batch is cut into at most DET_MAX_CHUNKS chunks of at least CHUNK
-// events) and the candidate window lengths: NCAND lengths in chunks, ratio sqrt(2),
-// the longest about 2.5x the queue length at the batch start (for a young stream, whose
-// queue is still growing, the whole sensor).
+// Chunk length S: at least CHUNK, at most DET_MAX_CHUNKS chunks per batch, and DET_G
+// chunks must cover twice the queue length at the batch start.
 __device__ __forceinline__ Geo geometry(const KParams &kp, const Ctrl *ctrl)
 {
     Geo g;
     g.base = ctrl->base;
     g.m = ctrl->m;
-    unsigned long long S = ((unsigned long long)g.m + DET_MAX_CHUNKS - 1) / DET_MAX_CHUNKS;
+    const unsigned long long qprev = g.base - (unsigned long long)ctrl->det.h;
+    unsigned long long S = (2ull * qprev + 4ull * CHUNK + DET_G - 1) / DET_G;
+    S = max(S, ((unsigned long long)g.m + DET_MAX_CHUNKS - 1) / DET_MAX_CHUNKS);
     S = (S + 15) / 16 * 16;
     g.S = (unsigned)max((unsigned long long)CHUNK, S);
     g.nchunks = (g.m + g.S - 1) / g.S;
-    const unsigned long long qprev = g.base - (unsigned long long)ctrl->det.h;
-    unsigned long long reach;
-    if (g.base < kp.q_max) reach = kp.q_max;
-    else reach = min((unsigned long long)kp.q_max, (5ull * qprev) / 2 + 4ull * g.S);
-    g.gtop = (unsigned)((reach + g.S - 1) / g.S) + 1;
     const unsigned long long old_chunks = (g.base + g.S - 1) / g.S;
-    g.Gold = (unsigned)min((unsigned long long)g.gtop, old_chunks);
+    g.Gold = (unsigned)min((unsigned long long)DET_G, old_chunks);
     return g;
-}
-
-// candidate i (0 = longest) in chunks
-__device__ __forceinline__ unsigned cand_g(unsigned gtop, int i)
-{
-    // gtop * 2^(-i/2), at least 1
-    const float f = exp2f(-0.5f * (float)i);
-    return max(1u, (unsigned)((float)gtop * f + 0.5f));
 }
 
 // the two halves of an event's ring record: {dP, dT} (previous) and {nP, nT} (next)
@@ -79,239 +65,193 @@ __device__ __forceinline__ unsigned warp_sum(unsigned v)
     return v;
 }
 
-// Exact distinct pixel / tile counts of the candidate windows W_i(c) = [(c-g_i)S, cS)
-// (clipped at the stream start) of every chunk c, by sliding-window recurrences:
-//   N_i(c+1) = N_i(c) + A(c) - B_i(c) - E_i(c - g_i)
-//   A(c)   = #{j in chunk c : next(j) >= (c+1)S}         (last of its pixel at the chunk end)
-//   B_i(c) = #{j in chunk c : prev(j) in W_i(c)}          (its predecessor stops being last)
-//   E_i(c) = #{j in chunk c : next(j) >= (c+g_i+1)S}      (last events leaving the window)
-//   N_i(0) = #{j in W_i(0) : next(j) >= 0}.
-// One warp per chunk (old chunks -Gold..-1 and the batch's chunks); the last block scans
-// the increments into init[c][i] = {N_ap, N_at}.
+// Chunk of a batch-relative index (indices below -Gold*S are never asked for).
+__device__ __forceinline__ long long chunk_of(long long x, unsigned S, unsigned Gold)
+{
+    return (x + (long long)Gold * S) / S - Gold;
+}
+
+// Suffix histograms, stored transposed: for chunk c' (old chunks -Gold..-1 and the
+// batch's chunks) and distance g = 1..DET_G,
+//   Mt[t][g][c' + Gold] = #{j in c' : next(j) >= (c'+g) S}      (t = 0 pixels, 1 tiles)
+// i.e. the events of c' still last of their pixel / tile at the start of chunk c'+g.
+// The distinct counts of the aligned window [(c-g)S, cS) are then
+// N(c, g) = sum_{g'=1..g} Mt[g'][c - g'], which lanes handling consecutive chunks read
+// with coalesced loads.  A block handles HB_CHUNKS consecutive chunks: each warp builds
+// one chunk's histogram in shared memory, the block writes the rows out per distance.
+constexpr int HB_CHUNKS = 32;
+
+struct HistSmem {
+    unsigned hist[8][DET_G + 1];
+    unsigned short tile[HB_CHUNKS][DET_G + 1];
+};
+
 __global__ void __launch_bounds__(256)
-k_det_counts(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *cA, unsigned *cB, unsigned *cE,
-             uint2 *init, size_t max_chunks)
+k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t mt_stride)
 {
     PDL_ENTRY();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    HistSmem &H = *reinterpret_cast<HistSmem *>(smem_raw);
     const Geo g = geometry(kp, ctrl);
-    const unsigned lane = threadIdx.x & 31;
+    const unsigned lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const unsigned nwork = g.nchunks + g.Gold;
-    const unsigned warps_total = gridDim.x * (blockDim.x >> 5);
+    const unsigned nblk = (nwork + HB_CHUNKS - 1) / HB_CHUNKS;
     const long long lo_exist = -(long long)g.base;
-    unsigned gc[NCAND];
-#pragma unroll
-    for (int i = 0; i < NCAND; ++i) gc[i] = cand_g(g.gtop, i);
-    for (unsigned wi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wi < nwork; wi += warps_total) {
-        const long long c = (long long)wi - (long long)g.Gold;
-        const long long lo = c * g.S;
-        unsigned aP = 0, aT = 0;
-        unsigned bP[NCAND], bT[NCAND], eP[NCAND], eT[NCAND];
-#pragma unroll
-        for (int i = 0; i < NCAND; ++i) bP[i] = bT[i] = eP[i] = eT[i] = 0;
-        for (unsigned r = lane; r < g.S; r += 32) {
-            const long long j = lo + r;
-            if (j < lo_exist || j >= (long long)g.m) continue;
-            const unsigned long long slot = (g.base + (unsigned long long)j) & kp.ring_mask;
-            const uint2 n = nxt_of(ring, slot);
-            const long long np = n.x == SAT ? 0x7FFFFFFFFFFFFFFFll : j + (long long)n.x;
-            const long long nt = n.y == SAT ? 0x7FFFFFFFFFFFFFFFll : j + (long long)n.y;
-            if (c < 0) {
-                // only E (old chunks leave the windows), and N_i(0) contributions
-#pragma unroll
-                for (int i = 0; i < NCAND; ++i) {
-                    const long long eth = (c + (long long)gc[i] + 1) * (long long)g.S;
-                    eP[i] += np >= eth;
-                    eT[i] += nt >= eth;
-                    const bool inw = j >= -(long long)gc[i] * g.S;
-                    bP[i] += inw && np >= 0;  // reused as N_i(0) partials for old chunks
-                    bT[i] += inw && nt >= 0;
+    for (unsigned blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+        for (int t = 0; t < 2; ++t) {  // pixels, then tiles
+            for (unsigned cc = wl; cc < HB_CHUNKS; cc += 8) {
+                const unsigned wi = blk * HB_CHUNKS + cc;
+                unsigned *hp = H.hist[wl];
+                for (unsigned i = lane; i <= DET_G; i += 32) hp[i] = 0;
+                __syncwarp();
+                if (wi < nwork) {
+                    const long long c = (long long)wi - (long long)g.Gold;
+                    const long long lo = c * g.S;
+                    for (unsigned r = lane; r < g.S; r += 32) {
+                        const long long j = lo + r;
+                        if (j < lo_exist || j >= (long long)g.m) continue;
+                        const uint2 n = nxt_of(ring, (g.base + (unsigned long long)j) & kp.ring_mask);
+                        const unsigned nv = t ? n.y : n.x;
+                        const long long d = nv == SAT ? DET_G : min((long long)DET_G, chunk_of(j + nv, g.S, g.Gold) - c);
+                        atomicAdd(&hp[d], 1u);
+                    }
                 }
-            } else {
-                const long long ath = (c + 1) * (long long)g.S;
-                aP += np >= ath;
-                aT += nt >= ath;
-                const uint2 d = prv_of(ring, slot);
-                const long long pp = d.x == SAT ? -0x7FFFFFFFFFFFFFFFll : j - (long long)d.x;
-                const long long pt = d.y == SAT ? -0x7FFFFFFFFFFFFFFFll : j - (long long)d.y;
+                __syncwarp();
+                // suffix sums over d; lane owns d in [lane*BPL, lane*BPL+BPL)
+                constexpr int BPL = (DET_G + 1) / 32;
+                unsigned sp = 0;
+#pragma unroll 8
+                for (int i = 0; i < BPL; ++i) sp += hp[lane * BPL + i];
+                unsigned xp = sp;
 #pragma unroll
-                for (int i = 0; i < NCAND; ++i) {
-                    const long long eth = (c + (long long)gc[i] + 1) * (long long)g.S;
-                    eP[i] += np >= eth;
-                    eT[i] += nt >= eth;
-                    const long long wlo = (c - (long long)gc[i]) * (long long)g.S;
-                    bP[i] += pp >= wlo && pp < lo;
-                    bT[i] += pt >= wlo && pt < lo;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned yp = __shfl_down_sync(0xFFFFFFFFu, xp, o);
+                    if (lane + o < 32) xp += yp;
                 }
+                unsigned rp = xp - sp;  // counts of d above this lane's range
+#pragma unroll 8
+                for (int i = BPL - 1; i >= 0; --i) {
+                    const unsigned d = lane * BPL + i;
+                    rp += hp[d];
+                    H.tile[cc][d] = (unsigned short)rp;
+                }
+                __syncwarp();
             }
-        }
-        aP = warp_sum(aP);
-        aT = warp_sum(aT);
-#pragma unroll
-        for (int i = 0; i < NCAND; ++i) {
-            bP[i] = warp_sum(bP[i]); bT[i] = warp_sum(bT[i]);
-            eP[i] = warp_sum(eP[i]); eT[i] = warp_sum(eT[i]);
-        }
-        if (lane == 0) {
-            const size_t ei = (size_t)(c + g.Gold);
-#pragma unroll
-            for (int i = 0; i < NCAND; ++i) {
-                cE[(ei * NCAND + i) * 2] = eP[i];
-                cE[(ei * NCAND + i) * 2 + 1] = eT[i];
+            __syncthreads();
+            // write out transposed: row g holds the chunks' values contiguously
+            unsigned short *base_t = Mt + (size_t)t * (DET_G + 1) * mt_stride;
+            const unsigned c_first = blk * HB_CHUNKS;
+            for (unsigned gg = wl + 1; gg <= DET_G; gg += 8) {
+                if (c_first + lane < nwork) base_t[(size_t)gg * mt_stride + c_first + lane] = H.tile[lane][gg];
             }
-            if (c >= 0) {
-                cA[c * 2] = aP;
-                cA[c * 2 + 1] = aT;
-#pragma unroll
-                for (int i = 0; i < NCAND; ++i) {
-                    cB[((size_t)c * NCAND + i) * 2] = bP[i];
-                    cB[((size_t)c * NCAND + i) * 2 + 1] = bT[i];
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < NCAND; ++i) {
-                    if (bP[i]) atomicAdd(&ctrl->N0[i][0], bP[i]);
-                    if (bT[i]) atomicAdd(&ctrl->N0[i][1], bT[i]);
-                }
-            }
+            __syncthreads();
         }
     }
-    __threadfence();
-    __syncthreads();
-    __shared__ bool s_last;
-    __shared__ int s_tot[2 * NCAND][256];
-    if (threadIdx.x == 0) s_last = atomicAdd(&ctrl->cnt_done, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // 2*NCAND scans over the chunks: each thread owns a contiguous range of chunks
-    const unsigned n = g.nchunks;
-    const unsigned per = (n + 255) / 256;
-    const unsigned c0 = threadIdx.x * per, c1 = min(n, c0 + per);
-    const long long eloc = -(long long)g.Gold;
-    int tot[2 * NCAND];
-#pragma unroll
-    for (int q = 0; q < 2 * NCAND; ++q) tot[q] = 0;
-    for (unsigned c = c0; c < c1; ++c) {
-        const int a0 = (int)__ldcg(&cA[c * 2]), a1 = (int)__ldcg(&cA[c * 2 + 1]);
-#pragma unroll
-        for (int i = 0; i < NCAND; ++i) {
-            const long long ce = (long long)c - gc[i];
-            int e0 = 0, e1 = 0;
-            if (ce >= eloc) {
-                const size_t ei = (size_t)(ce + g.Gold);
-                e0 = (int)__ldcg(&cE[(ei * NCAND + i) * 2]);
-                e1 = (int)__ldcg(&cE[(ei * NCAND + i) * 2 + 1]);
-            }
-            tot[2 * i] += a0 - (int)__ldcg(&cB[((size_t)c * NCAND + i) * 2]) - e0;
-            tot[2 * i + 1] += a1 - (int)__ldcg(&cB[((size_t)c * NCAND + i) * 2 + 1]) - e1;
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 2 * NCAND; ++q) s_tot[q][threadIdx.x] = tot[q];
-    __syncthreads();
-    if (threadIdx.x < 2 * NCAND) {  // serial scan over the 256 partial sums of one sequence
-        const int q = threadIdx.x;
-        int run = (int)atomicAdd(&ctrl->N0[q / 2][q & 1], 0u);
-        for (int i = 0; i < 256; ++i) {
-            const int v = s_tot[q][i];
-            s_tot[q][i] = run;
-            run += v;
-        }
-    }
-    __syncthreads();
-    int r[2 * NCAND];
-#pragma unroll
-    for (int q = 0; q < 2 * NCAND; ++q) r[q] = s_tot[q][threadIdx.x];
-    for (unsigned c = c0; c < c1; ++c) {
-        const int a0 = (int)__ldcg(&cA[c * 2]), a1 = (int)__ldcg(&cA[c * 2 + 1]);
-#pragma unroll
-        for (int i = 0; i < NCAND; ++i) {
-            init[(size_t)c * NCAND + i] = make_uint2((unsigned)r[2 * i], (unsigned)r[2 * i + 1]);
-            const long long ce = (long long)c - gc[i];
-            int e0 = 0, e1 = 0;
-            if (ce >= eloc) {
-                const size_t ei = (size_t)(ce + g.Gold);
-                e0 = (int)__ldcg(&cE[(ei * NCAND + i) * 2]);
-                e1 = (int)__ldcg(&cE[(ei * NCAND + i) * 2 + 1]);
-            }
-            r[2 * i] += a0 - (int)__ldcg(&cB[((size_t)c * NCAND + i) * 2]) - e0;
-            r[2 * i + 1] += a1 - (int)__ldcg(&cB[((size_t)c * NCAND + i) * 2 + 1]) - e1;
-        }
-    }
-    if (threadIdx.x == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctrl->S = g.S;
         ctrl->nchunks = g.nchunks;
-        ctrl->G = g.gtop;
+        ctrl->G = DET_G;
         ctrl->Gold = g.Gold;
-        ctrl->cnt_done = 0;
     }
 }
 
-// Speculative start of chunk c (c >= 1), one warp per chunk: among the candidate
-// windows ending just before the chunk, take the shortest one that the regulator would
-// shrink at the next event (its length is at or past the equilibrium of Eq. 20; the
-// next candidate is sqrt(2) shorter), i.e. a slight overestimate of the true queue, which
-// merges with the true trajectory within a few tens of events.  The warp then applies
-// the chunk's first event exactly, popping the excess in parallel.
+// Speculative start of chunk c (c >= 1).  Lanes handle 32 consecutive chunks and scan the
+// aligned windows g = 1..DET_G ending just before their chunk (coalesced rows of Mt),
+// keeping the shortest one that the regulator would shrink at the next event (its length
+// is at the equilibrium of Eq. 20, to within one chunk) plus DET_MARGIN chunks: a slight
+// overestimate of the true queue, which merges with the true trajectory within a few
+// tens of events.  Then, chunk by chunk, the warp applies the chunk's first event exactly,
+// popping the excess in parallel.
 __global__ void __launch_bounds__(256)
-k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const uint2 *init, unsigned *qout,
-           DetState *E0)
+k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short *Mt, size_t mt_stride,
+           unsigned *qout, DetState *E0)
 {
     PDL_ENTRY();
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long base = ctrl->base;
-    const unsigned S = ctrl->S, nch = ctrl->nchunks, gtop = ctrl->G;
+    const unsigned S = ctrl->S, nch = ctrl->nchunks, Gold = ctrl->Gold;
     const unsigned warps_total = gridDim.x * (blockDim.x >> 5);
-    for (unsigned c = 1 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nch; c += warps_total) {
-        const long long k0 = (long long)c * S;
-        // lane i < NCAND evaluates candidate i
-        bool shrink = false;
-        uint2 cnt = make_uint2(0u, 0u);
-        if (lane < NCAND) {
-            const long long hs = max(k0 - (long long)cand_g(gtop, lane) * S, -(long long)base);
+    const unsigned short *MP = Mt, *MT = Mt + (size_t)(DET_G + 1) * mt_stride;
+    for (unsigned cb = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; cb < nch; cb += warps_total * 32) {
+        const unsigned c = cb + lane;
+        const bool real = c >= 1 && c < nch;
+        const unsigned long long reach = (unsigned long long)c * S + base;  // events before the chunk
+        unsigned np = 0, nt = 0, gsel = 0, snp = 0, snt = 0, found = 0;
+        for (unsigned g0 = 1; g0 <= DET_G; g0 += 8) {
+            // the next 8 distances' counts, all loads in flight together
+            unsigned short vp[8], vt[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const unsigned gg = g0 + u;
+                const long long cw = (long long)c - gg;  // chunk entering the window
+                vp[u] = vt[u] = 0;
+                if (real && gg <= DET_G && cw >= -(long long)Gold) {
+                    const size_t col = (size_t)(cw + Gold);
+                    vp[u] = MP[(size_t)gg * mt_stride + col];
+                    vt[u] = MT[(size_t)gg * mt_stride + col];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const unsigned gg = g0 + u;
+                if (gg > DET_G) break;
+                np += vp[u];
+                nt += vt[u];
+                if (real && !found) {
+                    const unsigned long long L = min((unsigned long long)gg * S, reach);
+                    const unsigned long long X = L * kp.numA * nt, Y = (unsigned long long)kp.den * np;
+                    const unsigned long long q = L + 1;
+                    if (np > 0 && q > kp.q_min && (q > kp.q_max || q * Y > X)) found = gg;
+                }
+                if (real && gsel == 0 && (found ? gg == min(found + DET_MARGIN, (unsigned)DET_G) : gg == DET_G)) {
+                    gsel = gg;
+                    snp = np;
+                    snt = nt;
+                }
+            }
+            if (!__any_sync(0xFFFFFFFFu, real && gsel == 0)) break;  // every lane has its window
+        }
+        // chunk by chunk: the first event of the chunk, pops counted by the whole warp
+        const unsigned todo = __ballot_sync(0xFFFFFFFFu, real);
+        for (unsigned bits = todo; bits; bits &= bits - 1) {
+            const int src = __ffs(bits) - 1;
+            const unsigned cc = cb + src;
+            const unsigned gs = __shfl_sync(0xFFFFFFFFu, gsel, src);
+            const unsigned nap0 = __shfl_sync(0xFFFFFFFFu, snp, src);
+            const unsigned nat0 = __shfl_sync(0xFFFFFFFFu, snt, src);
+            const long long k0 = (long long)cc * S;
+            const long long hs = max(k0 - (long long)gs * S, -(long long)base);
             const unsigned long long L = (unsigned long long)(k0 - hs);
-            cnt = init[(size_t)c * NCAND + lane];
-            const unsigned long long X = L * kp.numA * cnt.y, Y = (unsigned long long)kp.den * cnt.x;
+            unsigned long long X = L * kp.numA * nat0, Y = (unsigned long long)kp.den * nap0;
+            if (nap0 == 0) { X = kp.q_min; Y = 1; }
+            const uint2 d = prv_of(ring, (base + (unsigned long long)k0) & kp.ring_mask);
+            const unsigned nap = nap0 + ((long long)d.x > (long long)L);
+            const unsigned nat = nat0 + ((long long)d.y > (long long)L);
             const unsigned long long q = L + 1;
-            shrink = cnt.x > 0 && q > kp.q_min && (q > kp.q_max || q * Y > X);
-        }
-        // candidates are longest first: the shortest shrinking one is the highest lane set
-        const unsigned sb = __ballot_sync(0xFFFFFFFFu, shrink);
-        const int sel = sb ? 31 - __clz(sb) : 0;
-        const unsigned nap0 = __shfl_sync(0xFFFFFFFFu, cnt.x, sel);
-        const unsigned nat0 = __shfl_sync(0xFFFFFFFFu, cnt.y, sel);
-        const long long hs = max(k0 - (long long)cand_g(gtop, sel) * S, -(long long)base);
-        const unsigned long long L = (unsigned long long)(k0 - hs);
-        unsigned long long X = L * kp.numA * nat0, Y = (unsigned long long)kp.den * nap0;
-        if (nap0 == 0) { X = kp.q_min; Y = 1; }
-        // step k0: push, then pop down to q_targ = clamp(floor(X / Y))
-        const uint2 d = prv_of(ring, (base + (unsigned long long)k0) & kp.ring_mask);
-        unsigned nap = nap0 + ((long long)d.x > (long long)L);
-        unsigned nat = nat0 + ((long long)d.y > (long long)L);
-        const unsigned long long q = L + 1;
-        unsigned long long qt = X / Y;
-        qt = min(qt, (unsigned long long)kp.q_max);
-        qt = max(qt, (unsigned long long)kp.q_min);
-        const unsigned long long npop = q > qt ? q - qt : 0ull;
-        unsigned dp = 0, dtt = 0;
-        for (unsigned long long i = lane; i < npop; i += 32) {
-            const long long j = hs + (long long)i;
-            const uint2 nn = nxt_of(ring, (base + (unsigned long long)j) & kp.ring_mask);
-            dp += (long long)nn.x > k0 - j;
-            dtt += (long long)nn.y > k0 - j;
-        }
-        dp = warp_sum(dp);
-        dtt = warp_sum(dtt);
-        if (lane == 0) {
-            DetState st0;
-            const unsigned long long qa = q - npop;
-            st0.h = hs + (long long)npop;
-            st0.nap = nap - dp;
-            st0.nat = nat - dtt;
-            st0.X = qa * kp.numA * st0.nat;
-            st0.Y = (unsigned long long)kp.den * st0.nap;
-            E0[c] = st0;
-            qout[k0] = (unsigned)qa;
+            unsigned long long qt = X / Y;
+            qt = min(qt, (unsigned long long)kp.q_max);
+            qt = max(qt, (unsigned long long)kp.q_min);
+            const unsigned long long npop = q > qt ? q - qt : 0ull;
+            unsigned dp = 0, dtt = 0;
+            for (unsigned long long i = lane; i < npop; i += 32) {
+                const long long j = hs + (long long)i;
+                const uint2 nn = nxt_of(ring, (base + (unsigned long long)j) & kp.ring_mask);
+                dp += (long long)nn.x > k0 - j;
+                dtt += (long long)nn.y > k0 - j;
+            }
+            dp = warp_sum(dp);
+            dtt = warp_sum(dtt);
+            if (lane == 0) {
+                DetState st0;
+                const unsigned long long qa = q - npop;
+                st0.h = hs + (long long)npop;
+                st0.nap = nap - dp;
+                st0.nat = nat - dtt;
+                st0.X = qa * kp.numA * st0.nat;
+                st0.Y = (unsigned long long)kp.den * st0.nap;
+                E0[cc] = st0;
+                qout[k0] = (unsigned)qa;
+            }
         }
     }
 }
@@ -332,7 +272,7 @@ template <int GW, bool kMerge>
 __device__ __forceinline__ bool group_run(const KParams &kp, unsigned long long base,
                                           const uint4 *__restrict__ ring,
                                           unsigned *qout, unsigned k0, unsigned k1, DetState &st,
-                                          unsigned *err, unsigned *nsteps = nullptr)
+                                          unsigned *err, unsigned *nsteps = nullptr, unsigned kw = 0)
 {
     static_assert(GW == 8 || GW == 16 || GW == 32, "group width");
     const unsigned lane = threadIdx.x & 31;
@@ -434,7 +374,7 @@ __device__ __forceinline__ bool group_run(const KParams &kp, unsigned long long 
             }
             if (bad) active = false;
         }
-        if (gl < nwrite) qout[kb + gl] = qmine;
+        if (gl < nwrite && kb + gl >= kw) qout[kb + gl] = qmine;
     }
     if (nsteps) *nsteps = done;
     st.h = h; st.nap = nap; st.nat = nat; st.X = X; st.Y = Y;
@@ -443,6 +383,10 @@ __device__ __forceinline__ bool group_run(const KParams &kp, unsigned long long 
 
 constexpr int DET_GW = 8;  // lanes per chunk in the parallel passes
 
+// Pass 1, groups of DET_GW lanes per chunk.  Chunk c >= 1 warms up over the previous
+// chunk: it starts from the speculative state of chunk c-1's first event (E0[c-1]) and
+// records the queue lengths of its own chunk only, so its trajectory has had a whole
+// chunk to merge with the true one by the time its own chunk starts.
 __global__ void __launch_bounds__(128)
 k_det_pass1(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *qout,
             const DetState *E0, DetState *E1)
@@ -456,19 +400,20 @@ k_det_pass1(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *qout,
     for (unsigned wb = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * CPW; wb < nch; wb += warps * CPW) {
         const unsigned c = wb + lane / DET_GW;
         DetState st{0, 0, 0, 0, 1};
-        unsigned k0 = 0, k1 = 0;
+        unsigned k0 = 0, k1 = 0, kw = 0;
         if (c < nch) {
-            k0 = c * S;
+            kw = c * S;
             k1 = min(m, (c + 1) * S);
-            if (c == 0) {
+            if (c <= 1) {  // from the true state at the batch start
                 st = ctrl->det;
                 st.h = (long long)((unsigned long long)st.h - base);
+                k0 = 0;
             } else {
-                st = E0[c];
-                k0 += 1;  // the chunk's first event was applied by k_det_init
+                st = E0[c - 1];
+                k0 = (c - 1) * S + 1;  // chunk c-1's first event was applied by k_det_init
             }
         }
-        group_run<DET_GW, false>(kp, base, ring, qout, k0, k1, st, &ctrl->error);
+        group_run<DET_GW, false>(kp, base, ring, qout, k0, k1, st, &ctrl->error, nullptr, kw);
         if (c < nch && lane % DET_GW == 0) E1[c] = st;
     }
 }
@@ -588,10 +533,17 @@ __global__ void k_det_fix(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *q
 cudaError_t launch_det_counts(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)
 {
     nl += 2;
-    if (cudaError_t e_ = launch_pdl(k_det_counts, grid_for(8), 256, 0, s, kp, b.ctrl, b.ring4, b.cA, b.cB, b.cE,
-                                    b.cinit, b.max_chunks))
+    static bool attr_set = false;
+    const size_t smem = sizeof(HistSmem);
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_det_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (cudaError_t e_ = launch_pdl(k_det_hist, grid_for(2), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_stride))
         return e_;
-    if (cudaError_t e_ = launch_pdl(k_det_init, grid_for(4), 256, 0, s, kp, b.ctrl, b.ring4, b.cinit, b.qout, b.E0))
+    if (cudaError_t e_ = launch_pdl(k_det_init, grid_for(2), 256, 0, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_stride,
+                                    b.qout, b.E0))
         return e_;
     return cudaGetLastError();
 }

@@ -140,15 +140,21 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
         if (tile >= ntiles) break;
         const unsigned pos0 = tile * DEC_TILE;
 
-        // coalesced 16-byte loads; classify each record
+        // coalesced 16-byte loads, all in flight before any is used; classify each record
+        int4 ev[DEC_PER_THREAD];
+#pragma unroll
+        for (int i = 0; i < DEC_PER_THREAD; ++i) {
+            const unsigned pos = pos0 + i * DEC_THREADS + threadIdx.x;
+            ev[i] = pos < total ? fetch_rec(T, s_ptr, s_start, carry_n, pos) : make_int4(0, 0, 0, 0);
+        }
         unsigned vloc = S_NONE;
-#pragma unroll 4
+#pragma unroll
         for (int i = 0; i < DEC_PER_THREAD; ++i) {
             const unsigned r = i * DEC_THREADS + threadIdx.x;
             const unsigned pos = pos0 + r;
             unsigned info = NOREC;
             if (pos < total) {
-                const int4 e = fetch_rec(T, s_ptr, s_start, carry_n, pos);
+                const int4 e = ev[i];
                 const unsigned x = (unsigned)e.x & 0xFFFFu, y = (unsigned)e.x >> 16;
                 const int p = (int)(signed char)(e.y & 0xFF);
                 const unsigned long long t =

@@ -70,7 +70,6 @@ __global__ void k_commit(Ctrl *ctrl, unsigned long long *dec_status, size_t n_st
         ctrl->dec_ticket = 0;
         for (int p = 0; p < SORT_MAX_PASSES; ++p) ctrl->sort_ticket[p] = 0;
         ctrl->unmerged = 0;
-        for (int i = 0; i < NCAND; ++i) ctrl->N0[i][0] = ctrl->N0[i][1] = 0;
         ctrl->s1_blurs += ctrl->nblur;
         ctrl->nblur = 0;
         ctrl->blur_ticket = 0;
@@ -98,7 +97,6 @@ __global__ void k_init(KParams kp, Ctrl *ctrl)
     ctrl->error = 0;
     ctrl->unmerged = 0;
     ctrl->fixups = 0;
-    for (int i = 0; i < NCAND; ++i) ctrl->N0[i][0] = ctrl->N0[i][1] = 0;
     ctrl->unmerged_total = ctrl->pass2_steps = ctrl->fix_steps = ctrl->s1_blurs = 0;
     ctrl->batch_no = 1;
     ctrl->h_prev = 0;
