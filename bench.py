@@ -50,21 +50,12 @@ def dist_env():
     return rank, world, local
 
 
-def step_plan(n_steps: int, first_step: int, t_col):
-    """Per step: list of (lo, hi) packets and the read-out time."""
-    plans = []
-    for s in range(first_step, first_step + n_steps):
-        lo = s * READ_EVERY
+def step_plan(n_steps: int, t_col):
+    """Per step: the (lo, hi) packets of the 65,536-event grid that end the step's
+    read-out interval, and the read-out time (the interval's last time stamp)."""
+    out, pushed = [], 0
+    for s in range(n_steps):
         hi = (s + 1) * READ_EVERY
-        # packets on the 65,536 grid of the stream
-        p0 = (lo // PACKET) * PACKET
-        pk = []
-        # the pushes needed to cover [pushed_so_far, hi): packets whose start is < hi
-        # and whose start is >= the first packet not yet pushed
-        plans.append((lo, hi))
-    out = []
-    pushed = (first_step * READ_EVERY + PACKET - 1) // PACKET * PACKET if first_step else 0
-    for lo, hi in plans:
         pk = []
         while pushed < hi:
             pk.append((pushed, min(pushed + PACKET, len(t_col))))
@@ -145,19 +136,11 @@ def make_stream(device, seed_offset=0):
     return eventsim.simulate(cfg.pop("W"), cfg.pop("H"), n, device=device, **cfg)
 
 
-def run_device(args, ev, f, torch, stream):
-    """Warm-up + timed steps with device packets and device images."""
-    t_col = ev[:, 1].cpu()
-    plan = step_plan(args.warmup + args.steps, 0, t_col)
-    out = torch.empty((H, W), dtype=torch.float32, device=ev.device)
-    for pk, t in plan[: args.warmup]:
+def run_steps(f, ev, steps, out):
+    for pk, t in steps:
         for lo, hi in pk:
             f.push(ev[lo:hi])
         f.readout(t, out)
-    f.stage_times(reset=True)
-    launches0 = f.stats()["kernel_launches"]
-    f.set_timing(True)
-    return plan, out, launches0
 
 
 def main():
@@ -185,7 +168,10 @@ def main():
         dist.init_process_group("nccl")
     from paper_2510_20071_gb300 import Fibar
 
-    need = (args.warmup + args.steps) * READ_EVERY
+    n_lat = min(args.steps, 50)     # read-out latency pass
+    n_stage = min(args.steps, 20)   # per-stage timing pass
+    n_total = args.warmup + args.steps + n_lat + n_stage
+    need = n_total * READ_EVERY
     stream_events = max(args.stream_events or STREAM_EVENTS, need + PACKET)
     t0 = time.time()
     import eventsim
@@ -205,12 +191,16 @@ def main():
         params.update(spatial_filter=0)
     stream = torch.cuda.current_stream()
     f = Fibar(W, H, stream=stream, **params)
-    plan, out, launches0 = run_device(args, ev, f, torch, stream)
+    plan = step_plan(n_total, ev[:, 1].cpu())
+    out = torch.empty((H, W), dtype=torch.float32, device=ev.device)
+    w0, w1 = args.warmup, args.warmup + args.steps
+    run_steps(f, ev, plan[:w0], out)
+    timed = plan[w0:w1]
     det0 = f.stats()
-    timed = plan[args.warmup:]
-    n_timed = sum(min(hi, ev.shape[0]) - lo for pk, _ in timed for lo, hi in pk)
-    applied0 = f.stats()["events_applied"]
+    launches0 = det0["kernel_launches"]
+    applied0 = det0["events_applied"]
 
+    # timed region: K steps, no instrumentation between the kernels
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.4)
@@ -220,10 +210,7 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for pk, t in timed:
-        for lo, hi in pk:
-            f.push(ev[lo:hi])
-        f.readout(t, out)
+    run_steps(f, ev, timed, out)
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -232,11 +219,30 @@ def main():
     time.sleep(0.3)
     clocks = sampler.stop()
     st = f.stats()
-    stages = f.stage_times(reset=True)
-    st0 = getattr(f, "_st0", None)
     applied = st["events_applied"] - applied0
     launches = st["kernel_launches"] - launches0
+
+    # read-out latency: one step per event pair (all of a step's work runs in its read-out)
+    lat = []
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_lat)]
+    for (a, b), step in zip(evs, plan[w1:w1 + n_lat]):
+        a.record(stream)
+        run_steps(f, ev, [step], out)
+        b.record(stream)
+    torch.cuda.synchronize()
+    lat = sorted(a.elapsed_time(b) for a, b in evs)
+
+    # per-stage CUDA-event times (events between the pipeline's kernels)
+    f.stage_times(reset=True)
+    f.set_timing(True)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    run_steps(f, ev, plan[w1 + n_lat:w1 + n_lat + n_stage], out)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    stages = f.stage_times(reset=True)
     f.set_timing(False)
+    stage_pass_ms = s0.elapsed_time(s1) / max(n_stage, 1)
 
     ms_all = torch.tensor([ms], device="cuda")
     ev_all = torch.tensor([float(applied)], device="cuda")
@@ -247,7 +253,7 @@ def main():
     total_events = float(ev_all.item())
     value = total_events / (ms_max / 1e3) / 1e6  # Mevents/s, whole job
 
-    # roofline of the dominant kernel stage, from its CUDA-event time in the timed region
+    # roofline of the dominant kernel stage, from its CUDA-event time in the stage pass
     peak, peak_kind = load_peaks()
     steps = len(timed)
     per_step_events = applied / steps
@@ -263,6 +269,9 @@ def main():
     dom_ms = stage_ms[dom] / max(stages["calls"], 1)
     achieved = bytes_per_launch / (dom_ms / 1e3) / 1e9
     whole_gbs = B_ev * total_events / (ms_max / 1e3) / 1e9
+
+    def pct(p):
+        return round(lat[min(len(lat) - 1, int(math.ceil(p / 100 * len(lat))) - 1)], 4) if lat else None
 
     result = {
         "metric": METRIC,
@@ -290,15 +299,19 @@ def main():
                      "whole_step_gbs": round(whole_gbs, 1),
                      "whole_step_frac": round(whole_gbs / peak, 4),
                      "alg_bytes_per_event": B_ev},
+        "readout_latency_ms": {"p50": pct(50), "p99": pct(99), "max": pct(100), "samples": len(lat),
+                               "what": "device time of one read-out (1 M pending events + image)"},
         "stages_ms_per_step": {k: round(v / max(stages["calls"], 1), 5) for k, v in stage_ms.items()},
+        "stage_pass_ms_per_step": round(stage_pass_ms, 5),
         "clocks": clocks,
         "gpu_launches": int(launches),
         "detector": {k: st[k] - det0[k] for k in ["detector_fixups", "detector_unmerged",
-                                                   "detector_pass2_steps", "detector_fix_steps", "s1_blurs"]},
+                                                   "detector_pass2_steps", "detector_fix_steps", "s1_blurs",
+                                                   "detector_big_pops", "detector_ring_misses"]},
     }
 
     if not args.no_e2e:
-        result["e2e"] = run_e2e(args, ev, plan, params, torch)
+        result["e2e"] = run_e2e(args, ev, plan[:w1], params, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = run_cpu_baseline(ev, params)
     f.close()

@@ -90,6 +90,8 @@ typedef struct {
     uint64_t detector_pass2_steps; /* events re-run by the merging pass (cumulative)       */
     uint64_t detector_fix_steps;   /* events re-run serially by the fixup (cumulative)     */
     uint64_t s1_blurs;             /* S1 in-place blurs applied (cumulative)               */
+    uint64_t detector_big_pops;    /* detector steps whose many pops a whole warp counted  */
+    uint64_t detector_ring_misses; /* popped-event links read past the staged ring         */
 } fibar_stats_t;
 
 /* Stages of one read-out, in launch order (fibar_stage_times). */

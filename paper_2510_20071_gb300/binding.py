@@ -47,7 +47,8 @@ class FibarStats(C.Structure):
                                           "events_pending", "readouts", "q", "q_targ", "n_ap",
                                           "n_at", "detector_fixups", "kernel_launches",
                                           "detector_unmerged", "detector_pass2_steps",
-                                          "detector_fix_steps", "s1_blurs"]]
+                                          "detector_fix_steps", "s1_blurs", "detector_big_pops",
+                                          "detector_ring_misses"]]
 
 
 class FibarStageTimes(C.Structure):

@@ -150,7 +150,7 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     b.max_dec_tiles = (maxp + DEC_TILE - 1) / DEC_TILE + 1;
     b.max_sort_tiles = (maxp + SORT_TILE - 1) / SORT_TILE + 1;
     b.max_chunks = std::min<unsigned long long>((maxp + CHUNK - 1) / CHUNK, DET_MAX_CHUNKS) + 1;
-    b.mt_stride = (b.max_chunks + DET_G + 1 + 31) / 32 * 32;
+    b.mt_rows = b.max_chunks;
     cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, n)                                  \
     if (e == cudaSuccess) e = dalloc(&(ptr), (n));
@@ -179,7 +179,7 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
         ALLOC(b.qout, maxp);
         ALLOC(b.ring4, h->R);
         ALLOC(b.ring_pix, h->R);
-        ALLOC(b.dMt, 2 * (DET_G + 1) * b.mt_stride);
+        ALLOC(b.dMt, 2 * b.mt_rows * (DET_G + 1));
         ALLOC(b.E0, b.max_chunks);
         ALLOC(b.E1, b.max_chunks);
         ALLOC(b.E2, b.max_chunks);
@@ -526,6 +526,8 @@ extern "C" int fibar_stats(fibar_t *h, fibar_stats_t *st, void *cuda_stream)
     st->detector_pass2_steps = c.pass2_steps;
     st->detector_fix_steps = c.fix_steps;
     st->s1_blurs = c.s1_blurs;
+    st->detector_big_pops = c.big_pops;
+    st->detector_ring_misses = c.ring_misses;
     return rc;
 }
 

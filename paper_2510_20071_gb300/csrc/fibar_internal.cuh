@@ -38,7 +38,6 @@ constexpr int MAX_BUCKETS = 8192;              // buckets of <= 512 tiles (W*H <
 constexpr int MAXSEG = 192;                    // pending device packets per read-out
 constexpr uint32_t CHUNK = 64;                 // minimum detector chunk length (events)
 constexpr unsigned DET_G = 1023;               // reach of the guessed windows, in chunks
-constexpr unsigned DET_MARGIN = 2;             // extra chunks added to the equilibrium window
 constexpr unsigned DET_MAX_CHUNKS = 32768;     // chunks per batch at most (S grows beyond)
 constexpr int LB_WIN = 8;                      // look-back window (predecessor tiles per load round)
 constexpr int LB_GROUP = 32;                   // sort tiles per published group total
@@ -84,6 +83,7 @@ struct Ctrl {
     unsigned long long pass2_steps;
     unsigned long long fix_steps;
     unsigned long long s1_blurs;
+    unsigned long long big_pops, ring_misses;
 };
 
 // Constant per-handle parameters passed to kernels by value.
@@ -131,8 +131,8 @@ struct Bufs {
     unsigned int *bucket_start;  // [nbuckets] first sorted position of each bucket
     unsigned int *bucket_cnt;    // [nbuckets] scratch histogram
     // detector chunk data
-    unsigned short *dMt;         // [2][DET_G + 1][mt_stride] transposed suffix histograms
-    size_t mt_stride;            // chunks (old + batch) per row of dMt
+    unsigned short *dMt;         // [2][mt_rows][DET_G + 1] suffix histograms by target chunk
+    size_t mt_rows;              // chunk rows per table of dMt
     DetState *E0, *E1, *E2;
     unsigned char *merged;
     unsigned *unm_bits;          // [chunks / 32] chunks that did not merge in pass 2

@@ -11,16 +11,19 @@
 //            kept as the ratio X / Y: "q > q_targ" is tested as q > q_min and
 //            (q > q_max or q * Y > X), which needs no division.
 //
-// Pass 1: chunk c starts from a guessed window slightly longer than the true one: the
-//         shortest chunk-aligned window that the regulator would shrink, plus a margin
-//         (k_det_hist, k_det_init); its exact distinct counts come from per-chunk suffix
-//         histograms.  A too-long window pops down to its target in the first steps and
-//         then coincides with the true trajectory; each chunk also warms up over the
-//         previous chunk.
+// Guess:  chunk c's window before its first step is guessed as the shortest window that
+//         the regulator would shrink (k_det_hist, k_det_init): first to the chunk, from
+//         per-chunk suffix histograms of the distance to each event's next occurrence,
+//         then to the event inside the chunk where it starts.  k_det_init applies step cS
+//         to it; the trajectory then coincides with the true one within a few tens of
+//         steps (most often fewer than 16).
+// Pass 1: each chunk runs from its guess, warming up over the previous chunk.
 // Pass 2: chunk c restarts from pass 1's exit state of chunk c-1 and runs until its
 //         queue length equals pass 1's at the same step (the trajectories merged).
-// Fixup:  if some chunk did not merge, one thread walks the chunks in order and re-runs
+// Fixup:  if some chunk did not merge, one warp walks the chunks in order and re-runs
 //         exactly those whose entry state was wrong.  The result is exact in all cases.
+// Passes 1 and 2 run one chunk per lane (lane_run); the fixup runs one chunk per warp
+// (group_run).
 #include "fibar_internal.cuh"
 
 namespace fibar {
@@ -71,81 +74,90 @@ __device__ __forceinline__ long long chunk_of(long long x, unsigned S, unsigned 
     return (x + (long long)Gold * S) / S - Gold;
 }
 
-// Suffix histograms, stored transposed: for chunk c' (old chunks -Gold..-1 and the
-// batch's chunks) and distance g = 1..DET_G,
-//   Mt[t][g][c' + Gold] = #{j in c' : next(j) >= (c'+g) S}      (t = 0 pixels, 1 tiles)
-// i.e. the events of c' still last of their pixel / tile at the start of chunk c'+g.
-// The distinct counts of the aligned window [(c-g)S, cS) are then
-// N(c, g) = sum_{g'=1..g} Mt[g'][c - g'], which lanes handling consecutive chunks read
-// with coalesced loads.  A block handles HB_CHUNKS consecutive chunks: each warp builds
-// one chunk's histogram in shared memory, the block writes the rows out per distance.
-constexpr int HB_CHUNKS = 32;
+// Suffix histograms by target chunk: for a batch chunk c and distance g = 1..DET_G,
+//   Mt[t][c][g] = #{j in chunk c-g : next(j) >= cS}          (t = 0 pixels, 1 tiles)
+// i.e. the events of chunk c-g still last of their pixel / tile at the start of chunk c
+// (source chunks reach back to -Gold; entries of older sources are never written and
+// never read).  The distinct counts of the aligned window [(c-g)S, cS) are the prefix
+// sums N(c, g) = sum_{g'=1..g} Mt[t][c][g'] along a contiguous row.
+// A block handles HB_CHUNKS consecutive source chunks and one t: the histogram of chunk
+// distances in shared memory (one word of padding per 32 bins and a row pitch of 2 mod
+// 32 words, so that a lane's run of 32 bins and the diagonal read-out both spread over
+// the banks), suffix sums in registers, then per target row a run of HB_CHUNKS
+// consecutive distances.
+constexpr int HB_CHUNKS = 16;
+constexpr int HB_PITCH = 1058;  // >= 1024 + 32 bins with padding, = 2 (mod 32)
+constexpr int MT_PITCH = DET_G + 1;  // u16 per target row (2 KB: 16-byte aligned rows)
+
+__device__ __forceinline__ int hb_slot(int d) { return d + (d >> 5); }
 
 struct HistSmem {
-    unsigned hist[8][DET_G + 1];
-    unsigned short tile[HB_CHUNKS][DET_G + 1];
+    unsigned h[HB_CHUNKS][HB_PITCH];
 };
 
 __global__ void __launch_bounds__(256)
-k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t mt_stride)
+k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t mt_rows)
 {
     PDL_ENTRY();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HistSmem &H = *reinterpret_cast<HistSmem *>(smem_raw);
     const Geo g = geometry(kp, ctrl);
-    const unsigned lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const unsigned tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
     const unsigned nwork = g.nchunks + g.Gold;
-    const unsigned nblk = (nwork + HB_CHUNKS - 1) / HB_CHUNKS;
+    const unsigned nunits = 2 * ((nwork + HB_CHUNKS - 1) / HB_CHUNKS);
     const long long lo_exist = -(long long)g.base;
-    for (unsigned blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-        for (int t = 0; t < 2; ++t) {  // pixels, then tiles
-            for (unsigned cc = wl; cc < HB_CHUNKS; cc += 8) {
-                const unsigned wi = blk * HB_CHUNKS + cc;
-                unsigned *hp = H.hist[wl];
-                for (unsigned i = lane; i <= DET_G; i += 32) hp[i] = 0;
-                __syncwarp();
-                if (wi < nwork) {
-                    const long long c = (long long)wi - (long long)g.Gold;
-                    const long long lo = c * g.S;
-                    for (unsigned r = lane; r < g.S; r += 32) {
-                        const long long j = lo + r;
-                        if (j < lo_exist || j >= (long long)g.m) continue;
-                        const uint2 n = nxt_of(ring, (g.base + (unsigned long long)j) & kp.ring_mask);
-                        const unsigned nv = t ? n.y : n.x;
-                        const long long d = nv == SAT ? DET_G : min((long long)DET_G, chunk_of(j + nv, g.S, g.Gold) - c);
-                        atomicAdd(&hp[d], 1u);
-                    }
-                }
-                __syncwarp();
-                // suffix sums over d; lane owns d in [lane*BPL, lane*BPL+BPL)
-                constexpr int BPL = (DET_G + 1) / 32;
-                unsigned sp = 0;
-#pragma unroll 8
-                for (int i = 0; i < BPL; ++i) sp += hp[lane * BPL + i];
-                unsigned xp = sp;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned yp = __shfl_down_sync(0xFFFFFFFFu, xp, o);
-                    if (lane + o < 32) xp += yp;
-                }
-                unsigned rp = xp - sp;  // counts of d above this lane's range
-#pragma unroll 8
-                for (int i = BPL - 1; i >= 0; --i) {
-                    const unsigned d = lane * BPL + i;
-                    rp += hp[d];
-                    H.tile[cc][d] = (unsigned short)rp;
-                }
-                __syncwarp();
-            }
-            __syncthreads();
-            // write out transposed: row g holds the chunks' values contiguously
-            unsigned short *base_t = Mt + (size_t)t * (DET_G + 1) * mt_stride;
-            const unsigned c_first = blk * HB_CHUNKS;
-            for (unsigned gg = wl + 1; gg <= DET_G; gg += 8) {
-                if (c_first + lane < nwork) base_t[(size_t)gg * mt_stride + c_first + lane] = H.tile[lane][gg];
-            }
-            __syncthreads();
+    for (unsigned unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+        const int t = unit & 1;
+        const long long c_lo = (long long)((unit >> 1) * HB_CHUNKS) - (long long)g.Gold;  // first source chunk
+        unsigned *hw = &H.h[0][0];
+        for (unsigned i = tid; i < HB_CHUNKS * HB_PITCH; i += 256) hw[i] = 0;
+        __syncthreads();
+        // histogram of the chunk distance to the next event of the same pixel / tile
+        const long long j_lo = c_lo * g.S;
+        const unsigned n_hi = (unsigned)min((long long)HB_CHUNKS * g.S, (long long)g.m - j_lo);
+        const unsigned n_lo = (unsigned)max(0ll, lo_exist - j_lo);
+        const unsigned long long lim = (unsigned long long)DET_G * g.S;  // offsets from here on: distance DET_G
+        for (unsigned i = n_lo + tid; i < n_hi; i += 256) {
+            const unsigned long long j = g.base + (unsigned long long)(j_lo + i);
+            const uint2 n = nxt_of(ring, j & kp.ring_mask);
+            const unsigned nv = t ? n.y : n.x;
+            const unsigned cc = i / g.S, r = i - cc * g.S;
+            const unsigned long long rel = (unsigned long long)r + nv;  // from the start of chunk cc
+            const unsigned d = (nv == SAT || rel >= lim) ? (unsigned)DET_G
+                             : (lim <= 0xFFFFFFFFull ? (unsigned)rel / g.S : (unsigned)(rel / g.S));
+            atomicAdd(&H.h[cc][hb_slot((int)d)], 1u);
         }
+        __syncthreads();
+        // suffix sums over d: warp per chunk, lane l owns bins 32l .. 32l+31
+        for (unsigned cc = wl; cc < HB_CHUNKS; cc += 8) {
+            unsigned *row = &H.h[cc][33 * lane];
+            unsigned v[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = row[i];
+#pragma unroll
+            for (int i = 30; i >= 0; --i) v[i] += v[i + 1];
+            unsigned x = v[0];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_down_sync(0xFFFFFFFFu, x, o);
+                if (lane + o < 32) x += y;
+            }
+            const unsigned carry = x - v[0];  // bins above this lane's run
+#pragma unroll
+            for (int i = 0; i < 32; ++i) row[i] = v[i] + carry;
+        }
+        __syncthreads();
+        // target row c_lo + D receives distances D-15 .. D from the block's sources;
+        // HB_CHUNKS threads write one row's run
+        unsigned short *base_t = Mt + (size_t)t * mt_rows * MT_PITCH;
+        for (unsigned i = tid; i < (unsigned)(HB_CHUNKS - 1 + DET_G) * HB_CHUNKS; i += 256) {
+            const int D = 1 + (int)(i / HB_CHUNKS), u = (int)(i % HB_CHUNKS);
+            const int cc = HB_CHUNKS - 1 - u, d = D - cc;
+            const long long ct = c_lo + D;  // target chunk
+            if (d >= 1 && d <= DET_G && ct >= 1 && ct < (long long)g.nchunks)
+                base_t[(size_t)ct * MT_PITCH + d] = (unsigned short)H.h[cc][hb_slot(d)];
+        }
+        __syncthreads();
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctrl->S = g.S;
@@ -155,103 +167,168 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
     }
 }
 
-// Speculative start of chunk c (c >= 1).  Lanes handle 32 consecutive chunks and scan the
-// aligned windows g = 1..DET_G ending just before their chunk (coalesced rows of Mt),
-// keeping the shortest one that the regulator would shrink at the next event (its length
-// is at the equilibrium of Eq. 20, to within one chunk) plus DET_MARGIN chunks: a slight
-// overestimate of the true queue, which merges with the true trajectory within a few
-// tens of events.  Then, chunk by chunk, the warp applies the chunk's first event exactly,
-// popping the excess in parallel.
+// Speculative start of chunk c >= 1, one warp per chunk.
+// (1) The window: scan the aligned windows g = 1..DET_G ending at cS, 256 distances per
+//     round (8 per lane, one 16-byte load per row and lane, prefix sums by shuffles), up
+//     to the first one that the regulator would shrink at the next event (Eq. 20); then,
+//     inside the chunk where that window starts, the shortest window, to the event, that
+//     would still be shrunk.  Its length is where the regulator holds the queue.
+// (2) Step cS applied to it.  All pops of a step test against the ratio X / Y of the
+//     previous step, so their number is q - q_targ at once (q_targ = max(q_min,
+//     min(q_max, floor(X / Y)))); the warp counts the pixels and tiles whose last queued
+//     event is among the popped ones.
+__device__ __forceinline__ unsigned pick8(const unsigned (&a)[8], unsigned u)
+{
+    unsigned r = a[0];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) r = u == (unsigned)i ? a[i] : r;
+    return r;
+}
+
 __global__ void __launch_bounds__(256)
-k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short *Mt, size_t mt_stride,
-           unsigned *qout, DetState *E0)
+k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short *Mt, size_t mt_rows,
+           DetState *E0)
 {
     PDL_ENTRY();
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long base = ctrl->base;
     const unsigned S = ctrl->S, nch = ctrl->nchunks, Gold = ctrl->Gold;
     const unsigned warps_total = gridDim.x * (blockDim.x >> 5);
-    const unsigned short *MP = Mt, *MT = Mt + (size_t)(DET_G + 1) * mt_stride;
-    for (unsigned cb = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; cb < nch; cb += warps_total * 32) {
-        const unsigned c = cb + lane;
-        const bool real = c >= 1 && c < nch;
+    for (unsigned c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) + 1; c < nch; c += warps_total) {
+        const unsigned short *rp = Mt + (size_t)c * MT_PITCH;
+        const unsigned short *rt = Mt + (mt_rows + c) * MT_PITCH;
+        const unsigned gmax = min((unsigned)DET_G, c + Gold);  // sources that exist in the table
         const unsigned long long reach = (unsigned long long)c * S + base;  // events before the chunk
-        unsigned np = 0, nt = 0, gsel = 0, snp = 0, snt = 0, found = 0;
-        for (unsigned g0 = 1; g0 <= DET_G; g0 += 8) {
-            // the next 8 distances' counts, all loads in flight together
-            unsigned short vp[8], vt[8];
+        unsigned carry_p = 0, carry_t = 0, found = 0, snp = 0, snt = 0, fp1 = 0, ft1 = 0;
+        for (unsigned g0 = 0; g0 <= DET_G && !found; g0 += 256) {
+            const uint4 wp = *reinterpret_cast<const uint4 *>(rp + g0 + 8 * lane);
+            const uint4 wt = *reinterpret_cast<const uint4 *>(rt + g0 + 8 * lane);
+            const unsigned xp[4] = {wp.x, wp.y, wp.z, wp.w}, xt[4] = {wt.x, wt.y, wt.z, wt.w};
+            unsigned pp[8], pt[8];
+            unsigned sp = 0, st = 0;
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const unsigned gg = g0 + u;
-                const long long cw = (long long)c - gg;  // chunk entering the window
-                vp[u] = vt[u] = 0;
-                if (real && gg <= DET_G && cw >= -(long long)Gold) {
-                    const size_t col = (size_t)(cw + Gold);
-                    vp[u] = MP[(size_t)gg * mt_stride + col];
-                    vt[u] = MT[(size_t)gg * mt_stride + col];
-                }
+                const unsigned gg = g0 + 8 * lane + u;
+                const bool ok = gg >= 1 && gg <= gmax;
+                sp += ok ? (xp[u >> 1] >> (16 * (u & 1))) & 0xFFFFu : 0u;
+                st += ok ? (xt[u >> 1] >> (16 * (u & 1))) & 0xFFFFu : 0u;
+                pp[u] = sp;
+                pt[u] = st;
             }
+            // exclusive prefix of the lanes' sums
+            unsigned ip = sp, it = st;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const unsigned gg = g0 + u;
-                if (gg > DET_G) break;
-                np += vp[u];
-                nt += vt[u];
-                if (real && !found) {
-                    const unsigned long long L = min((unsigned long long)gg * S, reach);
-                    const unsigned long long X = L * kp.numA * nt, Y = (unsigned long long)kp.den * np;
-                    const unsigned long long q = L + 1;
-                    if (np > 0 && q > kp.q_min && (q > kp.q_max || q * Y > X)) found = gg;
-                }
-                if (real && gsel == 0 && (found ? gg == min(found + DET_MARGIN, (unsigned)DET_G) : gg == DET_G)) {
-                    gsel = gg;
-                    snp = np;
-                    snt = nt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned yp = __shfl_up_sync(0xFFFFFFFFu, ip, o), yt = __shfl_up_sync(0xFFFFFFFFu, it, o);
+                if (lane >= (unsigned)o) { ip += yp; it += yt; }
+            }
+            const unsigned op = carry_p + ip - sp, ot = carry_t + it - st;
+            unsigned mine = 0;
+#pragma unroll
+            for (int u = 7; u >= 0; --u) {
+                const unsigned gg = g0 + 8 * lane + u;
+                const unsigned long long np = op + pp[u], nt = ot + pt[u];
+                const unsigned long long L = min((unsigned long long)gg * S, reach), q = L + 1;
+                if (gg >= 1 && gg <= DET_G && np > 0 && q > kp.q_min &&
+                    (q > kp.q_max || q * kp.den * np > L * kp.numA * nt))
+                    mine = gg;
+            }
+            const unsigned any = __ballot_sync(0xFFFFFFFFu, mine != 0);
+            if (any) {
+                found = __shfl_sync(0xFFFFFFFFu, mine, __ffs(any) - 1);
+                // N(c, found - 1): in this round, or the carry when found is its first distance
+                const unsigned g1 = found - 1;
+                if (g1 + 1 == g0) {
+                    fp1 = carry_p;
+                    ft1 = carry_t;
+                } else {
+                    const unsigned owner = (g1 - g0) >> 3, u = (g1 - g0) & 7;
+                    fp1 = __shfl_sync(0xFFFFFFFFu, op + pick8(pp, u), owner);
+                    ft1 = __shfl_sync(0xFFFFFFFFu, ot + pick8(pt, u), owner);
                 }
             }
-            if (!__any_sync(0xFFFFFFFFu, real && gsel == 0)) break;  // every lane has its window
+            carry_p += __shfl_sync(0xFFFFFFFFu, ip, 31);
+            carry_t += __shfl_sync(0xFFFFFFFFu, it, 31);
         }
-        // chunk by chunk: the first event of the chunk, pops counted by the whole warp
-        const unsigned todo = __ballot_sync(0xFFFFFFFFu, real);
-        for (unsigned bits = todo; bits; bits &= bits - 1) {
-            const int src = __ffs(bits) - 1;
-            const unsigned cc = cb + src;
-            const unsigned gs = __shfl_sync(0xFFFFFFFFu, gsel, src);
-            const unsigned nap0 = __shfl_sync(0xFFFFFFFFu, snp, src);
-            const unsigned nat0 = __shfl_sync(0xFFFFFFFFu, snt, src);
-            const long long k0 = (long long)cc * S;
-            const long long hs = max(k0 - (long long)gs * S, -(long long)base);
-            const unsigned long long L = (unsigned long long)(k0 - hs);
-            unsigned long long X = L * kp.numA * nat0, Y = (unsigned long long)kp.den * nap0;
-            if (nap0 == 0) { X = kp.q_min; Y = 1; }
-            const uint2 d = prv_of(ring, (base + (unsigned long long)k0) & kp.ring_mask);
-            const unsigned nap = nap0 + ((long long)d.x > (long long)L);
-            const unsigned nat = nat0 + ((long long)d.y > (long long)L);
-            const unsigned long long q = L + 1;
-            unsigned long long qt = X / Y;
-            qt = min(qt, (unsigned long long)kp.q_max);
-            qt = max(qt, (unsigned long long)kp.q_min);
-            const unsigned long long npop = q > qt ? q - qt : 0ull;
-            unsigned dp = 0, dtt = 0;
-            for (unsigned long long i = lane; i < npop; i += 32) {
-                const long long j = hs + (long long)i;
-                const uint2 nn = nxt_of(ring, (base + (unsigned long long)j) & kp.ring_mask);
-                dp += (long long)nn.x > k0 - j;
-                dtt += (long long)nn.y > k0 - j;
+        const long long k0 = (long long)c * S;
+        long long h;
+        if (found && (unsigned long long)found * S <= reach) {
+            // The window starts in chunk c - found: take the shortest one, to the event, that
+            // the regulator would still shrink.  Its counts are N(c, found - 1) plus the
+            // events from its start to the end of that chunk that are the last of their
+            // pixel / tile before k0 (suffix sums of those flags, 32 events per round from
+            // the chunk's end).
+            const long long j0 = k0 - (long long)found * S;
+            unsigned cfp = 0, cft = 0, best = 0;
+            bool got = false;
+            for (int blk = (int)((S - 1) / 32); blk >= 0 && !got; --blk) {
+                const unsigned y = (unsigned)blk * 32 + lane;
+                unsigned fp = 0, ft = 0;
+                if (y < S) {
+                    const long long j = j0 + y;
+                    const uint2 n = nxt_of(ring, (base + (unsigned long long)j) & kp.ring_mask);
+                    const unsigned long long dj = (unsigned long long)(k0 - j);
+                    fp = n.x == SAT || n.x >= dj;
+                    ft = n.y == SAT || n.y >= dj;
+                }
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned yp = __shfl_down_sync(0xFFFFFFFFu, fp, o), yt = __shfl_down_sync(0xFFFFFFFFu, ft, o);
+                    if (lane + o < 32) { fp += yp; ft += yt; }
+                }
+                const unsigned long long np = fp1 + cfp + fp, nt = ft1 + cft + ft;
+                const unsigned long long L = (unsigned long long)found * S - y, q = L + 1;
+                const bool shr = y < S && np > 0 && q > kp.q_min && (q > kp.q_max || q * kp.den * np > L * kp.numA * nt);
+                const unsigned bal = __ballot_sync(0xFFFFFFFFu, shr);
+                if (bal) {
+                    const unsigned top = 31 - __clz(bal);
+                    best = (unsigned)blk * 32 + top;
+                    snp = __shfl_sync(0xFFFFFFFFu, (unsigned)np, top);
+                    snt = __shfl_sync(0xFFFFFFFFu, (unsigned)nt, top);
+                    got = true;
+                }
+                cfp += __shfl_sync(0xFFFFFFFFu, fp, 0);
+                cft += __shfl_sync(0xFFFFFFFFu, ft, 0);
             }
-            dp = warp_sum(dp);
-            dtt = warp_sum(dtt);
-            if (lane == 0) {
-                DetState st0;
-                const unsigned long long qa = q - npop;
-                st0.h = hs + (long long)npop;
-                st0.nap = nap - dp;
-                st0.nat = nat - dtt;
-                st0.X = qa * kp.numA * st0.nat;
-                st0.Y = (unsigned long long)kp.den * st0.nap;
-                E0[cc] = st0;
-                qout[k0] = (unsigned)qa;
-            }
+            h = j0 + best;  // y = 0 always shrinks (the aligned window of `found` chunks)
+        } else {
+            // no shrinking window within DET_G chunks (then all of them), or the window
+            // reaches back to the stream start (then the whole history): the counts
+            // accumulated over the scanned distances
+            h = max(k0 - (long long)(found ? found : DET_G) * S, -(long long)base);
+            snp = carry_p;
+            snt = carry_t;
+        }
+        const unsigned long long ql = (unsigned long long)(k0 - h);
+        const unsigned long long X = ql * kp.numA * snt, Y = (unsigned long long)kp.den * snp;
+        // step k0
+        const uint2 d = prv_of(ring, (base + (unsigned long long)k0) & kp.ring_mask);
+        unsigned nap = snp + (d.x > ql ? 1u : 0u);
+        unsigned nat = snt + (d.y > ql ? 1u : 0u);
+        const unsigned long long q = ql + 1;
+        unsigned long long thr = Y == 0 ? kp.q_max : min((unsigned long long)kp.q_max, X / Y);
+        thr = max(thr, (unsigned long long)kp.q_min);
+        const unsigned P = q > thr ? (unsigned)(q - thr) : 0u;
+        unsigned offp = 0, offt = 0;
+#pragma unroll 4
+        for (unsigned u = lane; u < P; u += 32) {
+            const long long j = h + u;
+            const uint2 n = nxt_of(ring, (base + (unsigned long long)j) & kp.ring_mask);
+            const unsigned long long dj = (unsigned long long)(k0 - j);
+            offp += n.x > dj;
+            offt += n.y > dj;
+        }
+        nap -= warp_sum(offp);
+        nat -= warp_sum(offt);
+        if (lane == 0) {
+            const unsigned long long qn = q - P;
+            DetState st0;
+            st0.h = h + P;
+            st0.nap = nap;
+            st0.nat = nat;
+            st0.X = qn * kp.numA * nat;
+            st0.Y = (unsigned long long)kp.den * nap;
+            E0[c] = st0;
         }
     }
 }
@@ -381,55 +458,268 @@ __device__ __forceinline__ bool group_run(const KParams &kp, unsigned long long 
     return merged;
 }
 
-constexpr int DET_GW = 8;  // lanes per chunk in the parallel passes
+// ---------------------------------------------------------------------------------------
+// Lane engine for the parallel passes: lane j of a warp runs chunk j's steps one after
+// the other (32 chunks per warp).  Each lane stages the links its next steps need in
+// shared memory with asynchronous copies, one block of LR_B steps ahead:
+//   push: {dP, dT} of the block's events, double buffered;
+//   pop:  {nP, nT} of the events from the queue front h on, a ring of LR_R entries kept
+//         full; pops past the landed entries read the ring buffer in global memory;
+//   ref:  (merge mode) the queue lengths already in qout, to detect the merge.
+// A step counts its pops first (the pop test needs only q and the ratio of the previous
+// step), then reads the popped events' links.  A lane with more than LR_BIG pops in a
+// step (after a too-long start) has them counted by the whole warp with coalesced loads,
+// and its ring refilled from the new queue front.
+constexpr int LR_B = 16;      // steps per staged block
+constexpr int LR_R = 128;     // pop-link ring entries per lane (power of two)
+constexpr int LR_BIG = 16;    // pops per step handled by the lane alone
+constexpr int LR_WARPS = 2;   // warps per block
 
-// Pass 1, groups of DET_GW lanes per chunk.  Chunk c >= 1 warms up over the previous
-// chunk: it starts from the speculative state of chunk c-1's first event (E0[c-1]) and
-// records the queue lengths of its own chunk only, so its trajectory has had a whole
-// chunk to merge with the true one by the time its own chunk starts.
-__global__ void __launch_bounds__(128)
+// q_targ = max(q_min, min(q_max, floor(X / Y))) (Eq. 20 as the ratio X / Y, Y = 0 when
+// N_ap = 0): a single-precision quotient, then corrected with exact 64-bit products so
+// that the result is the exact floor.
+__device__ __forceinline__ unsigned q_target(const KParams &kp, unsigned long long X, unsigned Y)
+{
+    if (Y == 0) return max(kp.q_min, kp.q_max);
+    const float r = __fdividef((float)X, (float)Y);
+    unsigned t = r >= (float)kp.q_max ? kp.q_max + 1u : (unsigned)r;
+    while (t > 0 && (unsigned long long)t * Y > X) --t;                     // t <= X / Y
+    while (t <= kp.q_max && (unsigned long long)(t + 1) * Y <= X) ++t;      // t = floor, or above q_max
+    return max(kp.q_min, min(kp.q_max, t));
+}
+
+struct LaneSmem {
+    uint2 push[2][32][LR_B + 1];
+    uint2 pop[32][LR_R + 1];
+    unsigned ref[2][32][LR_B + 1];
+};
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+__device__ __forceinline__ const uint2 *nxt_ptr(const uint4 *ring, unsigned base32, unsigned mask32, int e)
+{
+    return reinterpret_cast<const uint2 *>(ring) + 2 * ((base32 + (unsigned)e) & mask32) + 1;
+}
+
+// Lane j runs its chunk's steps [k0, k1) from st, writing the queue lengths of steps
+// k >= kw to qout.  kMerge: stop before the first step whose queue length equals qout's
+// (the entry is already right) and return whether that happened; *nsteps counts the steps
+// up to and including the merge.
+template <bool kMerge>
+__device__ bool lane_run(const KParams &kp, unsigned long long base, const uint4 *__restrict__ ring,
+                         unsigned *qout, unsigned k0, unsigned k1, unsigned kw, DetState &st,
+                         LaneSmem &sm, Ctrl *ctrl, unsigned *nsteps)
+{
+    unsigned *err = &ctrl->error;
+    unsigned n_big = 0, n_miss = 0;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned mask32 = (unsigned)kp.ring_mask, base32 = (unsigned)base;
+    const uint2 *ring2 = reinterpret_cast<const uint2 *>(ring);
+    int h = (int)st.h;
+    unsigned nap = st.nap, nat = st.nat;
+    unsigned long long X = st.X;
+    unsigned Y = (unsigned)st.Y;
+    bool active = k0 < k1, merged = false;
+    unsigned done = 0;
+    unsigned span = active ? k1 - k0 : 0u;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) span = max(span, __shfl_xor_sync(0xFFFFFFFFu, span, o));
+    const unsigned nblk = (span + LR_B - 1) / LR_B;
+    // pop links [h, v) have landed, [v, f) are in flight
+    int f = h, v = h;
+    auto fill_pop = [&]() {
+        if (f < h) f = h;
+        const int want = active ? h + LR_R - f : 0;
+        for (int u = 0; u < want; ++u) cp_async8(&sm.pop[lane][(f + u) & (LR_R - 1)], nxt_ptr(ring, base32, mask32, f + u));
+        if (want > 0) f = h + LR_R;
+    };
+    auto stage = [&](int buf, unsigned b) {
+        const unsigned kb = k0 + b * LR_B;
+        for (unsigned i = 0; i < LR_B; ++i) {
+            const unsigned k = kb + i;
+            if (!(active && k < k1)) break;
+            cp_async8(&sm.push[buf][lane][i], ring2 + 2 * ((base32 + k) & mask32));
+            if (kMerge) cp_async4(&sm.ref[buf][lane][i], qout + k);
+        }
+    };
+    fill_pop();
+    stage(0, 0);
+    cp_async_wait_all();
+    v = f;
+    __syncwarp();
+    for (unsigned b = 0; b < nblk; ++b) {
+        if (!__any_sync(0xFFFFFFFFu, active)) break;
+        const int buf = b & 1;
+        if (b + 1 < nblk) stage(buf ^ 1, b + 1);
+        fill_pop();
+        for (unsigned i = 0; i < LR_B; ++i) {
+            const unsigned k = k0 + b * LR_B + i;
+            bool act = active && k < k1;
+            const int dist = (int)k - h;
+            if (act && dist < 0) {  // impossible for a consistent state; never loop on a bad one
+                atomicOr(err, ERR_BAD_STATE);
+                active = act = false;
+            }
+            unsigned q = 0, P = 0;
+            if (act) {
+                const uint2 d = sm.push[buf][lane][i];
+                nap += d.x > (unsigned)dist;
+                nat += d.y > (unsigned)dist;
+                q = (unsigned)dist + 1u;
+                // pops of this step: the test "q > q_targ" is monotone in q
+                const unsigned T = q_target(kp, X, Y);
+                P = q > T ? q - T : 0u;
+            }
+            unsigned big = __ballot_sync(0xFFFFFFFFu, P > LR_BIG);
+            if (big) {
+                // the warp counts the big pops with coalesced loads and refills those
+                // lanes' rings; in-flight copies land first so that no ring slot races
+                cp_async_wait_all();
+                __syncwarp();
+                if (f > v) v = f;
+                while (big) {
+                    const unsigned j = __ffs(big) - 1;
+                    big &= big - 1;
+                    const int hj = __shfl_sync(0xFFFFFFFFu, h, j);
+                    const unsigned Pj = __shfl_sync(0xFFFFFFFFu, P, j), kj = __shfl_sync(0xFFFFFFFFu, k, j);
+                    unsigned op = 0, ot = 0;
+#pragma unroll 4
+                    for (unsigned u = lane; u < Pj; u += 32) {
+                        const uint2 n = *nxt_ptr(ring, base32, mask32, hj + (int)u);
+                        const unsigned dj = kj - (unsigned)(hj + (int)u);
+                        op += n.x > dj;
+                        ot += n.y > dj;
+                    }
+                    op = warp_sum(op);
+                    ot = warp_sum(ot);
+                    const int hn = hj + (int)Pj;
+                    for (unsigned u = lane; u < LR_R; u += 32)
+                        sm.pop[j][(hn + (int)u) & (LR_R - 1)] = *nxt_ptr(ring, base32, mask32, hn + (int)u);
+                    if (lane == j) {
+                        ++n_big;
+                        nap -= op;
+                        nat -= ot;
+                        h = hn;
+                        q -= Pj;
+                        P = 0;
+                        f = v = hn + LR_R;
+                    }
+                }
+                __syncwarp();
+            }
+            // the lane's own pops, links from its ring (from global memory past the
+            // landed entries: rare, so the common case runs without that test)
+            if (__all_sync(0xFFFFFFFFu, h + (int)P <= v)) {
+                const uint2 *rg = sm.pop[lane];
+                for (unsigned u = 0; u < P; ++u) {
+                    const uint2 n = rg[(h + (int)u) & (LR_R - 1)];
+                    const unsigned dj = k - (unsigned)h - u;
+                    nap -= n.x > dj;
+                    nat -= n.y > dj;
+                }
+                h += (int)P;
+            } else {
+                for (unsigned u = 0; u < P; ++u) {
+                    n_miss += h >= v;
+                    const uint2 n = h < v ? sm.pop[lane][h & (LR_R - 1)] : *nxt_ptr(ring, base32, mask32, h);
+                    const unsigned dj = k - (unsigned)h;
+                    nap -= n.x > dj;
+                    nat -= n.y > dj;
+                    ++h;
+                }
+            }
+            q -= P;
+            if (act) {
+                X = (unsigned long long)q * kp.numA * nat;
+                Y = kp.den * nap;
+                if (kMerge && sm.ref[buf][lane][i] == q) {
+                    merged = true;
+                    active = false;
+                    done = k + 1 - k0;
+                } else if (k >= kw) {
+                    qout[k] = q;
+                }
+            }
+        }
+        cp_async_wait_all();
+        v = f;
+        __syncwarp();
+    }
+    if (!kMerge || !merged) done = k1 > k0 ? k1 - k0 : 0u;
+    if (nsteps) *nsteps = done;
+    n_big = warp_sum(n_big);
+    n_miss = warp_sum(n_miss);
+    if (lane == 0 && (n_big | n_miss)) {
+        atomicAdd(&ctrl->big_pops, (unsigned long long)n_big);
+        atomicAdd(&ctrl->ring_misses, (unsigned long long)n_miss);
+    }
+    st.h = h; st.nap = nap; st.nat = nat; st.X = X; st.Y = Y;
+    return merged;
+}
+
+// Pass 1.  Chunk c >= 2 warms up over the previous chunk: it starts from the speculative
+// state after chunk c-1's first event (E0[c-1]) and records the queue lengths of its own
+// chunk only, so its trajectory has had a whole chunk to merge with the true one by the
+// time its own chunk starts.  Chunks 0 and 1 start from the true state at the batch start.
+__global__ void __launch_bounds__(32 * LR_WARPS, 1)
 k_det_pass1(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *qout,
             const DetState *E0, DetState *E1)
 {
     PDL_ENTRY();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LaneSmem &sm = reinterpret_cast<LaneSmem *>(smem_raw)[threadIdx.x >> 5];
     const unsigned long long base = ctrl->base;
     const unsigned m = ctrl->m, S = ctrl->S, nch = ctrl->nchunks;
     const unsigned lane = threadIdx.x & 31;
-    constexpr unsigned CPW = 32 / DET_GW;  // chunks per warp
-    const unsigned warps = gridDim.x * (blockDim.x >> 5);
-    for (unsigned wb = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * CPW; wb < nch; wb += warps * CPW) {
-        const unsigned c = wb + lane / DET_GW;
+    const unsigned warps = gridDim.x * LR_WARPS;
+    for (unsigned wb = (blockIdx.x * LR_WARPS + (threadIdx.x >> 5)) * 32; wb < nch; wb += warps * 32) {
+        const unsigned c = wb + lane;
         DetState st{0, 0, 0, 0, 1};
         unsigned k0 = 0, k1 = 0, kw = 0;
         if (c < nch) {
             kw = c * S;
             k1 = min(m, (c + 1) * S);
-            if (c <= 1) {  // from the true state at the batch start
+            if (c <= 1) {
                 st = ctrl->det;
                 st.h = (long long)((unsigned long long)st.h - base);
                 k0 = 0;
             } else {
                 st = E0[c - 1];
-                k0 = (c - 1) * S + 1;  // chunk c-1's first event was applied by k_det_init
+                k0 = (c - 1) * S + 1;  // E0[c-1] holds the state after chunk c-1's first event
             }
         }
-        group_run<DET_GW, false>(kp, base, ring, qout, k0, k1, st, &ctrl->error, nullptr, kw);
-        if (c < nch && lane % DET_GW == 0) E1[c] = st;
+        lane_run<false>(kp, base, ring, qout, k0, k1, kw, st, sm, ctrl, nullptr);
+        if (c < nch) E1[c] = st;
     }
 }
 
-__global__ void __launch_bounds__(128)
+// Pass 2: chunk c >= 1 re-runs from pass 1's exit of chunk c-1 until it merges with
+// pass 1's trajectory of its own chunk.
+__global__ void __launch_bounds__(32 * LR_WARPS, 1)
 k_det_pass2(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *qout,
             const DetState *E1, DetState *E2, unsigned char *merged, unsigned *unm_bits)
 {
     PDL_ENTRY();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LaneSmem &sm = reinterpret_cast<LaneSmem *>(smem_raw)[threadIdx.x >> 5];
     const unsigned long long base = ctrl->base;
     const unsigned m = ctrl->m, S = ctrl->S, nch = ctrl->nchunks;
     const unsigned lane = threadIdx.x & 31;
-    constexpr unsigned CPW = 32 / DET_GW;
-    const unsigned warps = gridDim.x * (blockDim.x >> 5);
-    for (unsigned wb = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * CPW; wb < nch; wb += warps * CPW) {
-        const unsigned c = wb + lane / DET_GW;
+    const unsigned warps = gridDim.x * LR_WARPS;
+    for (unsigned wb = (blockIdx.x * LR_WARPS + (threadIdx.x >> 5)) * 32; wb < nch; wb += warps * 32) {
+        const unsigned c = wb + lane;
         const bool real = c >= 1 && c < nch;
         DetState st{0, 0, 0, 0, 1};
         unsigned k0 = 0, k1 = 0;
@@ -439,8 +729,8 @@ k_det_pass2(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *qout,
             k1 = min(m, (c + 1) * S);
         }
         unsigned steps = 0;
-        const bool mg = group_run<DET_GW, true>(kp, base, ring, qout, k0, k1, st, &ctrl->error, &steps);
-        if (real && lane % DET_GW == 0) {
+        const bool mg = lane_run<true>(kp, base, ring, qout, k0, k1, k0, st, sm, ctrl, &steps);
+        if (real) {
             merged[c] = mg;
             atomicAdd(&ctrl->pass2_steps, (unsigned long long)steps);
             if (!mg) {
@@ -540,26 +830,42 @@ cudaError_t launch_det_counts(const KParams &kp, const Bufs &b, cudaStream_t s, 
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (cudaError_t e_ = launch_pdl(k_det_hist, grid_for(2), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_stride))
+    if (cudaError_t e_ = launch_pdl(k_det_hist, grid_for(2), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows))
         return e_;
-    if (cudaError_t e_ = launch_pdl(k_det_init, grid_for(2), 256, 0, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_stride,
-                                    b.qout, b.E0))
+    if (cudaError_t e_ = launch_pdl(k_det_init, grid_for(8), 256, 0, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
+                                    b.E0))
         return e_;
     return cudaGetLastError();
+}
+
+static cudaError_t lane_smem_attr()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    const int smem = (int)(sizeof(LaneSmem) * LR_WARPS);
+    cudaError_t e = cudaFuncSetAttribute(k_det_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_det_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) done = true;
+    return e;
 }
 
 cudaError_t launch_det_pass1(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)
 {
     nl += 1;
-    if (cudaError_t e_ = launch_pdl(k_det_pass1, grid_for(8), 128, 0, s, kp, b.ctrl, b.ring4, b.qout, b.E0, b.E1)) return e_;
+    if (cudaError_t e = lane_smem_attr()) return e;
+    if (cudaError_t e_ = launch_pdl(k_det_pass1, grid_for(2), 32 * LR_WARPS, sizeof(LaneSmem) * LR_WARPS, s, kp,
+                                    b.ctrl, b.ring4, b.qout, b.E0, b.E1))
+        return e_;
     return cudaGetLastError();
 }
 
 cudaError_t launch_det_pass2(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)
 {
     nl += 1;
-    if (cudaError_t e_ = launch_pdl(k_det_pass2, grid_for(8), 128, 0, s, kp, b.ctrl, b.ring4, b.qout, b.E1, b.E2, b.merged,
-                                           b.unm_bits)) return e_;
+    if (cudaError_t e = lane_smem_attr()) return e;
+    if (cudaError_t e_ = launch_pdl(k_det_pass2, grid_for(2), 32 * LR_WARPS, sizeof(LaneSmem) * LR_WARPS, s, kp,
+                                    b.ctrl, b.ring4, b.qout, b.E1, b.E2, b.merged, b.unm_bits))
+        return e_;
     return cudaGetLastError();
 }
 
