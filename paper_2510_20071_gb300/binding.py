@@ -23,7 +23,7 @@ FIBAR_ETIMEOUT = -5
 
 EXPORTED = ["fibar_default_params", "fibar_create", "fibar_push_events", "fibar_readout",
             "fibar_flush", "fibar_debug_state", "fibar_stats", "fibar_set_timing",
-            "fibar_stage_times", "fibar_last_error", "fibar_destroy"]
+            "fibar_stage_times", "fibar_last_error", "fibar_destroy", "fibar_queue_counts_noalloc"]
 
 STAGES = ["decode", "sort", "walk", "det_counts", "det_pass1", "det_pass2", "det_fix", "s1_blur",
           "readout", "commit"]
@@ -102,6 +102,8 @@ def load_library(build_if_missing: bool = True):
             lib.fibar_last_error.restype = C.c_char_p
             lib.fibar_destroy.argtypes = [vp]
             lib.fibar_destroy.restype = None
+            lib.fibar_queue_counts_noalloc.argtypes = [vp, vp, C.c_int, vp]
+            lib.fibar_queue_counts_noalloc.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -154,6 +156,10 @@ def fibar_last_error(h) -> str:
 
 def fibar_destroy(h) -> None:
     load_library().fibar_destroy(h)
+
+
+def fibar_queue_counts_noalloc(h, cnt_ptr: int, on_device: int, stream: int) -> int:
+    return load_library().fibar_queue_counts_noalloc(h, cnt_ptr, on_device, stream)
 
 
 # --- convenience wrapper ---------------------------------------------------------------
@@ -248,6 +254,18 @@ class Fibar:
         st = FibarStats()
         self._check(fibar_stats(self.h, st, self._s))
         return {n: int(getattr(st, n)) for n, _ in FibarStats._fields_}
+
+    def queue_counts_noalloc(self, out=None):
+        """Queued events per pixel into ``out`` (a contiguous int32/uint32-sized tensor of
+        W*H elements, CUDA or CPU; default a new CUDA int32 tensor), allocating nothing
+        inside the library."""
+        t = self.torch
+        if out is None:
+            out = t.empty((self.H, self.W), dtype=t.int32, device="cuda")
+        if out.dtype != t.int32 or out.numel() != self.W * self.H or not out.is_contiguous():
+            raise TypeError("out must be a contiguous int32 tensor with W*H elements")
+        self._check(fibar_queue_counts_noalloc(self.h, out.data_ptr(), 1 if out.is_cuda else 0, self._s))
+        return out
 
     def state(self) -> dict:
         npix = self.W * self.H
