@@ -51,7 +51,7 @@ void free_all(fibar_t *h)
     Bufs &b = h->b;
     void *ptrs[] = {b.ctrl, b.pbar, b.L, b.last_pix, b.last_tile, b.staging, b.carry[0], b.carry[1],
                     b.dec_status, b.rec[0], b.rec[1], b.sort_hist, b.sort_base, b.sort_rows, b.sort_rowflag, b.sort_gtot, b.sort_gflag, b.sort_gcount,
-                    b.qout, b.ring4, b.ring_pix, b.bucket_start, b.bucket_cnt, b.dMt, b.E0, b.E1, b.E2, b.merged, b.unm_bits,
+                    b.qout, b.ring4, b.ring_pix, b.bucket_start, b.bucket_cnt, b.dMt, b.E0, b.E1, b.E2, b.p2_ids, b.merged, b.unm_bits,
                     b.out_staging, b.dbg_cnt, b.plist, b.plnb, b.epos, b.lbl, b.s1_info, b.s1_linit,
                     b.popk, b.blur_ord, b.bk, b.bpix, b.bj, b.bD, b.bflag, b.sel_status, b.beta_pow};
     for (void *p : ptrs)
@@ -183,6 +183,7 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
         ALLOC(b.E0, b.max_chunks);
         ALLOC(b.E1, b.max_chunks);
         ALLOC(b.E2, b.max_chunks);
+        ALLOC(b.p2_ids, b.max_chunks);
         ALLOC(b.merged, b.max_chunks);
         ALLOC(b.unm_bits, b.max_chunks / 32 + 2);
     }

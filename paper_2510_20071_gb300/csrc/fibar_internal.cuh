@@ -38,6 +38,7 @@ constexpr int MAX_BUCKETS = 8192;              // buckets of <= 512 tiles (W*H <
 constexpr int MAXSEG = 192;                    // pending device packets per read-out
 constexpr uint32_t CHUNK = 64;                 // minimum detector chunk length (events)
 constexpr unsigned DET_G = 1023;               // reach of the guessed windows, in chunks
+constexpr unsigned DET_WARM = 32;              // steps a chunk runs from its guess before its own steps
 constexpr unsigned DET_MAX_CHUNKS = 32768;     // chunks per batch at most (S grows beyond)
 constexpr int LB_WIN = 8;                      // look-back window (predecessor tiles per load round)
 constexpr int LB_GROUP = 32;                   // sort tiles per published group total
@@ -79,6 +80,7 @@ struct Ctrl {
     unsigned int blur_ticket;    // S1: dataflow work counter
     unsigned int sel_ticket;     // S1: stale-list compaction tile counter
     unsigned int walk_ticket;    // bucket walk work counter
+    unsigned int p2_count;       // chunks that pass 2 hands on to its warp-per-chunk stage
     unsigned long long unmerged_total;  // diagnostics, cumulative
     unsigned long long pass2_steps;
     unsigned long long fix_steps;
@@ -134,6 +136,7 @@ struct Bufs {
     unsigned short *dMt;         // [2][mt_rows][DET_G + 1] suffix histograms by target chunk
     size_t mt_rows;              // chunk rows per table of dMt
     DetState *E0, *E1, *E2;
+    unsigned int *p2_ids;        // [max_chunks] chunks continued by the warp-per-chunk pass 2
     unsigned char *merged;
     unsigned *unm_bits;          // [chunks / 32] chunks that did not merge in pass 2
     float *out_staging;

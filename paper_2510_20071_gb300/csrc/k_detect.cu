@@ -17,13 +17,14 @@
 //         then to the event inside the chunk where it starts.  k_det_init applies step cS
 //         to it; the trajectory then coincides with the true one within a few tens of
 //         steps (most often fewer than 16).
-// Pass 1: each chunk runs from its guess, warming up over the previous chunk.
+// Pass 1: each chunk runs from its guess.
 // Pass 2: chunk c restarts from pass 1's exit state of chunk c-1 and runs until its
-//         queue length equals pass 1's at the same step (the trajectories merged).
+//         queue length equals pass 1's at the same step (the trajectories merged):
+//         one chunk per lane for the first steps, then one chunk per warp for the few
+//         that take longer.
 // Fixup:  if some chunk did not merge, one warp walks the chunks in order and re-runs
 //         exactly those whose entry state was wrong.  The result is exact in all cases.
-// Passes 1 and 2 run one chunk per lane (lane_run); the fixup runs one chunk per warp
-// (group_run).
+// One chunk per lane is lane_run, one chunk per warp is group_run.
 #include "fibar_internal.cuh"
 
 namespace fibar {
@@ -187,7 +188,7 @@ __device__ __forceinline__ unsigned pick8(const unsigned (&a)[8], unsigned u)
 
 __global__ void __launch_bounds__(256)
 k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short *Mt, size_t mt_rows,
-           DetState *E0)
+           DetState *E0, unsigned *qout)
 {
     PDL_ENTRY();
     const unsigned lane = threadIdx.x & 31;
@@ -329,6 +330,7 @@ k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short
             st0.X = qn * kp.numA * nat;
             st0.Y = (unsigned long long)kp.den * nap;
             E0[c] = st0;
+            qout[k0] = (unsigned)qn;
         }
     }
 }
@@ -468,12 +470,18 @@ __device__ __forceinline__ bool group_run(const KParams &kp, unsigned long long 
 //   ref:  (merge mode) the queue lengths already in qout, to detect the merge.
 // A step counts its pops first (the pop test needs only q and the ratio of the previous
 // step), then reads the popped events' links.  A lane with more than LR_BIG pops in a
-// step (after a too-long start) has them counted by the whole warp with coalesced loads,
-// and its ring refilled from the new queue front.
+// step (after a bad start) has them counted by the whole warp with coalesced loads, and
+// its ring refilled.
 constexpr int LR_B = 16;      // steps per staged block
 constexpr int LR_R = 128;     // pop-link ring entries per lane (power of two)
-constexpr int LR_BIG = 16;    // pops per step handled by the lane alone
+constexpr int LR_BIG = 64;    // pops per step handled by the lane alone
 constexpr int LR_WARPS = 2;   // warps per block
+
+struct LaneSmem {
+    uint2 push[2][32][LR_B + 1];
+    uint2 pop[32][LR_R + 1];
+    unsigned ref[2][32][LR_B + 1];
+};
 
 // q_targ = max(q_min, min(q_max, floor(X / Y))) (Eq. 20 as the ratio X / Y, Y = 0 when
 // N_ap = 0): a single-precision quotient, then corrected with exact 64-bit products so
@@ -481,18 +489,14 @@ constexpr int LR_WARPS = 2;   // warps per block
 __device__ __forceinline__ unsigned q_target(const KParams &kp, unsigned long long X, unsigned Y)
 {
     if (Y == 0) return max(kp.q_min, kp.q_max);
-    const float r = __fdividef((float)X, (float)Y);
+    // X as a float from its 32-bit halves (a 64-bit conversion is slow)
+    const float xf = fmaf(__uint2float_rn((unsigned)(X >> 32)), 4294967296.0f, __uint2float_rn((unsigned)X));
+    const float r = __fdividef(xf, __uint2float_rn(Y));
     unsigned t = r >= (float)kp.q_max ? kp.q_max + 1u : (unsigned)r;
     while (t > 0 && (unsigned long long)t * Y > X) --t;                     // t <= X / Y
     while (t <= kp.q_max && (unsigned long long)(t + 1) * Y <= X) ++t;      // t = floor, or above q_max
     return max(kp.q_min, min(kp.q_max, t));
 }
-
-struct LaneSmem {
-    uint2 push[2][32][LR_B + 1];
-    uint2 pop[32][LR_R + 1];
-    unsigned ref[2][32][LR_B + 1];
-};
 
 __device__ __forceinline__ void cp_async8(void *dst, const void *src)
 {
@@ -527,6 +531,7 @@ __device__ bool lane_run(const KParams &kp, unsigned long long base, const uint4
     const unsigned lane = threadIdx.x & 31;
     const unsigned mask32 = (unsigned)kp.ring_mask, base32 = (unsigned)base;
     const uint2 *ring2 = reinterpret_cast<const uint2 *>(ring);
+    const uint2 *rg = sm.pop[lane];
     int h = (int)st.h;
     unsigned nap = st.nap, nat = st.nat;
     unsigned long long X = st.X;
@@ -539,20 +544,36 @@ __device__ bool lane_run(const KParams &kp, unsigned long long base, const uint4
     const unsigned nblk = (span + LR_B - 1) / LR_B;
     // pop links [h, v) have landed, [v, f) are in flight
     int f = h, v = h;
+    // copy the pop links of events [e, e + n) into the lane's ring (n <= LR_R), walking
+    // source and destination pointers through at most two wraps of each ring
+    auto copy_links = [&](int e, int n) {
+        while (n > 0) {
+            const unsigned gs = (base32 + (unsigned)e) & mask32;          // global slot
+            const unsigned ss = (unsigned)e & (LR_R - 1);                // ring slot
+            const int run = min(n, (int)min(mask32 + 1 - gs, (unsigned)LR_R - ss));
+            const uint2 *src = ring2 + 2 * (size_t)gs + 1;
+            uint2 *dst = &sm.pop[lane][ss];
+            for (int u = 0; u < run; ++u) cp_async8(dst + u, src + 2 * u);
+            e += run;
+            n -= run;
+        }
+    };
     auto fill_pop = [&]() {
         if (f < h) f = h;
         const int want = active ? h + LR_R - f : 0;
-        for (int u = 0; u < want; ++u) cp_async8(&sm.pop[lane][(f + u) & (LR_R - 1)], nxt_ptr(ring, base32, mask32, f + u));
+        copy_links(f, want);
         if (want > 0) f = h + LR_R;
     };
     auto stage = [&](int buf, unsigned b) {
         const unsigned kb = k0 + b * LR_B;
-        for (unsigned i = 0; i < LR_B; ++i) {
-            const unsigned k = kb + i;
-            if (!(active && k < k1)) break;
-            cp_async8(&sm.push[buf][lane][i], ring2 + 2 * ((base32 + k) & mask32));
-            if (kMerge) cp_async4(&sm.ref[buf][lane][i], qout + k);
-        }
+        const int n = active ? (int)min((unsigned)LR_B, k1 > kb ? k1 - kb : 0u) : 0;
+        const unsigned gs = (base32 + kb) & mask32;
+        const int run = min(n, (int)(mask32 + 1 - gs));
+        const uint2 *src = ring2 + 2 * (size_t)gs;
+        for (int u = 0; u < run; ++u) cp_async8(&sm.push[buf][lane][u], src + 2 * u);
+        for (int u = run; u < n; ++u) cp_async8(&sm.push[buf][lane][u], ring2 + 2 * (size_t)(u - run));
+        if (kMerge)
+            for (int u = 0; u < n; ++u) cp_async4(&sm.ref[buf][lane][u], qout + kb + u);
     };
     fill_pop();
     stage(0, 0);
@@ -572,20 +593,24 @@ __device__ bool lane_run(const KParams &kp, unsigned long long base, const uint4
                 atomicOr(err, ERR_BAD_STATE);
                 active = act = false;
             }
-            unsigned q = 0, P = 0;
+            // push
+            const uint2 d = sm.push[buf][lane][i];
+            const unsigned ud = (unsigned)dist;
             if (act) {
-                const uint2 d = sm.push[buf][lane][i];
-                nap += d.x > (unsigned)dist;
-                nat += d.y > (unsigned)dist;
-                q = (unsigned)dist + 1u;
-                // pops of this step: the test "q > q_targ" is monotone in q
+                nap += d.x > ud;
+                nat += d.y > ud;
+            }
+            unsigned q = ud + 1u;
+            // pops of this step: the test "q > q_targ" is monotone in q
+            unsigned P = 0;
+            if (act) {
                 const unsigned T = q_target(kp, X, Y);
                 P = q > T ? q - T : 0u;
             }
-            unsigned big = __ballot_sync(0xFFFFFFFFu, P > LR_BIG);
-            if (big) {
+            if (__any_sync(0xFFFFFFFFu, P > LR_BIG)) {
                 // the warp counts the big pops with coalesced loads and refills those
                 // lanes' rings; in-flight copies land first so that no ring slot races
+                unsigned big = __ballot_sync(0xFFFFFFFFu, P > LR_BIG);
                 cp_async_wait_all();
                 __syncwarp();
                 if (f > v) v = f;
@@ -619,15 +644,16 @@ __device__ bool lane_run(const KParams &kp, unsigned long long base, const uint4
                 }
                 __syncwarp();
             }
-            // the lane's own pops, links from its ring (from global memory past the
-            // landed entries: rare, so the common case runs without that test)
-            if (__all_sync(0xFFFFFFFFu, h + (int)P <= v)) {
-                const uint2 *rg = sm.pop[lane];
-                for (unsigned u = 0; u < P; ++u) {
-                    const uint2 n = rg[(h + (int)u) & (LR_R - 1)];
-                    const unsigned dj = k - (unsigned)h - u;
-                    nap -= n.x > dj;
-                    nat -= n.y > dj;
+            // the lane's own pops, links from its ring, two per iteration (from global
+            // memory past the landed entries: rare, a separate loop)
+            if (!__any_sync(0xFFFFFFFFu, h + (int)P > v)) {
+                const unsigned hu = (unsigned)h, kh = k - hu;  // k - e = kh - u for e = h + u
+                for (unsigned u = 0; u < P; u += 2) {
+                    const uint2 n0 = rg[(hu + u) & (LR_R - 1)];
+                    const uint2 n1 = rg[(hu + u + 1) & (LR_R - 1)];
+                    const bool two = u + 1 < P;
+                    nap -= (n0.x > kh - u) + (two && n1.x > kh - u - 1);
+                    nat -= (n0.y > kh - u) + (two && n1.y > kh - u - 1);
                 }
                 h += (int)P;
             } else {
@@ -669,10 +695,22 @@ __device__ bool lane_run(const KParams &kp, unsigned long long base, const uint4
     return merged;
 }
 
-// Pass 1.  Chunk c >= 2 warms up over the previous chunk: it starts from the speculative
-// state after chunk c-1's first event (E0[c-1]) and records the queue lengths of its own
-// chunk only, so its trajectory has had a whole chunk to merge with the true one by the
-// time its own chunk starts.  Chunks 0 and 1 start from the true state at the batch start.
+// Chunk c's own steps (its queue lengths are pass 1's and its exit is E1[c]) are
+// [own_begin(c), own_begin(c + 1)); for c >= 1 they start DET_WARM steps after its
+// speculative start at cS, which pass 1 uses to converge.  The last chunk keeps at
+// least its last event.
+__device__ __forceinline__ unsigned own_begin(unsigned c, unsigned S, unsigned m)
+{
+    return c == 0 ? 0u : min(c * S + DET_WARM, m - 1);
+}
+__device__ __forceinline__ unsigned own_end(unsigned c, unsigned S, unsigned m, unsigned nch)
+{
+    return c + 1 < nch ? own_begin(c + 1, S, m) : m;
+}
+
+// Pass 1: chunk c >= 1 runs from its speculative start E0[c] (the state after step cS)
+// to the end of its own steps, recording those; chunk 0 starts from the true state at the
+// batch start.
 __global__ void __launch_bounds__(32 * LR_WARPS, 1)
 k_det_pass1(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *qout,
             const DetState *E0, DetState *E1)
@@ -689,15 +727,15 @@ k_det_pass1(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *qout,
         DetState st{0, 0, 0, 0, 1};
         unsigned k0 = 0, k1 = 0, kw = 0;
         if (c < nch) {
-            kw = c * S;
-            k1 = min(m, (c + 1) * S);
-            if (c <= 1) {
+            k1 = own_end(c, S, m, nch);
+            kw = own_begin(c, S, m);
+            if (c == 0) {
                 st = ctrl->det;
                 st.h = (long long)((unsigned long long)st.h - base);
                 k0 = 0;
             } else {
-                st = E0[c - 1];
-                k0 = (c - 1) * S + 1;  // E0[c-1] holds the state after chunk c-1's first event
+                st = E0[c];
+                k0 = c * S + 1;
             }
         }
         lane_run<false>(kp, base, ring, qout, k0, k1, kw, st, sm, ctrl, nullptr);
@@ -706,10 +744,24 @@ k_det_pass1(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *qout,
 }
 
 // Pass 2: chunk c >= 1 re-runs from pass 1's exit of chunk c-1 until it merges with
-// pass 1's trajectory of its own chunk.
+// pass 1's trajectory of its own chunk.  Most chunks merge within a few steps, a few
+// need tens: the lane stage (k_det_pass2) runs every chunk for at most P2_LANE_STEPS
+// steps and lists the ones still running, which k_det_pass2w continues one warp per
+// chunk (a step costs a warp there, but the chains of the slow chunks run side by side).
+constexpr unsigned P2_LANE_STEPS = LR_B;
+
+__device__ __forceinline__ void p2_unmerged(Ctrl *ctrl, const DetState &st, unsigned c, DetState *E2,
+                                            unsigned *unm_bits)
+{
+    E2[c] = st;
+    atomicAdd(&ctrl->unmerged, 1u);
+    atomicAdd(&ctrl->unmerged_total, 1ull);
+    atomicOr(&unm_bits[c >> 5], 1u << (c & 31));
+}
+
 __global__ void __launch_bounds__(32 * LR_WARPS, 1)
 k_det_pass2(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *qout,
-            const DetState *E1, DetState *E2, unsigned char *merged, unsigned *unm_bits)
+            const DetState *E1, DetState *E2, unsigned char *merged, unsigned *unm_bits, unsigned *p2_ids)
 {
     PDL_ENTRY();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -722,23 +774,49 @@ k_det_pass2(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *qout,
         const unsigned c = wb + lane;
         const bool real = c >= 1 && c < nch;
         DetState st{0, 0, 0, 0, 1};
-        unsigned k0 = 0, k1 = 0;
+        unsigned k0 = 0, kend = 0, k1 = 0;
         if (real) {
             st = E1[c - 1];
-            k0 = c * S;
-            k1 = min(m, (c + 1) * S);
+            k0 = own_begin(c, S, m);
+            kend = own_end(c, S, m, nch);
+            k1 = min(kend, k0 + P2_LANE_STEPS);
         }
         unsigned steps = 0;
         const bool mg = lane_run<true>(kp, base, ring, qout, k0, k1, k0, st, sm, ctrl, &steps);
         if (real) {
-            merged[c] = mg;
             atomicAdd(&ctrl->pass2_steps, (unsigned long long)steps);
+            merged[c] = mg;
             if (!mg) {
-                E2[c] = st;
-                atomicAdd(&ctrl->unmerged, 1u);
-                atomicAdd(&ctrl->unmerged_total, 1ull);
-                atomicOr(&unm_bits[c >> 5], 1u << (c & 31));
+                if (k1 < kend) {  // continue in k_det_pass2w from the state at k1
+                    E2[c] = st;
+                    p2_ids[atomicAdd(&ctrl->p2_count, 1u)] = c;
+                } else {
+                    p2_unmerged(ctrl, st, c, E2, unm_bits);
+                }
             }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_det_pass2w(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *qout,
+             DetState *E2, unsigned char *merged, unsigned *unm_bits, const unsigned *p2_ids)
+{
+    PDL_ENTRY();
+    const unsigned long long base = ctrl->base;
+    const unsigned m = ctrl->m, S = ctrl->S, n = ctrl->p2_count, nch = ctrl->nchunks;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned warps = gridDim.x * (blockDim.x >> 5);
+    for (unsigned i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const unsigned c = p2_ids[i];
+        DetState st = E2[c];
+        const unsigned k0 = own_begin(c, S, m) + P2_LANE_STEPS, k1 = own_end(c, S, m, nch);
+        unsigned steps = 0;
+        const bool mg = group_run<32, true>(kp, base, ring, qout, k0, k1, st, &ctrl->error, &steps);
+        if (lane == 0) {
+            atomicAdd(&ctrl->pass2_steps, (unsigned long long)steps);
+            if (mg) merged[c] = 1;
+            else p2_unmerged(ctrl, st, c, E2, unm_bits);
         }
     }
 }
@@ -802,7 +880,7 @@ __global__ void k_det_fix(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *q
             if (same_state(E1[c - 1], exit_c)) { have_exit = false; continue; }
             DetState st = exit_c;
             unsigned steps = 0;
-            const bool mg = group_run<32, true>(kp, base, ring, qout, c * S, min(m, (c + 1) * S), st,
+            const bool mg = group_run<32, true>(kp, base, ring, qout, own_begin(c, S, m), own_end(c, S, m, nch), st,
                                            &ctrl->error, &steps);
             if (lane == 0) ctrl->fix_steps += steps;
             exit_c = mg ? (merged[c] ? E1[c] : E2[c]) : st;
@@ -833,7 +911,7 @@ cudaError_t launch_det_counts(const KParams &kp, const Bufs &b, cudaStream_t s, 
     if (cudaError_t e_ = launch_pdl(k_det_hist, grid_for(2), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows))
         return e_;
     if (cudaError_t e_ = launch_pdl(k_det_init, grid_for(8), 256, 0, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
-                                    b.E0))
+                                    b.E0, b.qout))
         return e_;
     return cudaGetLastError();
 }
@@ -861,10 +939,13 @@ cudaError_t launch_det_pass1(const KParams &kp, const Bufs &b, cudaStream_t s, u
 
 cudaError_t launch_det_pass2(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)
 {
-    nl += 1;
+    nl += 2;
     if (cudaError_t e = lane_smem_attr()) return e;
     if (cudaError_t e_ = launch_pdl(k_det_pass2, grid_for(2), 32 * LR_WARPS, sizeof(LaneSmem) * LR_WARPS, s, kp,
-                                    b.ctrl, b.ring4, b.qout, b.E1, b.E2, b.merged, b.unm_bits))
+                                    b.ctrl, b.ring4, b.qout, b.E1, b.E2, b.merged, b.unm_bits, b.p2_ids))
+        return e_;
+    if (cudaError_t e_ = launch_pdl(k_det_pass2w, grid_for(8), 256, 0, s, kp, b.ctrl, b.ring4, b.qout, b.E2,
+                                    b.merged, b.unm_bits, b.p2_ids))
         return e_;
     return cudaGetLastError();
 }

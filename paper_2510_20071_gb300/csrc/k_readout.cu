@@ -75,6 +75,7 @@ __global__ void k_commit(Ctrl *ctrl, unsigned long long *dec_status, size_t n_st
         ctrl->blur_ticket = 0;
         ctrl->sel_ticket = 0;
         ctrl->walk_ticket = 0;
+        ctrl->p2_count = 0;
         ctrl->batch_no += 1;
         // the carry slot just consumed becomes the output slot of the next decode
         ctrl->carry_n[1 - next_carry_slot] = 0;
@@ -99,6 +100,7 @@ __global__ void k_init(KParams kp, Ctrl *ctrl)
     ctrl->fixups = 0;
     ctrl->unmerged_total = ctrl->pass2_steps = ctrl->fix_steps = ctrl->s1_blurs = 0;
     ctrl->big_pops = ctrl->ring_misses = 0;
+    ctrl->p2_count = 0;
     ctrl->batch_no = 1;
     ctrl->h_prev = 0;
     ctrl->nblur = 0;
