@@ -73,7 +73,7 @@ __device__ __forceinline__ unsigned bw_scan(unsigned v, unsigned *s_warp, unsign
 }
 
 template <bool kLinks, bool kS1>
-__global__ void __launch_bounds__(BW_THREADS)
+__global__ void __launch_bounds__(BW_THREADS, 2)
 k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
 {
     PDL_ENTRY();
@@ -296,11 +296,11 @@ cudaError_t launch_walk(const KParams &kp, const Bufs &b, const unsigned long lo
     }
     cudaError_t e;
     if (kp.spatial && kp.blur_mode == 0)
-        e = launch_pdl(k_bwalk<true, true>, grid_for(1), BW_THREADS, smem, s, kp, b, sorted);
+        e = launch_pdl(k_bwalk<true, true>, grid_for(2), BW_THREADS, smem, s, kp, b, sorted);
     else if (kp.spatial)
-        e = launch_pdl(k_bwalk<true, false>, grid_for(1), BW_THREADS, smem, s, kp, b, sorted);
+        e = launch_pdl(k_bwalk<true, false>, grid_for(2), BW_THREADS, smem, s, kp, b, sorted);
     else
-        e = launch_pdl(k_bwalk<false, false>, grid_for(1), BW_THREADS, smem, s, kp, b, sorted);
+        e = launch_pdl(k_bwalk<false, false>, grid_for(2), BW_THREADS, smem, s, kp, b, sorted);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -168,6 +168,21 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
     }
 }
 
+// q_targ = max(q_min, min(q_max, floor(X / Y))) (Eq. 20 as the ratio X / Y, Y = 0 when
+// N_ap = 0): a single-precision quotient, then corrected with exact 64-bit products so
+// that the result is the exact floor.
+__device__ __forceinline__ unsigned q_target(const KParams &kp, unsigned long long X, unsigned Y)
+{
+    if (Y == 0) return max(kp.q_min, kp.q_max);
+    // X as a float from its 32-bit halves (a 64-bit conversion is slow)
+    const float xf = fmaf(__uint2float_rn((unsigned)(X >> 32)), 4294967296.0f, __uint2float_rn((unsigned)X));
+    const float r = __fdividef(xf, __uint2float_rn(Y));
+    unsigned t = r >= (float)kp.q_max ? kp.q_max + 1u : (unsigned)r;
+    while (t > 0 && (unsigned long long)t * Y > X) --t;                     // t <= X / Y
+    while (t <= kp.q_max && (unsigned long long)(t + 1) * Y <= X) ++t;      // t = floor, or above q_max
+    return max(kp.q_min, min(kp.q_max, t));
+}
+
 // Speculative start of chunk c >= 1, one warp per chunk.
 // (1) The window: scan the aligned windows g = 1..DET_G ending at cS, 256 distances per
 //     round (8 per lane, one 16-byte load per row and lane, prefix sums by shuffles), up
@@ -307,8 +322,7 @@ k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short
         unsigned nap = snp + (d.x > ql ? 1u : 0u);
         unsigned nat = snt + (d.y > ql ? 1u : 0u);
         const unsigned long long q = ql + 1;
-        unsigned long long thr = Y == 0 ? kp.q_max : min((unsigned long long)kp.q_max, X / Y);
-        thr = max(thr, (unsigned long long)kp.q_min);
+        const unsigned thr = q_target(kp, X, (unsigned)Y);
         const unsigned P = q > thr ? (unsigned)(q - thr) : 0u;
         unsigned offp = 0, offt = 0;
 #pragma unroll 4
@@ -482,21 +496,6 @@ struct LaneSmem {
     uint2 pop[32][LR_R + 1];
     unsigned ref[2][32][LR_B + 1];
 };
-
-// q_targ = max(q_min, min(q_max, floor(X / Y))) (Eq. 20 as the ratio X / Y, Y = 0 when
-// N_ap = 0): a single-precision quotient, then corrected with exact 64-bit products so
-// that the result is the exact floor.
-__device__ __forceinline__ unsigned q_target(const KParams &kp, unsigned long long X, unsigned Y)
-{
-    if (Y == 0) return max(kp.q_min, kp.q_max);
-    // X as a float from its 32-bit halves (a 64-bit conversion is slow)
-    const float xf = fmaf(__uint2float_rn((unsigned)(X >> 32)), 4294967296.0f, __uint2float_rn((unsigned)X));
-    const float r = __fdividef(xf, __uint2float_rn(Y));
-    unsigned t = r >= (float)kp.q_max ? kp.q_max + 1u : (unsigned)r;
-    while (t > 0 && (unsigned long long)t * Y > X) --t;                     // t <= X / Y
-    while (t <= kp.q_max && (unsigned long long)(t + 1) * Y <= X) ++t;      // t = floor, or above q_max
-    return max(kp.q_min, min(kp.q_max, t));
-}
 
 __device__ __forceinline__ void cp_async8(void *dst, const void *src)
 {
@@ -851,6 +850,11 @@ __global__ void k_det_fix(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *q
     } else {
         if (lane == 0) ctrl->fixups += 1;
         const unsigned nwords = (nch + 31) / 32;
+        // the bitmap in shared memory first: all its loads in flight at once
+        __shared__ unsigned s_bits[DET_MAX_CHUNKS / 32 + 1];
+#pragma unroll 8
+        for (unsigned wi = lane; wi < nwords; wi += 32) s_bits[wi] = unm_bits[wi];
+        __syncwarp();
         unsigned c = 1;  // chunks < c are exact and chunk c's pass-2 entry E1[c-1] is exact
         DetState exit_c;
         bool have_exit = false;  // exit of chunk c-1 if it differs from E1[c-1]
@@ -860,7 +864,7 @@ __global__ void k_det_fix(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *q
                 unsigned w = c >> 5, found = nch;
                 for (unsigned wb = w; wb < nwords && found == nch; wb += 32) {
                     const unsigned wi = wb + lane;
-                    unsigned bits = wi < nwords ? unm_bits[wi] : 0u;
+                    unsigned bits = wi < nwords ? s_bits[wi] : 0u;
                     if (wi == w) bits &= ~0u << (c & 31);
                     const unsigned any = __ballot_sync(0xFFFFFFFFu, bits != 0u);
                     if (any) {

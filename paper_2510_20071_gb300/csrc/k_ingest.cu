@@ -90,16 +90,34 @@ __device__ __forceinline__ unsigned long long dpack(unsigned flag, DAgg a)
     return ((unsigned long long)flag << 62) | ((unsigned long long)a.s << 31) | a.c;
 }
 
-__device__ __forceinline__ int4 fetch_rec(const SegTable &T, const int4 *const *s_ptr,
-                                          const unsigned *s_start, unsigned carry_n, unsigned pos)
+// Segment holding record pos (pos >= carry_n): the last segment starting at or before it.
+__device__ __forceinline__ int seg_of(const SegTable &T, const unsigned *s_start, unsigned pos)
 {
-    if (pos < carry_n) return __ldg(T.carry + pos);
     int lo = 0, hi = (int)T.nseg - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (s_start[mid] <= pos) lo = mid; else hi = mid - 1;
     }
-    return __ldg(s_ptr[lo] + (pos - s_start[lo]));
+    return lo;
+}
+
+__device__ __forceinline__ int4 fetch_rec(const SegTable &T, const int4 *const *s_ptr,
+                                          const unsigned *s_start, unsigned carry_n, unsigned pos)
+{
+    if (pos < carry_n) return __ldg(T.carry + pos);
+    const int sg = seg_of(T, s_start, pos);
+    return __ldg(s_ptr[sg] + (pos - s_start[sg]));
+}
+
+// The same, starting the segment search from the segment of an earlier record of the
+// tile (a tile spans one or two packets almost always).
+__device__ __forceinline__ int4 fetch_rec_from(const SegTable &T, const int4 *const *s_ptr,
+                                               const unsigned *s_start, unsigned carry_n, unsigned pos,
+                                               int sg)
+{
+    if (pos < carry_n) return __ldg(T.carry + pos);
+    while (sg + 1 < (int)T.nseg && s_start[sg + 1] <= pos) ++sg;
+    return __ldg(s_ptr[sg] + (pos - s_start[sg]));
 }
 
 __global__ void __launch_bounds__(DEC_THREADS)
@@ -142,10 +160,11 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
 
         // coalesced 16-byte loads, all in flight before any is used; classify each record
         int4 ev[DEC_PER_THREAD];
+        const int sg0 = T.nseg ? seg_of(T, s_start, max(pos0, carry_n)) : 0;
 #pragma unroll
         for (int i = 0; i < DEC_PER_THREAD; ++i) {
             const unsigned pos = pos0 + i * DEC_THREADS + threadIdx.x;
-            ev[i] = pos < total ? fetch_rec(T, s_ptr, s_start, carry_n, pos) : make_int4(0, 0, 0, 0);
+            ev[i] = pos < total ? fetch_rec_from(T, s_ptr, s_start, carry_n, pos, sg0) : make_int4(0, 0, 0, 0);
         }
         unsigned vloc = S_NONE;
 #pragma unroll
@@ -282,10 +301,21 @@ k_sort_hist(Ctrl *ctrl, const unsigned long long *rec, unsigned passes, unsigned
     __syncthreads();
     const unsigned m = ctrl->m;
     const unsigned dmask = (1u << dbits) - 1u;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        const unsigned key = (unsigned)(rec[i] >> 32) >> lb;
-        for (unsigned p = 0; p < passes; ++p) atomicAdd(&h[p][(key >> (dbits * p)) & dmask], 1u);
-        atomicAdd(&hb[key], 1u);
+    // eight records per thread and round, all loads in flight before the counting
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += 8 * stride) {
+        unsigned key[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const unsigned i = i0 + u * stride;
+            key[u] = i < m ? (unsigned)(rec[i] >> 32) >> lb : 0xFFFFFFFFu;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (key[u] == 0xFFFFFFFFu) continue;
+            for (unsigned p = 0; p < passes; ++p) atomicAdd(&h[p][(key[u] >> (dbits * p)) & dmask], 1u);
+            atomicAdd(&hb[key[u]], 1u);
+        }
     }
     __syncthreads();
     for (unsigned p = 0; p < passes; ++p)
@@ -387,11 +417,18 @@ k_sort_pass(Ctrl *ctrl, const unsigned long long *in, unsigned long long *out, u
         if (tile >= ntiles) break;
         const unsigned base = tile * SORT_TILE;
         const unsigned n_here = min((unsigned)SORT_TILE, m - base);
-#pragma unroll 4
+        // asynchronous copies: the whole tile in flight at once
+#pragma unroll
         for (int i = 0; i < SORT_PER_THREAD; ++i) {
             const unsigned r = i * SORT_THREADS + threadIdx.x;
-            S.key[r] = r < n_here ? in[base + r] : ~0ull;
+            if (r < n_here) {
+                const unsigned d = (unsigned)__cvta_generic_to_shared(&S.key[r]);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(in + base + r) : "memory");
+            } else {
+                S.key[r] = ~0ull;
+            }
         }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
         __syncthreads();
         // stable rank within (warp range, digit): warp w owns records [w*512, w*512+512)
         for (int q = 0; q < 16; ++q) {
