@@ -29,6 +29,10 @@
 
 namespace fibar {
 
+// Distances stored in the window table: 1..DET_GT.  S is sized so that the regulator's
+// window is about DET_G / 2 chunks at the batch start; the table reaches 1.5 times that.
+constexpr unsigned DET_GT = 767;
+
 struct Geo {
     unsigned long long base;
     unsigned m, S, nchunks, Gold;
@@ -48,7 +52,7 @@ __device__ __forceinline__ Geo geometry(const KParams &kp, const Ctrl *ctrl)
     g.S = (unsigned)max((unsigned long long)CHUNK, S);
     g.nchunks = (g.m + g.S - 1) / g.S;
     const unsigned long long old_chunks = (g.base + g.S - 1) / g.S;
-    g.Gold = (unsigned)min((unsigned long long)DET_G, old_chunks);
+    g.Gold = (unsigned)min((unsigned long long)DET_GT, old_chunks);
     return g;
 }
 
@@ -75,7 +79,7 @@ __device__ __forceinline__ long long chunk_of(long long x, unsigned S, unsigned 
     return (x + (long long)Gold * S) / S - Gold;
 }
 
-// Suffix histograms by target chunk: for a batch chunk c and distance g = 1..DET_G,
+// Suffix histograms by target chunk: for a batch chunk c and distance g = 1..DET_GT,
 //   Mt[t][c][g] = #{j in chunk c-g : next(j) >= cS}          (t = 0 pixels, 1 tiles)
 // i.e. the events of chunk c-g still last of their pixel / tile at the start of chunk c
 // (source chunks reach back to -Gold; entries of older sources are never written and
@@ -89,6 +93,7 @@ __device__ __forceinline__ long long chunk_of(long long x, unsigned S, unsigned 
 constexpr int HB_CHUNKS = 16;
 constexpr int HB_PITCH = 1058;  // >= 1024 + 32 bins with padding, = 2 (mod 32)
 constexpr int MT_PITCH = DET_G + 1;  // u16 per target row (2 KB: 16-byte aligned rows)
+
 
 __device__ __forceinline__ int hb_slot(int d) { return d + (d >> 5); }
 
@@ -110,21 +115,21 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
     for (unsigned unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
         const int t = unit & 1;
         const long long c_lo = (long long)((unit >> 1) * HB_CHUNKS) - (long long)g.Gold;  // first source chunk
-        unsigned *hw = &H.h[0][0];
-        for (unsigned i = tid; i < HB_CHUNKS * HB_PITCH; i += 256) hw[i] = 0;
+        uint4 *hw = reinterpret_cast<uint4 *>(&H.h[0][0]);
+        for (unsigned i = tid; i < HB_CHUNKS * HB_PITCH / 4; i += 256) hw[i] = make_uint4(0u, 0u, 0u, 0u);
         __syncthreads();
         // histogram of the chunk distance to the next event of the same pixel / tile
         const long long j_lo = c_lo * g.S;
         const unsigned n_hi = (unsigned)min((long long)HB_CHUNKS * g.S, (long long)g.m - j_lo);
         const unsigned n_lo = (unsigned)max(0ll, lo_exist - j_lo);
-        const unsigned long long lim = (unsigned long long)DET_G * g.S;  // offsets from here on: distance DET_G
+        const unsigned long long lim = (unsigned long long)DET_GT * g.S;  // offsets from here on: distance DET_GT
         for (unsigned i = n_lo + tid; i < n_hi; i += 256) {
             const unsigned long long j = g.base + (unsigned long long)(j_lo + i);
             const uint2 n = nxt_of(ring, j & kp.ring_mask);
             const unsigned nv = t ? n.y : n.x;
             const unsigned cc = i / g.S, r = i - cc * g.S;
             const unsigned long long rel = (unsigned long long)r + nv;  // from the start of chunk cc
-            const unsigned d = (nv == SAT || rel >= lim) ? (unsigned)DET_G
+            const unsigned d = (nv == SAT || rel >= lim) ? DET_GT
                              : (lim <= 0xFFFFFFFFull ? (unsigned)rel / g.S : (unsigned)(rel / g.S));
             atomicAdd(&H.h[cc][hb_slot((int)d)], 1u);
         }
@@ -151,11 +156,11 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
         // target row c_lo + D receives distances D-15 .. D from the block's sources;
         // HB_CHUNKS threads write one row's run
         unsigned short *base_t = Mt + (size_t)t * mt_rows * MT_PITCH;
-        for (unsigned i = tid; i < (unsigned)(HB_CHUNKS - 1 + DET_G) * HB_CHUNKS; i += 256) {
+        for (unsigned i = tid; i < (unsigned)(HB_CHUNKS - 1 + DET_GT) * HB_CHUNKS; i += 256) {
             const int D = 1 + (int)(i / HB_CHUNKS), u = (int)(i % HB_CHUNKS);
             const int cc = HB_CHUNKS - 1 - u, d = D - cc;
             const long long ct = c_lo + D;  // target chunk
-            if (d >= 1 && d <= DET_G && ct >= 1 && ct < (long long)g.nchunks)
+            if (d >= 1 && d <= (int)DET_GT && ct >= 1 && ct < (long long)g.nchunks)
                 base_t[(size_t)ct * MT_PITCH + d] = (unsigned short)H.h[cc][hb_slot(d)];
         }
         __syncthreads();
@@ -184,7 +189,7 @@ __device__ __forceinline__ unsigned q_target(const KParams &kp, unsigned long lo
 }
 
 // Speculative start of chunk c >= 1, one warp per chunk.
-// (1) The window: scan the aligned windows g = 1..DET_G ending at cS, 256 distances per
+// (1) The window: scan the aligned windows g = 1..DET_GT ending at cS, 256 distances per
 //     round (8 per lane, one 16-byte load per row and lane, prefix sums by shuffles), up
 //     to the first one that the regulator would shrink at the next event (Eq. 20); then,
 //     inside the chunk where that window starts, the shortest window, to the event, that
@@ -213,10 +218,10 @@ k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short
     for (unsigned c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) + 1; c < nch; c += warps_total) {
         const unsigned short *rp = Mt + (size_t)c * MT_PITCH;
         const unsigned short *rt = Mt + (mt_rows + c) * MT_PITCH;
-        const unsigned gmax = min((unsigned)DET_G, c + Gold);  // sources that exist in the table
+        const unsigned gmax = min(DET_GT, c + Gold);  // sources that exist in the table
         const unsigned long long reach = (unsigned long long)c * S + base;  // events before the chunk
         unsigned carry_p = 0, carry_t = 0, found = 0, snp = 0, snt = 0, fp1 = 0, ft1 = 0;
-        for (unsigned g0 = 0; g0 <= DET_G && !found; g0 += 256) {
+        for (unsigned g0 = 0; g0 <= DET_GT && !found; g0 += 256) {
             const uint4 wp = *reinterpret_cast<const uint4 *>(rp + g0 + 8 * lane);
             const uint4 wt = *reinterpret_cast<const uint4 *>(rt + g0 + 8 * lane);
             const unsigned xp[4] = {wp.x, wp.y, wp.z, wp.w}, xt[4] = {wt.x, wt.y, wt.z, wt.w};
@@ -245,7 +250,7 @@ k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short
                 const unsigned gg = g0 + 8 * lane + u;
                 const unsigned long long np = op + pp[u], nt = ot + pt[u];
                 const unsigned long long L = min((unsigned long long)gg * S, reach), q = L + 1;
-                if (gg >= 1 && gg <= DET_G && np > 0 && q > kp.q_min &&
+                if (gg >= 1 && gg <= DET_GT && np > 0 && q > kp.q_min &&
                     (q > kp.q_max || q * kp.den * np > L * kp.numA * nt))
                     mine = gg;
             }
@@ -308,10 +313,10 @@ k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short
             }
             h = j0 + best;  // y = 0 always shrinks (the aligned window of `found` chunks)
         } else {
-            // no shrinking window within DET_G chunks (then all of them), or the window
+            // no shrinking window within DET_GT chunks (then all of them), or the window
             // reaches back to the stream start (then the whole history): the counts
             // accumulated over the scanned distances
-            h = max(k0 - (long long)(found ? found : DET_G) * S, -(long long)base);
+            h = max(k0 - (long long)(found ? found : DET_GT) * S, -(long long)base);
             snp = carry_p;
             snt = carry_t;
         }

@@ -219,6 +219,7 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
                 unsigned spins = 0;
                 while ((v >> 62) == 0ull) {
                     if (++spins > SPIN_LIMIT) { atomicOr(&ctrl->error, ERR_DEC_WAIT); break; }
+                    __nanosleep(64);  // back off: the polls would compete with the loads awaited
                     v = ld_relaxed(&status[tp]);
                 }
                 acc = dcombine(acc, DAgg{(unsigned)(v >> 31) & 0x7FFFFFFFu, (unsigned)v & 0x7FFFFFFFu});
@@ -253,16 +254,30 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
         const unsigned pre_s = s_pre_s, pre_c = s_pre_c;
         if (pre_s == S_NONE) {
             const unsigned long long base = ctrl->base;
-            unsigned k = pre_c + excl;
+            // compact the kept records in shared memory (each thread moves its own, in
+            // order, after all have read theirs), then write them out coalesced
+            unsigned my_info[DEC_PER_THREAD], my_pix[DEC_PER_THREAD];
+#pragma unroll
+            for (int j = 0; j < DEC_PER_THREAD; ++j) {
+                my_info[j] = s_info[threadIdx.x * DEC_PER_THREAD + j];
+                my_pix[j] = s_pix[threadIdx.x * DEC_PER_THREAD + j];
+            }
+            __syncthreads();
+            unsigned li = excl;
 #pragma unroll
             for (int j = 0; j < DEC_PER_THREAD; ++j) {
                 if (keep >> j & 1u) {
-                    const unsigned info = s_info[threadIdx.x * DEC_PER_THREAD + j];
-                    rec_out[k] = ((unsigned long long)((info >> 3) & 0x0FFFFFFFu) << 32) |
-                                 ((unsigned long long)k << 3) | (info & 7u);
-                    if (ring_pix) ring_pix[(base + k) & kp.ring_mask] = s_pix[threadIdx.x * DEC_PER_THREAD + j];
-                    ++k;
+                    s_info[li] = my_info[j];
+                    s_pix[li] = my_pix[j];
+                    ++li;
                 }
+            }
+            __syncthreads();
+            for (unsigned i = threadIdx.x; i < tile_cnt; i += DEC_THREADS) {
+                const unsigned k = pre_c + i, info = s_info[i];
+                rec_out[k] = ((unsigned long long)((info >> 3) & 0x0FFFFFFFu) << 32) |
+                             ((unsigned long long)k << 3) | (info & 7u);
+                if (ring_pix) ring_pix[(base + k) & kp.ring_mask] = s_pix[i];
             }
             if (threadIdx.x == 0 && s_drop) atomicAdd(&ctrl->dropped, (unsigned long long)s_drop);
             if (vfirst != S_NONE) {
@@ -378,6 +393,7 @@ __device__ __forceinline__ void wait_flag(const unsigned *flag, unsigned epoch, 
     unsigned spins = 0;
     while (ld_acq_u32(flag) != epoch) {
         if (++spins > SPIN_LIMIT) { atomicOr(&ctrl->error, ERR_SORT_WAIT); return; }
+        __nanosleep(64);
     }
 }
 

@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_s1_select(KParams kp, Bufs b)
             unsigned spins = 0;
             while ((v >> 32) != (tag >> 32) || ((v >> 30) & 3ull) == 0ull) {
                 if (++spins > SPIN_LIMIT) { atomicOr(&ctrl->error, ERR_SORT_WAIT); break; }
+                __nanosleep(64);
                 v = ld_acquire_u64b(&st[tp]);
             }
             part += (unsigned)v & 0x3FFFFFFFu;
