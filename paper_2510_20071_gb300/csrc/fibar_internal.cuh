@@ -25,6 +25,7 @@ namespace fibar {
 
 constexpr uint32_t SAT = 0xFFFFFFFFu;          // saturated / absent distance
 constexpr unsigned long long NONE64 = ~0ull;   // "no event yet"
+constexpr unsigned TMA_SPIN_LIMIT = 1u << 16;    // bounded waits on bulk-copy barriers (each try blocks a while)
 constexpr int DEC_THREADS = 256;
 constexpr int DEC_PER_THREAD = 16;
 constexpr int DEC_TILE = DEC_THREADS * DEC_PER_THREAD;   // records per decode tile

@@ -546,7 +546,8 @@ __device__ bool lane_run(const KParams &kp, unsigned long long base, const uint4
 #pragma unroll
     for (int o = 16; o; o >>= 1) span = max(span, __shfl_xor_sync(0xFFFFFFFFu, span, o));
     const unsigned nblk = (span + LR_B - 1) / LR_B;
-    // pop links [h, v) have landed, [v, f) are in flight
+    // pop links [h, v) have landed, [v, f) are in flight; a short run stages fewer
+    const int ring_fill = (int)min((unsigned)LR_R, 4u * span + 16u);
     int f = h, v = h;
     // copy the pop links of events [e, e + n) into the lane's ring (n <= LR_R), walking
     // source and destination pointers through at most two wraps of each ring
@@ -564,9 +565,9 @@ __device__ bool lane_run(const KParams &kp, unsigned long long base, const uint4
     };
     auto fill_pop = [&]() {
         if (f < h) f = h;
-        const int want = active ? h + LR_R - f : 0;
+        const int want = active ? h + ring_fill - f : 0;
         copy_links(f, want);
-        if (want > 0) f = h + LR_R;
+        if (want > 0) f = h + ring_fill;
     };
     auto stage = [&](int buf, unsigned b) {
         const unsigned kb = k0 + b * LR_B;
@@ -752,7 +753,7 @@ k_det_pass1(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *qout,
 // need tens: the lane stage (k_det_pass2) runs every chunk for at most P2_LANE_STEPS
 // steps and lists the ones still running, which k_det_pass2w continues one warp per
 // chunk (a step costs a warp there, but the chains of the slow chunks run side by side).
-constexpr unsigned P2_LANE_STEPS = LR_B;
+constexpr unsigned P2_LANE_STEPS = 4;
 
 __device__ __forceinline__ void p2_unmerged(Ctrl *ctrl, const DetState &st, unsigned c, DetState *E2,
                                             unsigned *unm_bits)

@@ -39,6 +39,49 @@ __device__ __forceinline__ void st_release(unsigned long long *p, unsigned long 
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// Bulk asynchronous copies (TMA) into shared memory, completing on an mbarrier.
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned phase)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(phase)
+                 : "memory");
+    return ok != 0;
+}
+// Bounded wait for an mbarrier phase; false (and the error flag) if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned phase, Ctrl *ctrl, unsigned flag)
+{
+    unsigned spins = 0;
+    while (!mbar_try_wait(bar, phase)) {
+        if (++spins > TMA_SPIN_LIMIT) {
+            atomicOr(&ctrl->error, flag);
+            return false;
+        }
+    }
+    return true;
+}
+
 // Block-wide exclusive scan of one value per thread (blockDim.x == 256).
 __device__ __forceinline__ unsigned block_excl_scan256(unsigned v, unsigned *s_warp, unsigned *total)
 {
@@ -125,6 +168,8 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
          unsigned *ring_pix)
 {
     PDL_ENTRY();
+    extern __shared__ __align__(128) int4 s_rec[];  // the tile's records (DEC_TILE)
+    __shared__ __align__(8) unsigned long long s_bar;
     __shared__ unsigned s_start[MAXSEG + 1];
     __shared__ const int4 *s_ptr[MAXSEG];
     __shared__ unsigned s_info[DEC_TILE];
@@ -142,10 +187,13 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
             acc += T.n[i];
         }
         s_start[T.nseg] = acc;
+        mbar_init(&s_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     const unsigned total = s_start[T.nseg];
     const unsigned ntiles = (total + DEC_TILE - 1) / DEC_TILE;
+    unsigned phase = 0;
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -158,14 +206,29 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
         if (tile >= ntiles) break;
         const unsigned pos0 = tile * DEC_TILE;
 
-        // coalesced 16-byte loads, all in flight before any is used; classify each record
-        int4 ev[DEC_PER_THREAD];
-        const int sg0 = T.nseg ? seg_of(T, s_start, max(pos0, carry_n)) : 0;
-#pragma unroll
-        for (int i = 0; i < DEC_PER_THREAD; ++i) {
-            const unsigned pos = pos0 + i * DEC_THREADS + threadIdx.x;
-            ev[i] = pos < total ? fetch_rec_from(T, s_ptr, s_start, carry_n, pos, sg0) : make_int4(0, 0, 0, 0);
+        // the tile's records into shared memory with bulk copies (TMA), one per contiguous
+        // piece of the carry buffer and the packets (16-byte records, 16-byte aligned)
+        const unsigned pos1 = min(pos0 + DEC_TILE, total);
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(&s_bar, (pos1 - pos0) * 16u);
+            unsigned p = pos0;
+            if (p < carry_n) {
+                const unsigned e = min(pos1, carry_n);
+                bulk_g2s(s_rec, T.carry + p, (e - p) * 16u, &s_bar);
+                p = e;
+            }
+            if (p < pos1) {
+                int sg = seg_of(T, s_start, p);
+                while (p < pos1) {
+                    while (sg + 1 < (int)T.nseg && s_start[sg + 1] <= p) ++sg;
+                    const unsigned e = min(pos1, s_start[sg + 1]);
+                    bulk_g2s(s_rec + (p - pos0), s_ptr[sg] + (p - s_start[sg]), (e - p) * 16u, &s_bar);
+                    p = e;
+                }
+            }
         }
+        if (!mbar_wait(&s_bar, phase, ctrl, ERR_DEC_WAIT)) mbar_wait(&s_bar, phase, ctrl, ERR_DEC_WAIT);
+        phase ^= 1u;
         unsigned vloc = S_NONE;
 #pragma unroll
         for (int i = 0; i < DEC_PER_THREAD; ++i) {
@@ -173,7 +236,7 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
             const unsigned pos = pos0 + r;
             unsigned info = NOREC;
             if (pos < total) {
-                const int4 e = ev[i];
+                const int4 e = s_rec[r];
                 const unsigned x = (unsigned)e.x & 0xFFFFu, y = (unsigned)e.x >> 16;
                 const int p = (int)(signed char)(e.y & 0xFF);
                 const unsigned long long t =
@@ -285,14 +348,14 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
                 for (int i = 0; i < DEC_PER_THREAD; ++i) {
                     const unsigned r = i * DEC_THREADS + threadIdx.x;
                     const unsigned pos = pos0 + r;
-                    if (r >= vfirst && pos < total)
-                        T.carry_out[pos - s] = fetch_rec(T, s_ptr, s_start, carry_n, pos);
+                    if (r >= vfirst && pos < total) T.carry_out[pos - s] = s_rec[r];
                 }
             }
         } else {
             for (int i = 0; i < DEC_PER_THREAD; ++i) {
-                const unsigned pos = pos0 + i * DEC_THREADS + threadIdx.x;
-                if (pos < total) T.carry_out[pos - pre_s] = fetch_rec(T, s_ptr, s_start, carry_n, pos);
+                const unsigned r = i * DEC_THREADS + threadIdx.x;
+                const unsigned pos = pos0 + r;
+                if (pos < total) T.carry_out[pos - pre_s] = s_rec[r];
             }
         }
         __syncthreads();
@@ -581,7 +644,13 @@ cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, c
                           unsigned long long &nl)
 {
     nl += 1;
-    if (cudaError_t e_ = launch_pdl(k_decode, grid_for(2), DEC_THREADS, 0, s, kp, t, b.ctrl, b.dec_status, b.rec[0],
+    static bool attr_set = false;
+    const int smem = DEC_TILE * (int)sizeof(int4);
+    if (!attr_set) {
+        if (cudaError_t e = cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) return e;
+        attr_set = true;
+    }
+    if (cudaError_t e_ = launch_pdl(k_decode, grid_for(2), DEC_THREADS, smem, s, kp, t, b.ctrl, b.dec_status, b.rec[0],
                                     kp.spatial ? b.ring_pix : nullptr)) return e_;
     return cudaGetLastError();
 }
