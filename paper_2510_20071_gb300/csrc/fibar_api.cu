@@ -51,7 +51,7 @@ void free_all(fibar_t *h)
     Bufs &b = h->b;
     void *ptrs[] = {b.ctrl, b.pbar, b.L, b.last_pix, b.last_tile, b.staging, b.carry[0], b.carry[1],
                     b.dec_status, b.rec[0], b.rec[1], b.sort_hist, b.sort_base, b.sort_rows, b.sort_rowflag, b.sort_gtot, b.sort_gflag, b.sort_gcount,
-                    b.qout, b.ring4, b.ring_pix, b.bucket_start, b.bucket_cnt, b.dMt, b.E0, b.E1, b.E2, b.p2_ids, b.merged, b.unm_bits,
+                    b.qout, b.ring4, b.ring_pix, b.bucket_start, b.bucket_cnt, b.dMt, b.det_base, b.E0, b.E1, b.E2, b.p2_ids, b.merged, b.unm_bits,
                     b.out_staging, b.dbg_cnt, b.plist, b.plnb, b.epos, b.lbl, b.s1_info, b.s1_linit,
                     b.popk, b.blur_ord, b.bk, b.bpix, b.bj, b.bD, b.bflag, b.sel_status, b.beta_pow};
     for (void *p : ptrs)
@@ -179,7 +179,8 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
         ALLOC(b.qout, maxp);
         ALLOC(b.ring4, h->R);
         ALLOC(b.ring_pix, h->R);
-        ALLOC(b.dMt, 2 * b.mt_rows * (DET_G + 1));
+        ALLOC(b.dMt, 2 * b.mt_rows * 256);
+        ALLOC(b.det_base, 2 * b.mt_rows);
         ALLOC(b.E0, b.max_chunks);
         ALLOC(b.E1, b.max_chunks);
         ALLOC(b.E2, b.max_chunks);
@@ -228,6 +229,7 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     if (e == cudaSuccess) e = cudaMemsetAsync(b.bucket_cnt, 0, (size_t)kp.nbuckets * 4, s);
     if (e == cudaSuccess && p.spatial_filter) e = cudaMemsetAsync(b.ring_pix, 0, h->R * 4, s);
     if (e == cudaSuccess && b.unm_bits) e = cudaMemsetAsync(b.unm_bits, 0, (b.max_chunks / 32 + 2) * 4, s);
+    if (e == cudaSuccess && b.det_base) e = cudaMemsetAsync(b.det_base, 0, 2 * b.mt_rows * 4, s);
     if (e == cudaSuccess && b.s1_info) e = cudaMemsetAsync(b.s1_info, 0, npix * sizeof(int4), s);
     if (e == cudaSuccess && b.bflag) e = cudaMemsetAsync(b.bflag, 0, b.max_pops * 4, s);
     if (e == cudaSuccess && b.sel_status) e = cudaMemsetAsync(b.sel_status, 0, b.max_sel_tiles * 8, s);

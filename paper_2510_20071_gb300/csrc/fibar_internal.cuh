@@ -73,7 +73,7 @@ struct Ctrl {
     unsigned int error;
     unsigned int unmerged;       // chunks whose second detector pass did not merge
     unsigned int fixups;         // batches that needed the serial detector fixup
-    unsigned int S, nchunks, G, Gold;
+    unsigned int S, nchunks, g_lo, Gold;  // detector geometry of the batch (k_det_hist)
     unsigned int batch_no;       // read-outs/flushes committed (epoch of S1 flags)
     DetState det;                // detector state at the batch start (h global)
     long long h_prev;            // global h before the current batch (set by the fixup)
@@ -134,7 +134,8 @@ struct Bufs {
     unsigned int *bucket_start;  // [nbuckets] first sorted position of each bucket
     unsigned int *bucket_cnt;    // [nbuckets] scratch histogram
     // detector chunk data
-    unsigned short *dMt;         // [2][mt_rows][DET_G + 1] suffix histograms by target chunk
+    unsigned short *dMt;         // [2][mt_rows][256] band of suffix histograms by target chunk
+    unsigned int *det_base;      // [2][mt_rows] window counts below the band (zero between batches)
     size_t mt_rows;              // chunk rows per table of dMt
     DetState *E0, *E1, *E2;
     unsigned int *p2_ids;        // [max_chunks] chunks continued by the warp-per-chunk pass 2

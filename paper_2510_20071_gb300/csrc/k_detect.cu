@@ -29,13 +29,15 @@
 
 namespace fibar {
 
-// Distances stored in the window table: 1..DET_GT.  S is sized so that the regulator's
-// window is about DET_G / 2 chunks at the batch start; the table reaches 1.5 times that.
-constexpr unsigned DET_GT = 767;
+// The window table holds a band of DET_BAND distances [g_lo, g_lo + DET_BAND) around
+// the regulator's window at the batch start (q / S chunks, about DET_G / 2); distances
+// below the band enter only through their sum N(c, g_lo - 1).
+constexpr unsigned DET_BAND = 256;
 
 struct Geo {
     unsigned long long base;
     unsigned m, S, nchunks, Gold;
+    unsigned g_lo, g_hi;  // band of stored distances [g_lo, g_hi]
 };
 
 // Chunk length S: at least CHUNK, at most DET_MAX_CHUNKS chunks per batch, and DET_G
@@ -51,8 +53,11 @@ __device__ __forceinline__ Geo geometry(const KParams &kp, const Ctrl *ctrl)
     S = (S + 15) / 16 * 16;
     g.S = (unsigned)max((unsigned long long)CHUNK, S);
     g.nchunks = (g.m + g.S - 1) / g.S;
+    const unsigned long long mid = qprev / g.S;
+    g.g_lo = (unsigned)max(1ull, mid > DET_BAND / 2 ? mid - DET_BAND / 2 : 1ull);
+    g.g_hi = g.g_lo + DET_BAND - 1;
     const unsigned long long old_chunks = (g.base + g.S - 1) / g.S;
-    g.Gold = (unsigned)min((unsigned long long)DET_GT, old_chunks);
+    g.Gold = (unsigned)min((unsigned long long)g.g_hi, old_chunks);
     return g;
 }
 
@@ -79,20 +84,21 @@ __device__ __forceinline__ long long chunk_of(long long x, unsigned S, unsigned 
     return (x + (long long)Gold * S) / S - Gold;
 }
 
-// Suffix histograms by target chunk: for a batch chunk c and distance g = 1..DET_GT,
-//   Mt[t][c][g] = #{j in chunk c-g : next(j) >= cS}          (t = 0 pixels, 1 tiles)
+// Suffix histograms by target chunk: for a batch chunk c and distance g,
+//   M(c, g) = #{j in chunk c-g : next(j) >= cS}          (per t = 0 pixels, 1 tiles)
 // i.e. the events of chunk c-g still last of their pixel / tile at the start of chunk c
-// (source chunks reach back to -Gold; entries of older sources are never written and
-// never read).  The distinct counts of the aligned window [(c-g)S, cS) are the prefix
-// sums N(c, g) = sum_{g'=1..g} Mt[t][c][g'] along a contiguous row.
+// (source chunks reach back to -Gold).  The distinct counts of the aligned window
+// [(c-g)S, cS) are N(c, g) = sum_{g'=1..g} M(c, g').  Stored per target chunk c:
+//   base[t][c]          = N(c, g_lo - 1)               (accumulated with atomics)
+//   Mt[t][c][g - g_lo]  = M(c, g) for g in [g_lo, g_hi]  (a contiguous row)
 // A block handles HB_CHUNKS consecutive source chunks and one t: the histogram of chunk
 // distances in shared memory (one word of padding per 32 bins and a row pitch of 2 mod
-// 32 words, so that a lane's run of 32 bins and the diagonal read-out both spread over
-// the banks), suffix sums in registers, then per target row a run of HB_CHUNKS
-// consecutive distances.
+// 32 words, so that a lane's run of 32 bins and the diagonal reads both spread over the
+// banks), suffix sums in registers, then per target the sum of its distances below the
+// band and, per target row, a run of HB_CHUNKS consecutive band distances.
 constexpr int HB_CHUNKS = 16;
 constexpr int HB_PITCH = 1058;  // >= 1024 + 32 bins with padding, = 2 (mod 32)
-constexpr int MT_PITCH = DET_G + 1;  // u16 per target row (2 KB: 16-byte aligned rows)
+constexpr int MT_PITCH = DET_BAND;  // u16 per target row (512 B: 16-byte aligned rows)
 
 
 __device__ __forceinline__ int hb_slot(int d) { return d + (d >> 5); }
@@ -102,7 +108,7 @@ struct HistSmem {
 };
 
 __global__ void __launch_bounds__(256)
-k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t mt_rows)
+k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t mt_rows, unsigned *base_cnt)
 {
     PDL_ENTRY();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -112,6 +118,7 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
     const unsigned nwork = g.nchunks + g.Gold;
     const unsigned nunits = 2 * ((nwork + HB_CHUNKS - 1) / HB_CHUNKS);
     const long long lo_exist = -(long long)g.base;
+    const int g_lo = (int)g.g_lo, g_hi = (int)g.g_hi;
     for (unsigned unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
         const int t = unit & 1;
         const long long c_lo = (long long)((unit >> 1) * HB_CHUNKS) - (long long)g.Gold;  // first source chunk
@@ -119,17 +126,18 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
         for (unsigned i = tid; i < HB_CHUNKS * HB_PITCH / 4; i += 256) hw[i] = make_uint4(0u, 0u, 0u, 0u);
         __syncthreads();
         // histogram of the chunk distance to the next event of the same pixel / tile
+        // (distances beyond g_hi counted at g_hi)
         const long long j_lo = c_lo * g.S;
         const unsigned n_hi = (unsigned)min((long long)HB_CHUNKS * g.S, (long long)g.m - j_lo);
         const unsigned n_lo = (unsigned)max(0ll, lo_exist - j_lo);
-        const unsigned long long lim = (unsigned long long)DET_GT * g.S;  // offsets from here on: distance DET_GT
+        const unsigned long long lim = (unsigned long long)g_hi * g.S;
         for (unsigned i = n_lo + tid; i < n_hi; i += 256) {
             const unsigned long long j = g.base + (unsigned long long)(j_lo + i);
             const uint2 n = nxt_of(ring, j & kp.ring_mask);
             const unsigned nv = t ? n.y : n.x;
             const unsigned cc = i / g.S, r = i - cc * g.S;
             const unsigned long long rel = (unsigned long long)r + nv;  // from the start of chunk cc
-            const unsigned d = (nv == SAT || rel >= lim) ? DET_GT
+            const unsigned d = (nv == SAT || rel >= lim) ? (unsigned)g_hi
                              : (lim <= 0xFFFFFFFFull ? (unsigned)rel / g.S : (unsigned)(rel / g.S));
             atomicAdd(&H.h[cc][hb_slot((int)d)], 1u);
         }
@@ -153,22 +161,35 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
             for (int i = 0; i < 32; ++i) row[i] = v[i] + carry;
         }
         __syncthreads();
-        // target row c_lo + D receives distances D-15 .. D from the block's sources;
-        // HB_CHUNKS threads write one row's run
+        // below the band: target c_lo + D gets sum_{cc} M at distance D - cc in [1, g_lo)
+        for (int D = 1 + (int)tid; D < HB_CHUNKS + g_lo - 1; D += 256) {
+            const long long ct = c_lo + D;
+            if (ct < 1 || ct >= (long long)g.nchunks) continue;
+            unsigned acc = 0;
+#pragma unroll
+            for (int cc = 0; cc < HB_CHUNKS; ++cc) {
+                const int d = D - cc;
+                if (d >= 1 && d < g_lo) acc += H.h[cc][hb_slot(d)];
+            }
+            if (acc) atomicAdd(&base_cnt[(size_t)t * mt_rows + ct], acc);
+        }
+        // the band: target row c_lo + D receives distances D-15 .. D from the block's
+        // sources; HB_CHUNKS threads write one row's run
         unsigned short *base_t = Mt + (size_t)t * mt_rows * MT_PITCH;
-        for (unsigned i = tid; i < (unsigned)(HB_CHUNKS - 1 + DET_GT) * HB_CHUNKS; i += 256) {
-            const int D = 1 + (int)(i / HB_CHUNKS), u = (int)(i % HB_CHUNKS);
+        const int D0 = g_lo, D1 = g_hi + HB_CHUNKS - 1;  // targets with some band distance
+        for (unsigned i = tid; i < (unsigned)(D1 - D0 + 1) * HB_CHUNKS; i += 256) {
+            const int D = D0 + (int)(i / HB_CHUNKS), u = (int)(i % HB_CHUNKS);
             const int cc = HB_CHUNKS - 1 - u, d = D - cc;
             const long long ct = c_lo + D;  // target chunk
-            if (d >= 1 && d <= (int)DET_GT && ct >= 1 && ct < (long long)g.nchunks)
-                base_t[(size_t)ct * MT_PITCH + d] = (unsigned short)H.h[cc][hb_slot(d)];
+            if (d >= g_lo && d <= g_hi && ct >= 1 && ct < (long long)g.nchunks)
+                base_t[(size_t)ct * MT_PITCH + (d - g_lo)] = (unsigned short)H.h[cc][hb_slot(d)];
         }
         __syncthreads();
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctrl->S = g.S;
         ctrl->nchunks = g.nchunks;
-        ctrl->G = DET_G;
+        ctrl->g_lo = g.g_lo;
         ctrl->Gold = g.Gold;
     }
 }
@@ -189,15 +210,15 @@ __device__ __forceinline__ unsigned q_target(const KParams &kp, unsigned long lo
 }
 
 // Speculative start of chunk c >= 1, one warp per chunk.
-// (1) The window: scan the aligned windows g = 1..DET_GT ending at cS, 256 distances per
-//     round (8 per lane, one 16-byte load per row and lane, prefix sums by shuffles), up
-//     to the first one that the regulator would shrink at the next event (Eq. 20); then,
-//     inside the chunk where that window starts, the shortest window, to the event, that
-//     would still be shrunk.  Its length is where the regulator holds the queue.
+// (1) The window: among the aligned windows of g in [g_lo, g_hi] chunks ending at cS
+//     (N(c, g_lo - 1) plus a prefix sum of one band row: 8 distances per lane, one
+//     16-byte load per lane and type), the first that the regulator would shrink at the
+//     next event (Eq. 20); then, inside the chunk where that window starts, the shortest
+//     window, to the event, that would still be shrunk.  Its length is where the
+//     regulator holds the queue.
 // (2) Step cS applied to it.  All pops of a step test against the ratio X / Y of the
-//     previous step, so their number is q - q_targ at once (q_targ = max(q_min,
-//     min(q_max, floor(X / Y)))); the warp counts the pixels and tiles whose last queued
-//     event is among the popped ones.
+//     previous step, so their number is q - q_targ at once; the warp counts the pixels
+//     and tiles whose last queued event is among the popped ones.
 __device__ __forceinline__ unsigned pick8(const unsigned (&a)[8], unsigned u)
 {
     unsigned r = a[0];
@@ -208,69 +229,69 @@ __device__ __forceinline__ unsigned pick8(const unsigned (&a)[8], unsigned u)
 
 __global__ void __launch_bounds__(256)
 k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short *Mt, size_t mt_rows,
-           DetState *E0, unsigned *qout)
+           unsigned *base_cnt, DetState *E0, unsigned *qout)
 {
     PDL_ENTRY();
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long base = ctrl->base;
     const unsigned S = ctrl->S, nch = ctrl->nchunks, Gold = ctrl->Gold;
+    const unsigned g_lo = ctrl->g_lo, g_hi = g_lo + DET_BAND - 1;
     const unsigned warps_total = gridDim.x * (blockDim.x >> 5);
     for (unsigned c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) + 1; c < nch; c += warps_total) {
         const unsigned short *rp = Mt + (size_t)c * MT_PITCH;
         const unsigned short *rt = Mt + (mt_rows + c) * MT_PITCH;
-        const unsigned gmax = min(DET_GT, c + Gold);  // sources that exist in the table
+        const unsigned gmax = min(g_hi, c + Gold);  // sources that exist in the table
         const unsigned long long reach = (unsigned long long)c * S + base;  // events before the chunk
-        unsigned carry_p = 0, carry_t = 0, found = 0, snp = 0, snt = 0, fp1 = 0, ft1 = 0;
-        for (unsigned g0 = 0; g0 <= DET_GT && !found; g0 += 256) {
-            const uint4 wp = *reinterpret_cast<const uint4 *>(rp + g0 + 8 * lane);
-            const uint4 wt = *reinterpret_cast<const uint4 *>(rt + g0 + 8 * lane);
-            const unsigned xp[4] = {wp.x, wp.y, wp.z, wp.w}, xt[4] = {wt.x, wt.y, wt.z, wt.w};
-            unsigned pp[8], pt[8];
-            unsigned sp = 0, st = 0;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const unsigned gg = g0 + 8 * lane + u;
-                const bool ok = gg >= 1 && gg <= gmax;
-                sp += ok ? (xp[u >> 1] >> (16 * (u & 1))) & 0xFFFFu : 0u;
-                st += ok ? (xt[u >> 1] >> (16 * (u & 1))) & 0xFFFFu : 0u;
-                pp[u] = sp;
-                pt[u] = st;
-            }
-            // exclusive prefix of the lanes' sums
-            unsigned ip = sp, it = st;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned yp = __shfl_up_sync(0xFFFFFFFFu, ip, o), yt = __shfl_up_sync(0xFFFFFFFFu, it, o);
-                if (lane >= (unsigned)o) { ip += yp; it += yt; }
-            }
-            const unsigned op = carry_p + ip - sp, ot = carry_t + it - st;
-            unsigned mine = 0;
-#pragma unroll
-            for (int u = 7; u >= 0; --u) {
-                const unsigned gg = g0 + 8 * lane + u;
-                const unsigned long long np = op + pp[u], nt = ot + pt[u];
-                const unsigned long long L = min((unsigned long long)gg * S, reach), q = L + 1;
-                if (gg >= 1 && gg <= DET_GT && np > 0 && q > kp.q_min &&
-                    (q > kp.q_max || q * kp.den * np > L * kp.numA * nt))
-                    mine = gg;
-            }
-            const unsigned any = __ballot_sync(0xFFFFFFFFu, mine != 0);
-            if (any) {
-                found = __shfl_sync(0xFFFFFFFFu, mine, __ffs(any) - 1);
-                // N(c, found - 1): in this round, or the carry when found is its first distance
-                const unsigned g1 = found - 1;
-                if (g1 + 1 == g0) {
-                    fp1 = carry_p;
-                    ft1 = carry_t;
-                } else {
-                    const unsigned owner = (g1 - g0) >> 3, u = (g1 - g0) & 7;
-                    fp1 = __shfl_sync(0xFFFFFFFFu, op + pick8(pp, u), owner);
-                    ft1 = __shfl_sync(0xFFFFFFFFu, ot + pick8(pt, u), owner);
-                }
-            }
-            carry_p += __shfl_sync(0xFFFFFFFFu, ip, 31);
-            carry_t += __shfl_sync(0xFFFFFFFFu, it, 31);
+        // N(c, g_lo - 1), then cleared for the next batch's accumulation
+        const unsigned bp = base_cnt[c], bt = base_cnt[mt_rows + c];
+        unsigned found = 0, snp = 0, snt = 0, fp1 = bp, ft1 = bt;
+        const uint4 wp = *reinterpret_cast<const uint4 *>(rp + 8 * lane);
+        const uint4 wt = *reinterpret_cast<const uint4 *>(rt + 8 * lane);
+        __syncwarp();
+        if (lane == 0) {
+            base_cnt[c] = 0;
+            base_cnt[mt_rows + c] = 0;
         }
+        const unsigned xp[4] = {wp.x, wp.y, wp.z, wp.w}, xt[4] = {wt.x, wt.y, wt.z, wt.w};
+        unsigned pp[8], pt[8];
+        unsigned sp = 0, st = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const unsigned gg = g_lo + 8 * lane + u;
+            const bool ok = gg <= gmax;
+            sp += ok ? (xp[u >> 1] >> (16 * (u & 1))) & 0xFFFFu : 0u;
+            st += ok ? (xt[u >> 1] >> (16 * (u & 1))) & 0xFFFFu : 0u;
+            pp[u] = sp;
+            pt[u] = st;
+        }
+        // exclusive prefix of the lanes' sums
+        unsigned ip = sp, it = st;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned yp = __shfl_up_sync(0xFFFFFFFFu, ip, o), yt = __shfl_up_sync(0xFFFFFFFFu, it, o);
+            if (lane >= (unsigned)o) { ip += yp; it += yt; }
+        }
+        const unsigned op = bp + ip - sp, ot = bt + it - st;
+        unsigned mine = 0;
+#pragma unroll
+        for (int u = 7; u >= 0; --u) {
+            const unsigned gg = g_lo + 8 * lane + u;
+            const unsigned long long np = op + pp[u], nt = ot + pt[u];
+            const unsigned long long L = min((unsigned long long)gg * S, reach), q = L + 1;
+            if (np > 0 && q > kp.q_min && (q > kp.q_max || q * kp.den * np > L * kp.numA * nt)) mine = gg;
+        }
+        const unsigned any = __ballot_sync(0xFFFFFFFFu, mine != 0);
+        if (any) {
+            found = __shfl_sync(0xFFFFFFFFu, mine, __ffs(any) - 1);
+            // N(c, found - 1): the base when found is the band's first distance
+            if (found > g_lo) {
+                const unsigned g1 = found - 1 - g_lo, owner = g1 >> 3, u = g1 & 7;
+                fp1 = __shfl_sync(0xFFFFFFFFu, op + pick8(pp, u), owner);
+                ft1 = __shfl_sync(0xFFFFFFFFu, ot + pick8(pt, u), owner);
+            }
+        }
+        const unsigned carry_p = bp + __shfl_sync(0xFFFFFFFFu, ip, 31);  // N(c, g_hi)
+        const unsigned carry_t = bt + __shfl_sync(0xFFFFFFFFu, it, 31);
         const long long k0 = (long long)c * S;
         long long h;
         if (found && (unsigned long long)found * S <= reach) {
@@ -313,10 +334,10 @@ k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short
             }
             h = j0 + best;  // y = 0 always shrinks (the aligned window of `found` chunks)
         } else {
-            // no shrinking window within DET_GT chunks (then all of them), or the window
+            // no shrinking window within g_hi chunks (then all of them), or the window
             // reaches back to the stream start (then the whole history): the counts
             // accumulated over the scanned distances
-            h = max(k0 - (long long)(found ? found : DET_GT) * S, -(long long)base);
+            h = max(k0 - (long long)(found ? found : g_hi) * S, -(long long)base);
             snp = carry_p;
             snt = carry_t;
         }
@@ -918,10 +939,11 @@ cudaError_t launch_det_counts(const KParams &kp, const Bufs &b, cudaStream_t s, 
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (cudaError_t e_ = launch_pdl(k_det_hist, grid_for(2), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows))
+    if (cudaError_t e_ = launch_pdl(k_det_hist, grid_for(2), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
+                                    b.det_base))
         return e_;
     if (cudaError_t e_ = launch_pdl(k_det_init, grid_for(8), 256, 0, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
-                                    b.E0, b.qout))
+                                    b.det_base, b.E0, b.qout))
         return e_;
     return cudaGetLastError();
 }
