@@ -33,6 +33,7 @@ namespace fibar {
 // the regulator's window at the batch start (q / S chunks, about DET_G / 2); distances
 // below the band enter only through their sum N(c, g_lo - 1).
 constexpr unsigned DET_BAND = 256;
+constexpr int HB_BINS = 640;    // histogram bins (distances 0..639) >= the band's end
 
 struct Geo {
     unsigned long long base;
@@ -55,6 +56,7 @@ __device__ __forceinline__ Geo geometry(const KParams &kp, const Ctrl *ctrl)
     g.nchunks = (g.m + g.S - 1) / g.S;
     const unsigned long long mid = qprev / g.S;
     g.g_lo = (unsigned)max(1ull, mid > DET_BAND / 2 ? mid - DET_BAND / 2 : 1ull);
+    g.g_lo = min(g.g_lo, (unsigned)HB_BINS - DET_BAND);  // the choice of S keeps mid <= 511
     g.g_hi = g.g_lo + DET_BAND - 1;
     const unsigned long long old_chunks = (g.base + g.S - 1) / g.S;
     g.Gold = (unsigned)min((unsigned long long)g.g_hi, old_chunks);
@@ -97,7 +99,7 @@ __device__ __forceinline__ long long chunk_of(long long x, unsigned S, unsigned 
 // banks), suffix sums in registers, then per target the sum of its distances below the
 // band and, per target row, a run of HB_CHUNKS consecutive band distances.
 constexpr int HB_CHUNKS = 16;
-constexpr int HB_PITCH = 1058;  // >= 1024 + 32 bins with padding, = 2 (mod 32)
+constexpr int HB_PITCH = 674;   // >= HB_BINS + HB_BINS / 32 words with padding, = 2 (mod 32)
 constexpr int MT_PITCH = DET_BAND;  // u16 per target row (512 B: 16-byte aligned rows)
 
 
@@ -144,10 +146,11 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
         __syncthreads();
         // suffix sums over d: warp per chunk, lane l owns bins 32l .. 32l+31
         for (unsigned cc = wl; cc < HB_CHUNKS; cc += 8) {
-            unsigned *row = &H.h[cc][33 * lane];
+            const bool own = lane < HB_BINS / 32;
+            unsigned *row = &H.h[cc][33 * (own ? lane : 0)];
             unsigned v[32];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = row[i];
+            for (int i = 0; i < 32; ++i) v[i] = own ? row[i] : 0u;
 #pragma unroll
             for (int i = 30; i >= 0; --i) v[i] += v[i + 1];
             unsigned x = v[0];
@@ -157,8 +160,10 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
                 if (lane + o < 32) x += y;
             }
             const unsigned carry = x - v[0];  // bins above this lane's run
+            if (own) {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) row[i] = v[i] + carry;
+                for (int i = 0; i < 32; ++i) row[i] = v[i] + carry;
+            }
         }
         __syncthreads();
         // below the band: target c_lo + D gets sum_{cc} M at distance D - cc in [1, g_lo)
