@@ -222,6 +222,21 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
+// Lanes of the warp holding the same value as this lane, for values below 2^BITS: one
+// ballot per bit (a warp multisplit), much cheaper than a general match.
+template <int BITS>
+__device__ __forceinline__ unsigned warp_peers(unsigned v)
+{
+    unsigned peers = 0xFFFFFFFFu;
+#pragma unroll
+    for (int b = 0; b < BITS; ++b) {
+        const bool bit = (v >> b) & 1u;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
+}
+
 // launchers (kernels live in their own translation units); `nl` counts kernel launches
 cudaError_t launch_init(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
 cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, cudaStream_t s,

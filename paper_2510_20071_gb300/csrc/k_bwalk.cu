@@ -162,7 +162,7 @@ k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
                 const unsigned r = w * BW_PER_WARP + q * 32 + lane;
                 const bool valid = r < n;
                 const unsigned d = valid ? (unsigned)(S.key[r] >> 32) & lmask : BW_THREADS;
-                const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+                const unsigned peers = warp_peers<10>(d);  // local tile < 512, or 512 (none)
                 const unsigned rk = __popc(peers & lt_mask);
                 if (valid) S.rank[r] = (unsigned short)(S.whist[w][d] + rk);
                 __syncwarp();

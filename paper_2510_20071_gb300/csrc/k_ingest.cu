@@ -514,7 +514,7 @@ k_sort_pass(Ctrl *ctrl, const unsigned long long *in, unsigned long long *out, u
             const unsigned r = w * 512 + q * 32 + lane;
             const bool valid = r < n_here;
             const unsigned d = valid ? (unsigned)(S.key[r] >> shift) & dmask : RADIX;
-            const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+            const unsigned peers = warp_peers<10>(d);  // digit < 512, or RADIX (none)
             const unsigned rank = __popc(peers & lt_mask);
             if (valid) S.rank[r] = (unsigned short)(S.whist[w][d] + rank);
             __syncwarp();

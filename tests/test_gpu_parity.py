@@ -168,6 +168,35 @@ def test_large_batch_many_chunks(oracle_mod):
     _check(oracle_mod, W, H, ev, steps, "s1", c_on=0.2, c_off=0.2)
 
 
+def _swing_stream(W, H, phases, seed):
+    """Alternating phases: uniform pixels (mostly distinct tiles: Eq. 20 doubles the
+    target) and all four pixels of a few tiles (r = 1: the target halves), so the queue
+    length swings by orders of magnitude inside one batch."""
+    parts, t0 = [], 0
+    dense = np.array([(ty * 2 + dy) * W + tx * 2 + dx for ty in range(8) for tx in range(8)
+                      for dy in range(2) for dx in range(2)])
+    for i, (kind, n) in enumerate(phases):
+        ev = eventsim.random_events(W, H, n, seed=seed + i, pixels=dense if kind == "dense" else None)
+        ev[:, 1] += t0
+        t0 = int(ev[-1, 1]) + 1
+        parts.append(ev)
+    return torch.cat(parts)
+
+
+@pytest.mark.parametrize("mode", ["s2", "s1"])
+def test_queue_swings_within_a_batch(oracle_mod, mode):
+    """Inside one read-out the queue grows from ~40,000 events to the sensor size
+    (65,536) and back, and in the next it falls to ~170 and rises to ~40,000 again, so
+    the detector's window guesses fall outside the window table's band."""
+    W, H = 256, 256
+    ev = _swing_stream(W, H, [("spread", 150_000), ("dense", 60_000), ("spread", 200_000),
+                              ("dense", 150_000), ("spread", 100_000)], seed=31)
+    n = ev.shape[0]
+    steps = [("push", 0, 300_000), ("read", int(ev[299_999, 1])), ("push", 300_000, n),
+             ("read", int(ev[-1, 1]))]
+    _check(oracle_mod, W, H, ev, steps, mode, q_min=4)
+
+
 def test_determinism(oracle_mod):
     W, H = 64, 48
     ev = sim(W, H, 50_000, seed=16, noise=0.02)
