@@ -56,6 +56,8 @@ void free_all(fibar_t *h)
                     b.popk, b.blur_ord, b.bk, b.bpix, b.bj, b.bD, b.bflag, b.sel_status, b.beta_pow};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (h->snap_host) cudaFreeHost(h->snap_host);
+    h->snap_host = nullptr;
     memset(&h->b, 0, sizeof(h->b));
 }
 
@@ -155,6 +157,12 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
 #define ALLOC(ptr, n)                                  \
     if (e == cudaSuccess) e = dalloc(&(ptr), (n));
     ALLOC(b.ctrl, 1);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&h->snap_host, 2 * sizeof(unsigned), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        h->snap_host[0] = 0u;
+        h->snap_host[1] = 0u;
+        e = cudaHostGetDevicePointer((void **)&b.snap, h->snap_host, 0);
+    }
     ALLOC(b.pbar, npix);
     ALLOC(b.L, npix);
     ALLOC(b.last_pix, npix);
@@ -179,7 +187,7 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
         ALLOC(b.qout, maxp);
         ALLOC(b.ring4, h->R);
         ALLOC(b.ring_pix, h->R);
-        ALLOC(b.dMt, 2 * b.mt_rows * 256);
+        ALLOC(b.dMt, 2 * b.mt_rows * 640);
         ALLOC(b.det_base, 2 * b.mt_rows);
         ALLOC(b.E0, b.max_chunks);
         ALLOC(b.E1, b.max_chunks);
@@ -257,6 +265,8 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     }
     h->staging_used = 0;
     h->pending_upper = 0;
+    h->commits = 0;
+    h->pushed_since = 0;
     h->carry_slot = 0;
     h->epoch = 1;
     h->have_readout = false;
@@ -292,6 +302,11 @@ extern "C" int fibar_push_events(fibar_t *h, const fibar_event_t *ev, size_t n, 
     if (n == 0) return FIBAR_OK;
     if (!ev) return fail(h, FIBAR_EINVAL, "push: null event pointer");
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (h->pending_upper + n > h->params.max_pending && h->commits &&
+        __atomic_load_n(&h->snap_host[1], __ATOMIC_ACQUIRE) == (unsigned)h->commits) {
+        // the last commit has run: its count of records left pending is current
+        h->pending_upper = h->snap_host[0] + h->pushed_since;
+    }
     if (h->pending_upper + n > h->params.max_pending) {
         // the bound may be stale: learn the true carry count before refusing
         cudaError_t e = cudaStreamSynchronize(s);
@@ -328,6 +343,7 @@ extern "C" int fibar_push_events(fibar_t *h, const fibar_event_t *ev, size_t n, 
         h->staging_used += n;
     }
     h->pending_upper += n;
+    h->pushed_since += n;
     h->pushed += n;
     return FIBAR_OK;
 }
@@ -425,6 +441,8 @@ int process(fibar_t *h, unsigned long long t_read, float *out, cudaStream_t s)
     h->seg_ptr.clear();
     h->seg_n.clear();
     h->staging_used = 0;
+    h->commits += 1;
+    h->pushed_since = 0;
     return FIBAR_OK;
 }
 

@@ -134,11 +134,12 @@ struct Bufs {
     unsigned int *bucket_start;  // [nbuckets] first sorted position of each bucket
     unsigned int *bucket_cnt;    // [nbuckets] scratch histogram
     // detector chunk data
-    unsigned short *dMt;         // [2][mt_rows][256] band of suffix histograms by target chunk
+    unsigned short *dMt;         // [2][mt_rows][640] band of suffix histograms by target chunk
     unsigned int *det_base;      // [2][mt_rows] window counts below the band (zero between batches)
     size_t mt_rows;              // chunk rows per table of dMt
     DetState *E0, *E1, *E2;
     unsigned int *p2_ids;        // [max_chunks] chunks continued by the warp-per-chunk pass 2
+    unsigned int *snap;          // mapped host memory: {records left pending, commits} after a commit
     unsigned char *merged;
     unsigned *unm_bits;          // [chunks / 32] chunks that did not merge in pass 2
     float *out_staging;
@@ -177,6 +178,9 @@ struct fibar_s {
     std::vector<unsigned int> seg_n;
     unsigned long long staging_used;
     unsigned long long pending_upper;   // upper bound of records not yet applied
+    unsigned int *snap_host;            // host view of Bufs::snap (written by k_commit)
+    unsigned long long commits;         // read-outs and flushes launched
+    unsigned long long pushed_since;    // records pushed since the last read-out or flush
     int carry_slot;
     unsigned int epoch;
     bool have_readout;

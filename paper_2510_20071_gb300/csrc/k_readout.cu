@@ -59,7 +59,8 @@ __global__ void k_copy(const float4 *__restrict__ in, float4 *__restrict__ out, 
 }
 
 // After the last kernel of a read-out: base += m, reset tickets and look-back status.
-__global__ void k_commit(Ctrl *ctrl, unsigned long long *dec_status, size_t n_status, int next_carry_slot)
+__global__ void k_commit(Ctrl *ctrl, unsigned long long *dec_status, size_t n_status, int next_carry_slot,
+                         unsigned *snap)
 {
     PDL_ENTRY();
     for (size_t i = threadIdx.x; i < n_status; i += blockDim.x) dec_status[i] = 0ull;
@@ -79,6 +80,10 @@ __global__ void k_commit(Ctrl *ctrl, unsigned long long *dec_status, size_t n_st
         ctrl->batch_no += 1;
         // the carry slot just consumed becomes the output slot of the next decode
         ctrl->carry_n[1 - next_carry_slot] = 0;
+        // for the host: the records left pending, then (ordered after it) this commit's number
+        snap[0] = ctrl->carry_n[next_carry_slot];
+        __threadfence_system();
+        *(volatile unsigned *)&snap[1] = ctrl->batch_no - 1u;
     }
 }
 
@@ -157,7 +162,8 @@ cudaError_t launch_commit(const KParams &kp, const Bufs &b, int next_carry_slot,
 {
     nl += 1;
     (void)kp;
-    if (cudaError_t e_ = launch_pdl(k_commit, 1, 256, 0, s, b.ctrl, b.dec_status, b.max_dec_tiles, next_carry_slot)) return e_;
+    if (cudaError_t e_ = launch_pdl(k_commit, 1, 256, 0, s, b.ctrl, b.dec_status, b.max_dec_tiles, next_carry_slot,
+                                    b.snap)) return e_;
     return cudaGetLastError();
 }
 

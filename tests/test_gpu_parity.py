@@ -62,7 +62,10 @@ def test_config_perlin_1280x720_prefix(oracle_mod):
     ev = eventsim.make_config("perlin_1280x720_200M", n_events=n, device="cuda").cpu()
     steps = plan_packets(n, 65_536, 1_000_000, ev)
     for mode in ["s2", "s1"]:
-        _check(oracle_mod, 1280, 720, ev, steps, mode, c_on=0.2, c_off=0.2)
+        _, stats = _check(oracle_mod, 1280, 720, ev, steps, mode, c_on=0.2, c_off=0.2)
+        # the speculative detector's guesses hold from the first read-out on (the queue
+        # grows from empty to ~36,000 events in it): the serial fixup reruns few events
+        assert stats["detector_fix_steps"] < n // 100, stats
 
 
 @pytest.mark.parametrize("mode", ["nsf", "s1", "s2"])
