@@ -187,7 +187,7 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
         ALLOC(b.qout, maxp);
         ALLOC(b.ring4, h->R);
         ALLOC(b.ring_pix, h->R);
-        ALLOC(b.dMt, 2 * b.mt_rows * 640);
+        ALLOC(b.dMt, 2 * b.mt_rows * 256);
         ALLOC(b.det_base, 2 * b.mt_rows);
         ALLOC(b.E0, b.max_chunks);
         ALLOC(b.E1, b.max_chunks);

@@ -134,7 +134,7 @@ struct Bufs {
     unsigned int *bucket_start;  // [nbuckets] first sorted position of each bucket
     unsigned int *bucket_cnt;    // [nbuckets] scratch histogram
     // detector chunk data
-    unsigned short *dMt;         // [2][mt_rows][640] band of suffix histograms by target chunk
+    unsigned short *dMt;         // [2][mt_rows][256] band of suffix histograms by target chunk
     unsigned int *det_base;      // [2][mt_rows] window counts below the band (zero between batches)
     size_t mt_rows;              // chunk rows per table of dMt
     DetState *E0, *E1, *E2;

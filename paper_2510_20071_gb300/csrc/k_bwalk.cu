@@ -1,18 +1,20 @@
 // Bucket walk: the temporal filter and the detector links, one CTA per bucket of 2^LB
-// consecutive 2x2 tiles (LB <= 9), one thread per tile.
+// consecutive 2x2 tiles (LB <= 9).
 //
 // The radix sort orders the batch by bucket only (the tile id's high bits), stably, so
 // a bucket's events are contiguous and in arrival order.  The CTA loads them into shared
-// memory in pieces of BW_PIECE events, sorts each piece stably by the tile id's low bits
-// (per-warp match ranking), and every thread walks its tile's events in arrival order
-// with the four pixels' state in registers:
-//   - temporal filter of the event's pixel (Sec. 4.1): Eq. 7 (EMA of the increment
-//     C_p p), Eq. 6 with the updated average, Eq. 10; FP32 state;
-//   - links for the stale-pixel detector, one 16-byte record per event in the event
-//     ring: {dP, dT, nP, nT} = distance to the previous / next event of the same pixel
-//     and of the same tile (0xFFFFFFFF: none).  Each pixel keeps its last event's record
-//     pending in registers until its next event arrives (nP) or the bucket ends; events
-//     of earlier batches get nP / nT patched in place.
+// memory in pieces of BW_PIECE events and sorts each piece stably by the tile id's low
+// bits (warp multisplit ranking): each tile's events are then a contiguous segment in
+// arrival order.  Per piece:
+//   - links, one event per thread: one 16-byte record per event in the event ring,
+//     {dP, dT, nP, nT} = distance to the previous / next event of the same pixel and of
+//     the same tile (0xFFFFFFFF: none), from the event's neighbours in its tile segment
+//     (same pixel: the nearest with the same sub-pixel); the first event of a pixel /
+//     tile in the piece links to the last one before it (an earlier piece or batch),
+//     whose next-link it patches in place;
+//   - temporal filter, one thread per tile walking its segment in arrival order with
+//     the four pixels' state in registers (Sec. 4.1): Eq. 7 (EMA of the increment
+//     C_p p), Eq. 6 with the updated average, Eq. 10; FP32 state.
 // The active event queue of Sec. 4.2 is the index window [h, k]; with these links a
 // push activates a pixel iff dP > k - h, and popping event j deactivates it iff
 // nP(j) > k - j (likewise for tiles), so the detector never touches a per-pixel counter.
@@ -23,16 +25,19 @@
 namespace fibar {
 
 constexpr int BW_THREADS = 512;  // = max tiles per bucket
-constexpr int BW_PIECE = 4096;
+constexpr int BW_PIECE = 2048;
 constexpr int BW_WARPS = BW_THREADS / 32;
 constexpr int BW_PER_WARP = BW_PIECE / BW_WARPS;  // 256 events ranked by each warp
 
 struct BwSmem {
     unsigned long long key[BW_PIECE];
     unsigned long long out[BW_PIECE];
+    unsigned long long plast[4 * BW_THREADS];  // per pixel: its last event before the piece
+    unsigned long long tlast[BW_THREADS];      // per tile: its last event before the piece
     unsigned short rank[BW_PIECE];
     unsigned whist[BW_WARPS][BW_THREADS];
     unsigned tstart[BW_THREADS];
+    unsigned tcnt[BW_THREADS];
     unsigned warp[BW_WARPS];
     unsigned bucket;
 };
@@ -109,9 +114,8 @@ k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
         unsigned pix[4];
         bool ok[4];
         float pb[4], lv[4], l0[4];
-        unsigned long long lp[4], lp0[4];
-        uint4 pd[4];
-        unsigned ord[4], soff[4];
+        unsigned long long lp0[4];
+        unsigned ord[4], soff[4], seen = 0;  // seen: sub-pixels with an event in the bucket
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             const unsigned x = 2 * tx + (s & 1), y = 2 * ty + (s >> 1);
@@ -120,14 +124,12 @@ k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
             pb[s] = ok[s] ? b.pbar[pix[s]] : 0.f;
             lv[s] = ok[s] ? b.L[pix[s]] : 0.f;
             l0[s] = lv[s];
-            lp[s] = ok[s] ? b.last_pix[pix[s]] : NONE64;
-            lp0[s] = lp[s];
-            pd[s] = make_uint4(SAT, SAT, SAT, SAT);
+            lp0[s] = ok[s] ? b.last_pix[pix[s]] : NONE64;
+            S.plast[4 * threadIdx.x + s] = lp0[s];
             ord[s] = 0;
             soff[s] = 0;
         }
-        unsigned long long ltl = has_tile ? b.last_tile[tile] : NONE64;
-        int plast = 0;  // sub-pixel of the tile's last event (its record waits for nT)
+        S.tlast[threadIdx.x] = has_tile ? b.last_tile[tile] : NONE64;
 
         if (kS1) {
             // per (tile, sub-pixel) counts over the whole bucket -> list offsets
@@ -180,6 +182,7 @@ k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
             unsigned tot;
             const unsigned my_start = bw_scan(run, S.warp, &tot);
             S.tstart[threadIdx.x] = my_start;
+            S.tcnt[threadIdx.x] = run;
             __syncthreads();
             for (unsigned i = threadIdx.x; i < n; i += BW_THREADS) {
                 const unsigned long long kk = S.key[i];
@@ -187,52 +190,61 @@ k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
                 S.out[S.tstart[d] + S.whist[i / BW_PER_WARP][d] + S.rank[i]] = kk;
             }
             __syncthreads();
-            // walk this thread's tile
+            if (kLinks) {
+                // links, one event per thread (reads the last events before the piece)
+                for (unsigned i = threadIdx.x; i < n; i += BW_THREADS) {
+                    const unsigned long long r = S.out[i];
+                    const unsigned d = (unsigned)(r >> 32) & lmask;
+                    const unsigned ts = S.tstart[d], te = ts + S.tcnt[d];
+                    const unsigned k = (unsigned)(r >> 3) & 0x1FFFFFFFu, s = (unsigned)(r >> 1) & 3u;
+                    const unsigned long long g = base + k;
+                    unsigned dT, nT = SAT, dP = SAT, nP = SAT;
+                    if (i > ts) {
+                        dT = k - ((unsigned)(S.out[i - 1] >> 3) & 0x1FFFFFFFu);
+                    } else {
+                        const unsigned long long tl = S.tlast[d];
+                        dT = tl == NONE64 ? SAT : sat_dist2(g, tl);
+                        // the tile's previous event (an earlier piece or batch) learns its next
+                        if (tl != NONE64 && tl >= live_lo) ring_u[4 * (tl & kp.ring_mask) + 3] = dT;
+                    }
+                    if (i + 1 < te) nT = ((unsigned)(S.out[i + 1] >> 3) & 0x1FFFFFFFu) - k;
+                    // the same pixel: nearest earlier / later event of the segment with sub-pixel s
+                    bool found = false;
+                    for (unsigned j = i; j > ts && !found; --j) {
+                        const unsigned long long rj = S.out[j - 1];
+                        if (((unsigned)(rj >> 1) & 3u) == s) {
+                            dP = k - ((unsigned)(rj >> 3) & 0x1FFFFFFFu);
+                            found = true;
+                        }
+                    }
+                    if (!found) {
+                        const unsigned long long pl = S.plast[4 * d + s];
+                        dP = pl == NONE64 ? SAT : sat_dist2(g, pl);
+                        if (pl != NONE64 && pl >= live_lo) ring_u[4 * (pl & kp.ring_mask) + 2] = dP;
+                    }
+                    for (unsigned j = i + 1; j < te; ++j) {
+                        const unsigned long long rj = S.out[j];
+                        if (((unsigned)(rj >> 1) & 3u) == s) {
+                            nP = ((unsigned)(rj >> 3) & 0x1FFFFFFFu) - k;
+                            break;
+                        }
+                    }
+                    b.ring4[g & kp.ring_mask] = make_uint4(dP, dT, nP, nT);
+                }
+                __syncthreads();
+            }
+            // temporal filter: this thread's tile, in arrival order
             const unsigned e0 = my_start, e1 = my_start + run;
+            unsigned long long lastg[4] = {NONE64, NONE64, NONE64, NONE64};
             for (unsigned i = e0; i < e1; ++i) {
                 const unsigned long long r = S.out[i];
                 const unsigned k = (unsigned)(r >> 3) & 0x1FFFFFFFu;
                 const int s = (int)(r >> 1) & 3;
                 const bool off_ev = r & 1u;
-                const unsigned long long g = base + k;
-                unsigned long long lps = lp[0];
                 float pbs = pb[0], lvs = lv[0];
 #pragma unroll
                 for (int qq = 1; qq < 4; ++qq)
-                    if (qq == s) { lps = lp[qq]; pbs = pb[qq]; lvs = lv[qq]; }
-                if (kLinks) {
-                    const unsigned dP = lps == NONE64 ? SAT : sat_dist2(g, lps);
-                    const unsigned dT = ltl == NONE64 ? SAT : sat_dist2(g, ltl);
-                    // the tile's previous event learns its next tile event
-                    if (ltl != NONE64) {
-                        if (ltl >= base) {
-#pragma unroll
-                            for (int qq = 0; qq < 4; ++qq)
-                                if (qq == plast) pd[qq].w = dT;
-                        } else if (ltl >= live_lo) {
-                            ring_u[4 * (ltl & kp.ring_mask) + 3] = dT;
-                        }
-                    }
-                    // the pixel's previous event learns its next pixel event; its record is
-                    // complete (its next tile event came at or before this one)
-                    if (lps != NONE64) {
-                        if (lps >= base) {
-#pragma unroll
-                            for (int qq = 0; qq < 4; ++qq)
-                                if (qq == s) {
-                                    pd[qq].z = dP;
-                                    b.ring4[lps & kp.ring_mask] = pd[qq];
-                                }
-                        } else if (lps >= live_lo) {
-                            ring_u[4 * (lps & kp.ring_mask) + 2] = dP;
-                        }
-                    }
-#pragma unroll
-                    for (int qq = 0; qq < 4; ++qq)
-                        if (qq == s) pd[qq] = make_uint4(dP, dT, SAT, SAT);
-                }
-                ltl = g;
-                plast = s;
+                    if (qq == s) { pbs = pb[qq]; lvs = lv[qq]; }
                 // Eqs. 2-3: increment C_p p; Eq. 7 then Eq. 6 (updated average) and Eq. 10
                 const float inc = off_ev ? -kp.c_off : kp.c_on;
                 pbs = kp.a * pbs + kp.oma * inc;
@@ -250,18 +262,27 @@ k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
                 }
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq)
-                    if (qq == s) { lp[qq] = g; pb[qq] = pbs; lv[qq] = lvs; }
+                    if (qq == s) { pb[qq] = pbs; lv[qq] = lvs; lastg[qq] = base + k; }
+            }
+            // the tile's and its pixels' last events for the next piece
+            if (run) {
+                S.tlast[threadIdx.x] = base + ((S.out[e1 - 1] >> 3) & 0x1FFFFFFFull);
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq)
+                    if (lastg[qq] != NONE64) {
+                        S.plast[4 * threadIdx.x + qq] = lastg[qq];
+                        seen |= 1u << qq;
+                    }
             }
             __syncthreads();
         }
-        // write back the tile's state and the pending records (no next event yet)
+        // write back the tile's state
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-            if (!ok[s] || lp[s] == lp0[s]) continue;
+            if (!ok[s] || !(seen >> s & 1u)) continue;
             b.pbar[pix[s]] = pb[s];
             b.L[pix[s]] = lv[s];
-            b.last_pix[pix[s]] = lp[s];
-            if (kLinks) b.ring4[lp[s] & kp.ring_mask] = pd[s];
+            b.last_pix[pix[s]] = S.plast[4 * threadIdx.x + s];
             if (kS1) {
                 long long prev = -0x7FFFFFFFll - 1;  // no earlier event
                 if (lp0[s] != NONE64) {
@@ -272,7 +293,7 @@ k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
                 b.s1_linit[pix[s]] = l0[s];
             }
         }
-        if (has_tile) b.last_tile[tile] = ltl;
+        if (has_tile && seen) b.last_tile[tile] = S.tlast[threadIdx.x];
         __syncthreads();
     }
 }

@@ -29,15 +29,15 @@
 
 namespace fibar {
 
-// The window table holds the distances [g_lo, DET_GMAX]: from 64 chunks below the
-// regulator's window at the batch start (q / S chunks, at most DET_G / 2 by the choice of
-// S), but at most 256 distances in steady state, to DET_GMAX, so that a queue that grows
-// within the batch (the first read-outs of a stream) still finds its window; distances
-// below g_lo enter only through their sum N(c, g_lo - 1).  A queue that shrinks below
-// the band only makes the guess longer than the regulator's window, which the first
-// steps correct.
-constexpr unsigned DET_GMAX = 639;
-constexpr int HB_BINS = DET_GMAX + 1;  // histogram bins (distances 0..DET_GMAX)
+// The window table holds a band of DET_BAND distances [g_lo, g_lo + DET_BAND) starting
+// 64 chunks below the regulator's window at the batch start (q / S chunks, at most
+// DET_G / 2 by the choice of S), so that a queue that grows within the batch still finds
+// its window; distances below g_lo enter only through their sum N(c, g_lo - 1).  A
+// queue that shrinks below the band only makes the guess longer than the regulator's
+// window, which the first steps correct.  While the queue is short (a stream's first
+// read-out, or after it collapsed) S is raised so that the band reaches npix / 16 events.
+constexpr unsigned DET_BAND = 256;
+constexpr int HB_BINS = 640;  // histogram bins (distances 0..639 >= the band's end)
 
 struct Geo {
     unsigned long long base;
@@ -55,12 +55,13 @@ __device__ __forceinline__ Geo geometry(const KParams &kp, const Ctrl *ctrl)
     const unsigned long long qprev = g.base - (unsigned long long)ctrl->det.h;
     unsigned long long S = (2ull * qprev + 4ull * CHUNK + DET_G - 1) / DET_G;
     S = max(S, ((unsigned long long)g.m + DET_MAX_CHUNKS - 1) / DET_MAX_CHUNKS);
+    if (qprev < kp.npix / 32) S = max(S, ((unsigned long long)kp.npix + 16ull * DET_BAND - 1) / (16ull * DET_BAND));
     S = (S + 15) / 16 * 16;
     g.S = (unsigned)max((unsigned long long)CHUNK, S);
     g.nchunks = (g.m + g.S - 1) / g.S;
     const unsigned long long mid = qprev / g.S;  // <= 511 by the choice of S
-    g.g_lo = (unsigned)min((unsigned long long)DET_GMAX - 255, mid > 64 ? mid - 64 : 1ull);
-    g.g_hi = DET_GMAX;
+    g.g_lo = (unsigned)min((unsigned long long)HB_BINS - DET_BAND, mid > 128 ? mid - 128 : 1ull);
+    g.g_hi = g.g_lo + DET_BAND - 1;
     const unsigned long long old_chunks = (g.base + g.S - 1) / g.S;
     g.Gold = (unsigned)min((unsigned long long)g.g_hi, old_chunks);
     return g;
@@ -95,7 +96,7 @@ __device__ __forceinline__ long long chunk_of(long long x, unsigned S, unsigned 
 // (source chunks reach back to -Gold).  The distinct counts of the aligned window
 // [(c-g)S, cS) are N(c, g) = sum_{g'=1..g} M(c, g').  Stored per target chunk c:
 //   base[t][c]          = N(c, g_lo - 1)               (accumulated with atomics)
-//   Mt[t][c][g - g_lo]  = M(c, g) for g in [g_lo, DET_GMAX]  (a contiguous row)
+//   Mt[t][c][g - g_lo]  = M(c, g) for g in [g_lo, g_hi]  (a contiguous row)
 // A block handles HB_CHUNKS consecutive source chunks and one t: the histogram of chunk
 // distances in shared memory (one word of padding per 32 bins and a row pitch of 2 mod
 // 32 words, so that a lane's run of 32 bins and the diagonal reads both spread over the
@@ -103,7 +104,7 @@ __device__ __forceinline__ long long chunk_of(long long x, unsigned S, unsigned 
 // band and, per target row, a run of HB_CHUNKS consecutive band distances.
 constexpr int HB_CHUNKS = 16;
 constexpr int HB_PITCH = 674;   // >= HB_BINS + HB_BINS / 32 words with padding, = 2 (mod 32)
-constexpr int MT_PITCH = DET_GMAX + 1;  // u16 per target row (1280 B: 16-byte aligned rows)
+constexpr int MT_PITCH = DET_BAND;  // u16 per target row (512 B: 16-byte aligned rows)
 
 
 __device__ __forceinline__ int hb_slot(int d) { return d + (d >> 5); }
@@ -243,7 +244,7 @@ k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long base = ctrl->base;
     const unsigned S = ctrl->S, nch = ctrl->nchunks, Gold = ctrl->Gold;
-    const unsigned g_lo = ctrl->g_lo, g_hi = DET_GMAX;
+    const unsigned g_lo = ctrl->g_lo, g_hi = g_lo + DET_BAND - 1;
     const unsigned warps_total = gridDim.x * (blockDim.x >> 5);
     for (unsigned c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) + 1; c < nch; c += warps_total) {
         const unsigned short *rp = Mt + (size_t)c * MT_PITCH;
@@ -252,63 +253,54 @@ k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short
         const unsigned long long reach = (unsigned long long)c * S + base;  // events before the chunk
         // N(c, g_lo - 1), then cleared for the next batch's accumulation
         const unsigned bp = base_cnt[c], bt = base_cnt[mt_rows + c];
+        unsigned found = 0, snp = 0, snt = 0, fp1 = bp, ft1 = bt;
+        const uint4 wp = *reinterpret_cast<const uint4 *>(rp + 8 * lane);
+        const uint4 wt = *reinterpret_cast<const uint4 *>(rt + 8 * lane);
         __syncwarp();
         if (lane == 0) {
             base_cnt[c] = 0;
             base_cnt[mt_rows + c] = 0;
         }
-        unsigned found = 0, snp = 0, snt = 0, fp1 = bp, ft1 = bt;
-        unsigned carry_p = bp, carry_t = bt;  // N(c, g0 - 1) at each round's start
-        for (unsigned g0 = g_lo; g0 <= g_hi && !found; g0 += 256) {
-            const unsigned o = (g0 - g_lo) + 8 * lane;  // 8 distances per 16-byte load, inside the row
-            const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-            const uint4 wp = o < (unsigned)MT_PITCH ? *reinterpret_cast<const uint4 *>(rp + o) : z;
-            const uint4 wt = o < (unsigned)MT_PITCH ? *reinterpret_cast<const uint4 *>(rt + o) : z;
-            const unsigned xp[4] = {wp.x, wp.y, wp.z, wp.w}, xt[4] = {wt.x, wt.y, wt.z, wt.w};
-            unsigned pp[8], pt[8];
-            unsigned sp = 0, st = 0;
+        const unsigned xp[4] = {wp.x, wp.y, wp.z, wp.w}, xt[4] = {wt.x, wt.y, wt.z, wt.w};
+        unsigned pp[8], pt[8];
+        unsigned sp = 0, st = 0;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const unsigned gg = g0 + 8 * lane + u;
-                const bool ok = gg <= gmax;
-                sp += ok ? (xp[u >> 1] >> (16 * (u & 1))) & 0xFFFFu : 0u;
-                st += ok ? (xt[u >> 1] >> (16 * (u & 1))) & 0xFFFFu : 0u;
-                pp[u] = sp;
-                pt[u] = st;
-            }
-            // exclusive prefix of the lanes' sums
-            unsigned ip = sp, it = st;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned yp = __shfl_up_sync(0xFFFFFFFFu, ip, o), yt = __shfl_up_sync(0xFFFFFFFFu, it, o);
-                if (lane >= (unsigned)o) { ip += yp; it += yt; }
-            }
-            const unsigned op = carry_p + ip - sp, ot = carry_t + it - st;
-            unsigned mine = 0;
-#pragma unroll
-            for (int u = 7; u >= 0; --u) {
-                const unsigned gg = g0 + 8 * lane + u;
-                const unsigned long long np = op + pp[u], nt = ot + pt[u];
-                const unsigned long long L = min((unsigned long long)gg * S, reach), q = L + 1;
-                if (gg <= g_hi && np > 0 && q > kp.q_min && (q > kp.q_max || q * kp.den * np > L * kp.numA * nt))
-                    mine = gg;
-            }
-            const unsigned any = __ballot_sync(0xFFFFFFFFu, mine != 0);
-            if (any) {
-                found = __shfl_sync(0xFFFFFFFFu, mine, __ffs(any) - 1);
-                // N(c, found - 1): the carry when found is this round's first distance
-                if (found > g0) {
-                    const unsigned g1 = found - 1 - g0, owner = g1 >> 3, u = g1 & 7;
-                    fp1 = __shfl_sync(0xFFFFFFFFu, op + pick8(pp, u), owner);
-                    ft1 = __shfl_sync(0xFFFFFFFFu, ot + pick8(pt, u), owner);
-                } else {
-                    fp1 = carry_p;
-                    ft1 = carry_t;
-                }
-            }
-            carry_p += __shfl_sync(0xFFFFFFFFu, ip, 31);
-            carry_t += __shfl_sync(0xFFFFFFFFu, it, 31);
+        for (int u = 0; u < 8; ++u) {
+            const unsigned gg = g_lo + 8 * lane + u;
+            const bool ok = gg <= gmax;
+            sp += ok ? (xp[u >> 1] >> (16 * (u & 1))) & 0xFFFFu : 0u;
+            st += ok ? (xt[u >> 1] >> (16 * (u & 1))) & 0xFFFFu : 0u;
+            pp[u] = sp;
+            pt[u] = st;
         }
+        // exclusive prefix of the lanes' sums
+        unsigned ip = sp, it = st;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned yp = __shfl_up_sync(0xFFFFFFFFu, ip, o), yt = __shfl_up_sync(0xFFFFFFFFu, it, o);
+            if (lane >= (unsigned)o) { ip += yp; it += yt; }
+        }
+        const unsigned op = bp + ip - sp, ot = bt + it - st;
+        unsigned mine = 0;
+#pragma unroll
+        for (int u = 7; u >= 0; --u) {
+            const unsigned gg = g_lo + 8 * lane + u;
+            const unsigned long long np = op + pp[u], nt = ot + pt[u];
+            const unsigned long long L = min((unsigned long long)gg * S, reach), q = L + 1;
+            if (np > 0 && q > kp.q_min && (q > kp.q_max || q * kp.den * np > L * kp.numA * nt)) mine = gg;
+        }
+        const unsigned any = __ballot_sync(0xFFFFFFFFu, mine != 0);
+        if (any) {
+            found = __shfl_sync(0xFFFFFFFFu, mine, __ffs(any) - 1);
+            // N(c, found - 1): the base when found is the band's first distance
+            if (found > g_lo) {
+                const unsigned g1 = found - 1 - g_lo, owner = g1 >> 3, u = g1 & 7;
+                fp1 = __shfl_sync(0xFFFFFFFFu, op + pick8(pp, u), owner);
+                ft1 = __shfl_sync(0xFFFFFFFFu, ot + pick8(pt, u), owner);
+            }
+        }
+        const unsigned carry_p = bp + __shfl_sync(0xFFFFFFFFu, ip, 31);  // N(c, g_hi)
+        const unsigned carry_t = bt + __shfl_sync(0xFFFFFFFFu, it, 31);
         const long long k0 = (long long)c * S;
         long long h;
         if (found && (unsigned long long)found * S <= reach) {
@@ -554,6 +546,14 @@ __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
+// n 8-byte copies from a source with a 16-byte stride to consecutive shared slots (a
+// shared address and a global pointer walked by plain increments)
+__device__ __forceinline__ void cp_async8_run(unsigned dst_s, const uint2 *src, int n)
+{
+    const char *p = reinterpret_cast<const char *>(src);
+    for (int u = 0; u < n; ++u, dst_s += 8, p += 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst_s), "l"(p) : "memory");
+}
 __device__ __forceinline__ const uint2 *nxt_ptr(const uint4 *ring, unsigned base32, unsigned mask32, int e)
 {
     return reinterpret_cast<const uint2 *>(ring) + 2 * ((base32 + (unsigned)e) & mask32) + 1;
@@ -594,9 +594,7 @@ __device__ bool lane_run(const KParams &kp, unsigned long long base, const uint4
             const unsigned gs = (base32 + (unsigned)e) & mask32;          // global slot
             const unsigned ss = (unsigned)e & (LR_R - 1);                // ring slot
             const int run = min(n, (int)min(mask32 + 1 - gs, (unsigned)LR_R - ss));
-            const uint2 *src = ring2 + 2 * (size_t)gs + 1;
-            uint2 *dst = &sm.pop[lane][ss];
-            for (int u = 0; u < run; ++u) cp_async8(dst + u, src + 2 * u);
+            cp_async8_run((unsigned)__cvta_generic_to_shared(&sm.pop[lane][ss]), ring2 + 2 * (size_t)gs + 1, run);
             e += run;
             n -= run;
         }
@@ -612,9 +610,9 @@ __device__ bool lane_run(const KParams &kp, unsigned long long base, const uint4
         const int n = active ? (int)min((unsigned)LR_B, k1 > kb ? k1 - kb : 0u) : 0;
         const unsigned gs = (base32 + kb) & mask32;
         const int run = min(n, (int)(mask32 + 1 - gs));
-        const uint2 *src = ring2 + 2 * (size_t)gs;
-        for (int u = 0; u < run; ++u) cp_async8(&sm.push[buf][lane][u], src + 2 * u);
-        for (int u = run; u < n; ++u) cp_async8(&sm.push[buf][lane][u], ring2 + 2 * (size_t)(u - run));
+        const unsigned dst_s = (unsigned)__cvta_generic_to_shared(&sm.push[buf][lane][0]);
+        cp_async8_run(dst_s, ring2 + 2 * (size_t)gs, run);
+        cp_async8_run(dst_s + 8u * (unsigned)run, ring2, n - run);
         if (kMerge)
             for (int u = 0; u < n; ++u) cp_async4(&sm.ref[buf][lane][u], qout + kb + u);
     };
