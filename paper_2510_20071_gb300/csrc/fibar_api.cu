@@ -53,7 +53,7 @@ void free_all(fibar_t *h)
                     b.dec_status, b.rec[0], b.rec[1], b.sort_hist, b.sort_base, b.sort_rows, b.sort_rowflag, b.sort_gtot, b.sort_gflag, b.sort_gcount,
                     b.qout, b.ring4, b.ring_pix, b.bucket_start, b.bucket_cnt, b.dMt, b.det_base, b.E0, b.E1, b.E2, b.p2_ids, b.merged, b.unm_bits,
                     b.out_staging, b.dbg_cnt, b.plist, b.plnb, b.epos, b.lbl, b.s1_info, b.s1_linit,
-                    b.popk, b.blur_ord, b.bk, b.bpix, b.bj, b.bD, b.bflag, b.sel_status, b.beta_pow};
+                    b.popk, b.blur_ord, b.bk, b.bpix, b.bj, b.bval, b.sel_status, b.beta_pow};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->snap_host) cudaFreeHost(h->snap_host);
@@ -210,8 +210,7 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
         ALLOC(b.bk, b.max_pops);
         ALLOC(b.bpix, b.max_pops);
         ALLOC(b.bj, b.max_pops);
-        ALLOC(b.bD, b.max_pops);
-        ALLOC(b.bflag, b.max_pops);
+        ALLOC(b.bval, b.max_pops);
         ALLOC(b.sel_status, b.max_sel_tiles);
         ALLOC(b.beta_pow, 64);
     }
@@ -239,7 +238,7 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     if (e == cudaSuccess && b.unm_bits) e = cudaMemsetAsync(b.unm_bits, 0, (b.max_chunks / 32 + 2) * 4, s);
     if (e == cudaSuccess && b.det_base) e = cudaMemsetAsync(b.det_base, 0, 2 * b.mt_rows * 4, s);
     if (e == cudaSuccess && b.s1_info) e = cudaMemsetAsync(b.s1_info, 0, npix * sizeof(int4), s);
-    if (e == cudaSuccess && b.bflag) e = cudaMemsetAsync(b.bflag, 0, b.max_pops * 4, s);
+    if (e == cudaSuccess && b.bval) e = cudaMemsetAsync(b.bval, 0, b.max_pops * 8, s);
     if (e == cudaSuccess && b.sel_status) e = cudaMemsetAsync(b.sel_status, 0, b.max_sel_tiles * 8, s);
     if (e == cudaSuccess && b.beta_pow) {
         float tab[64];

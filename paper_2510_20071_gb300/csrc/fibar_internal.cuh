@@ -155,8 +155,8 @@ struct Bufs {
     unsigned int *blur_ord;      // [maxp + npix] blur ordinal of each popped event (or ~0)
     unsigned int *bk, *bpix;     // [maxp + npix] step and pixel of each blur
     int *bj;                     // [maxp + npix] popped event (batch-relative) of each blur
-    float *bD;                   // [maxp + npix] blurred value minus L-without-blurs
-    unsigned int *bflag;         // [maxp + npix] batch_no once bD is published
+    unsigned long long *bval;    // [maxp + npix] batch_no << 32 | bits of D (blurred value
+                                 // minus L-without-blurs), published in one store
     unsigned long long *sel_status;
     float *beta_pow;             // [64] beta^m
     size_t max_pops, max_sel_tiles;

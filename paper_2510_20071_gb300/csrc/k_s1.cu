@@ -297,12 +297,19 @@ __global__ void __launch_bounds__(128) k_s1_blur(KParams kp, Bufs b)
         }
         bool done = !active;
         unsigned spins = 0;
+        float dv[9];  // published D of each tap's blur (the value and its flag in one word)
+#pragma unroll
+        for (int t = 0; t < 9; ++t) dv[t] = 0.f;
         while (__any_sync(0xFFFFFFFFu, !done)) {
             if (!done) {
                 bool ready = true;
 #pragma unroll
                 for (int t = 0; t < 9; ++t)
-                    if (tp[t].bl != NOBLUR && ld_acquire_u32(&b.bflag[tp[t].bl]) != g.batch_no) ready = false;
+                    if (tp[t].bl != NOBLUR) {
+                        const unsigned long long v = ld_acquire_u64b(&b.bval[tp[t].bl]);
+                        if ((unsigned)(v >> 32) != g.batch_no) ready = false;
+                        dv[t] = __uint_as_float((unsigned)v);
+                    }
                 if (ready) {
                     float acc = 0.f;
 #pragma unroll
@@ -310,12 +317,11 @@ __global__ void __launch_bounds__(128) k_s1_blur(KParams kp, Bufs b)
                         const int dx = t % 3 - 1, dy = t / 3 - 1;
                         // taps outside the sensor hold lnb = 0 and no blur: they add 0
                         float v = tp[t].lnb;
-                        if (tp[t].bl != NOBLUR) v += beta_pow(kp, b.beta_pow, tp[t].m) * __ldcg(&b.bD[tp[t].bl]);
+                        if (tp[t].bl != NOBLUR) v += beta_pow(kp, b.beta_pow, tp[t].m) * dv[t];
                         acc += wt[dx + 1] * wt[dy + 1] * v;
                     }
                     const float D = acc / wsum - lself;
-                    b.bD[s] = D;
-                    st_release_u32(&b.bflag[s], g.batch_no);
+                    st_release_u64b(&b.bval[s], ((unsigned long long)g.batch_no << 32) | __float_as_uint(D));
                     done = true;
                 } else if (++spins > SPIN_LIMIT) {
                     atomicOr(&ctrl->error, ERR_S1_WAIT);
@@ -341,14 +347,14 @@ __global__ void __launch_bounds__(256) k_s1_apply(KParams kp, Bufs b)
         if (bl == NOBLUR) continue;
         const int jb = b.bj[bl];
         const int ord_b = jb >= 0 ? (int)b.epos[jb] : -1;
-        b.L[pix] = b.plnb[last] + beta_pow(kp, b.beta_pow, info.z - 1 - ord_b) * __ldcg(&b.bD[bl]);
+        b.L[pix] = b.plnb[last] + beta_pow(kp, b.beta_pow, info.z - 1 - ord_b) * __uint_as_float((unsigned)__ldcg(&b.bval[bl]));
     }
     // pixels without events in this batch whose previous event was popped (and blurred) now
     for (unsigned s = blockIdx.x * blockDim.x + threadIdx.x; s < nb; s += gridDim.x * blockDim.x) {
         if (b.bj[s] >= 0) continue;
         const unsigned pix = b.bpix[s];
         if ((unsigned)b.s1_info[pix].x == g.batch_no) continue;
-        b.L[pix] += __ldcg(&b.bD[s]);
+        b.L[pix] += __uint_as_float((unsigned)__ldcg(&b.bval[s]));
     }
 }
 
