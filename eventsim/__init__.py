@@ -355,3 +355,83 @@ def random_events(W: int, H: int, n: int, seed: int, *, t_step_us: int = 1,
     t = np.arange(n, dtype=np.int64) * t_step_us
     return pack_events(torch.from_numpy(pix % W), torch.from_numpy(pix // W),
                        torch.from_numpy(p), torch.from_numpy(t))
+
+
+# batched serving: many streams of mixed sensors ------------------------------------
+
+SERVING_SENSORS = [(240, 180), (346, 260), (640, 480), (1280, 720)]
+
+
+def retime(ev: torch.Tensor, seconds: float) -> torch.Tensor:
+    """Rescale a stream's time stamps linearly (integer arithmetic, order kept) so that
+    it spans [0, seconds]: its mean event rate becomes n / seconds."""
+    out = ev.clone()
+    if ev.shape[0] == 0:
+        return out
+    t = ev[:, 1]
+    t0 = t[0]
+    span = max(int(t[-1].item() - t0.item()), 1)
+    out[:, 1] = (t - t0) * int(round(seconds * 1e6)) // span
+    return out
+
+
+def mixed_streams(n_streams: int = 32, seconds: float = 0.2, *, seed: int = 11,
+                  sensors=None, rate_lo: float = 0.5e6, rate_hi: float = 20e6,
+                  noise_frac: float = 0.02, device="cpu", min_events: int = 1000) -> list[dict]:
+    """Seeded streams for batched serving: stream i uses sensor i mod len(sensors) and a
+    mean event rate drawn log-uniformly from [rate_lo, rate_hi] events/s; its scene
+    alternates between the rotating Perlin texture and the sine+checker; its time stamps
+    are rescaled to span `seconds`.
+    Returns dicts {W, H, rate, scene, events}."""
+    sensors = sensors or SERVING_SENSORS
+    rng = np.random.Generator(np.random.Philox(seed))
+    scenes = ["perlin", "sine_checker"]
+    out = []
+    for i in range(n_streams):
+        W, H = sensors[i % len(sensors)]
+        rate = math.exp(rng.uniform(math.log(rate_lo), math.log(rate_hi)))
+        n = max(min_events, int(rate * seconds))
+        scene = scenes[i % len(scenes)]
+        ev = simulate(W, H, n, scene=scene, seed=seed * 1000 + i, noise_frac=noise_frac, device=device)
+        out.append(dict(W=W, H=H, rate=n / seconds, scene=scene, events=retime(ev, seconds)))
+    return out
+
+
+def request_times(n_streams: int, seconds: float, *, rate_hz: float = 100.0, seed: int = 12) -> list[list[int]]:
+    """Read-out request times (microseconds) per stream: a Poisson process of `rate_hz`
+    on [0, seconds] (exponential gaps), at least one request per stream at the end."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    end = int(round(seconds * 1e6))
+    out = []
+    for _ in range(n_streams):
+        ts, t = [], 0.0
+        while True:
+            t += rng.exponential(1e6 / rate_hz)
+            if t >= end:
+                break
+            ts.append(int(t))
+        ts.append(end)
+        out.append(ts)
+    return out
+
+
+def serving_schedule(streams: list[dict], requests: list[list[int]], tick_us: int = 1000):
+    """Replay order for batched serving: per tick [T, T + tick_us), every stream's events
+    with time stamps in the tick as one packet (index range lo:hi), then that tick's
+    read-out requests.  Returns [(T, [(i, lo, hi), ...], [(i, t_us), ...]), ...]."""
+    ends = [int(s["events"][-1, 1]) if s["events"].shape[0] else 0 for s in streams]
+    end = max(ends + [max(r) for r in requests if r])
+    tcols = [s["events"][:, 1].cpu().numpy() for s in streams]
+    reqs = [np.asarray(r, dtype=np.int64) for r in requests]
+    out = []
+    for T in range(0, end + 1, tick_us):
+        pushes, reads = [], []
+        for i, t in enumerate(tcols):
+            lo, hi = np.searchsorted(t, [T, T + tick_us], side="left")
+            if hi > lo:
+                pushes.append((i, int(lo), int(hi)))
+        for i, r in enumerate(reqs):
+            a, b = np.searchsorted(r, [T, T + tick_us], side="left")
+            reads.extend((i, int(x)) for x in r[a:b])
+        out.append((T, pushes, reads))
+    return out

@@ -92,6 +92,7 @@ typedef struct {
     uint64_t s1_blurs;             /* S1 in-place blurs applied (cumulative)               */
     uint64_t detector_big_pops;    /* detector steps whose many pops a whole warp counted  */
     uint64_t detector_ring_misses; /* popped-event links read past the staged ring         */
+    uint64_t detector_recenters;   /* batches whose window bands were rebuilt from samples */
 } fibar_stats_t;
 
 /* Stages of one read-out, in launch order (fibar_stage_times). */
@@ -164,6 +165,33 @@ int fibar_push_events(fibar_t *h, const fibar_event_t *ev, size_t n, int on_devi
  *   on_device = 0: out is host memory; the call waits for the result.
  * Errors: EINVAL, EORDER (t_us < previous read-out time), ECUDA, ETIMEOUT. */
 int fibar_readout(fibar_t *h, uint64_t t_us, float *out, int on_device, void *cuda_stream);
+
+/* Read out n handles together: for every i, what fibar_readout(hs[i], t_us[i], outs[i],
+ * 1, ...) does, with the work of different handles running concurrently on the device.
+ * The paper reconstructs one stream; this serves many streams of different sensors at
+ * once.  Each handle's pipeline goes to one of the library's internal CUDA streams
+ * (16 per device, created on the first call): the handles are dealt out by their
+ * pending event counts, largest first, each to the internal stream with the least work
+ * so far.  The work of all handles starts after the work already queued on
+ * `cuda_stream`, and work queued on `cuda_stream` after the call starts after all of it,
+ * so calls on one caller stream stay ordered.
+ *   hs[n], t_us[n], outs[n]: handles, read-out times, device images of W_i*H_i floats.
+ *   done_events: NULL, or n cudaEvent_t (passed as void*, NULL entries skipped); entry
+ *                i is recorded when handle i's image is complete.
+ *   status:      NULL, or n ints that receive each handle's code as fibar_readout's.
+ * Returns FIBAR_OK, or the first non-zero status in index order (the other handles are
+ * still read out), or EINVAL before any work is queued when an array is NULL, n > 4096,
+ * a handle appears twice, or a handle belongs to a device that is not current.  Batch
+ * calls on one device from several host threads are serialised by the library. */
+int fibar_readout_batch(fibar_t *const *hs, const uint64_t *t_us, float *const *outs, size_t n,
+                        void *const *done_events, int *status, void *cuda_stream);
+
+/* Device memory in bytes that fibar_create(W, H, p) allocates (the sum of its buffers,
+ * each rounded up to 512 bytes; the CUDA context and the driver's page granularity are
+ * not included).  Host arithmetic only: needs no device.  The paper has no counterpart;
+ * a server uses it to admit streams by memory.  Errors: EINVAL (bytes NULL, or arguments
+ * that fibar_create rejects as EINVAL). */
+int fibar_memory_bytes(uint32_t W, uint32_t H, const fibar_params_t *p, uint64_t *bytes);
 
 /* Apply every pending event (as a read-out at t = +inf without output; does not
  * change the read-out time order). */

@@ -10,5 +10,6 @@ from .binding import (  # noqa: F401
     FibarError, FibarParams, FibarStats, FibarStateView, Fibar, load_library, library_path,
     fibar_default_params, fibar_create, fibar_push_events, fibar_readout, fibar_flush,
     fibar_debug_state, fibar_stats, fibar_set_timing, fibar_stage_times, fibar_last_error,
-    fibar_destroy, EXPORTED, STAGES, FibarStageTimes,
+    fibar_destroy, fibar_queue_counts_noalloc, fibar_readout_batch, fibar_memory_bytes,
+    memory_bytes, readout_batch, EXPORTED, STAGES, FibarStageTimes,
 )

@@ -23,7 +23,8 @@ FIBAR_ETIMEOUT = -5
 
 EXPORTED = ["fibar_default_params", "fibar_create", "fibar_push_events", "fibar_readout",
             "fibar_flush", "fibar_debug_state", "fibar_stats", "fibar_set_timing",
-            "fibar_stage_times", "fibar_last_error", "fibar_destroy", "fibar_queue_counts_noalloc"]
+            "fibar_stage_times", "fibar_last_error", "fibar_destroy", "fibar_queue_counts_noalloc",
+            "fibar_readout_batch", "fibar_memory_bytes"]
 
 STAGES = ["decode", "sort", "walk", "det_counts", "det_pass1", "det_pass2", "det_fix", "s1_blur",
           "readout", "commit"]
@@ -48,7 +49,7 @@ class FibarStats(C.Structure):
                                           "n_at", "detector_fixups", "kernel_launches",
                                           "detector_unmerged", "detector_pass2_steps",
                                           "detector_fix_steps", "s1_blurs", "detector_big_pops",
-                                          "detector_ring_misses"]]
+                                          "detector_ring_misses", "detector_recenters"]]
 
 
 class FibarStageTimes(C.Structure):
@@ -104,6 +105,11 @@ def load_library(build_if_missing: bool = True):
             lib.fibar_destroy.restype = None
             lib.fibar_queue_counts_noalloc.argtypes = [vp, vp, C.c_int, vp]
             lib.fibar_queue_counts_noalloc.restype = C.c_int
+            lib.fibar_readout_batch.argtypes = [C.POINTER(vp), C.POINTER(C.c_uint64), C.POINTER(vp), C.c_size_t,
+                                                C.POINTER(vp), C.POINTER(C.c_int), vp]
+            lib.fibar_readout_batch.restype = C.c_int
+            lib.fibar_memory_bytes.argtypes = [C.c_uint32, C.c_uint32, C.POINTER(FibarParams), C.POINTER(C.c_uint64)]
+            lib.fibar_memory_bytes.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -160,6 +166,23 @@ def fibar_destroy(h) -> None:
 
 def fibar_queue_counts_noalloc(h, cnt_ptr: int, on_device: int, stream: int) -> int:
     return load_library().fibar_queue_counts_noalloc(h, cnt_ptr, on_device, stream)
+
+
+def fibar_readout_batch(hs, t_us, outs, done_events, status, stream: int) -> int:
+    """hs, outs, done_events: sequences of raw pointers (ints or None); t_us: ints;
+    status: a ctypes c_int array of len(hs), or None."""
+    n = len(hs)
+    H = (C.c_void_p * n)(*hs)
+    T = (C.c_uint64 * n)(*t_us)
+    O = (C.c_void_p * n)(*outs)
+    D = (C.c_void_p * n)(*done_events) if done_events is not None else None
+    return load_library().fibar_readout_batch(H, T, O, n, D, status, stream)
+
+
+def fibar_memory_bytes(W: int, H: int, params: FibarParams | None):
+    b = C.c_uint64()
+    rc = load_library().fibar_memory_bytes(W, H, C.byref(params) if params is not None else None, C.byref(b))
+    return rc, int(b.value)
 
 
 # --- convenience wrapper ---------------------------------------------------------------
@@ -267,6 +290,12 @@ class Fibar:
         self._check(fibar_queue_counts_noalloc(self.h, out.data_ptr(), 1 if out.is_cuda else 0, self._s))
         return out
 
+    def memory_bytes(self) -> int:
+        """Device bytes this handle allocated (fibar_memory_bytes of its parameters)."""
+        rc, b = fibar_memory_bytes(self.W, self.H, self.params)
+        self._check(rc)
+        return b
+
     def state(self) -> dict:
         npix = self.W * self.H
         ntiles = ((self.W + 1) // 2) * ((self.H + 1) // 2)
@@ -279,3 +308,58 @@ class Fibar:
         for k in ["k", "h", "q", "q_targ", "n_ap", "n_at"]:
             out[k] = int(getattr(v, k))
         return out
+
+
+def memory_bytes(W: int, H: int, **params) -> int:
+    """Device bytes a handle for a W x H sensor with these parameters allocates (host
+    arithmetic in the library; needs no device)."""
+    p = fibar_default_params()
+    for k, v in params.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k!r}")
+        setattr(p, k, v)
+    rc, b = fibar_memory_bytes(int(W), int(H), p)
+    if rc != 0:
+        raise FibarError(rc, "fibar_memory_bytes rejected the arguments")
+    return b
+
+
+def readout_batch(fibars, t_us, outs=None, done_events=None, stream=None):
+    """Read out several :class:`Fibar` handles together (``fibar_readout_batch``).
+
+    ``outs``: CUDA float32 tensors of each handle's W*H (default: new ones);
+    ``done_events``: optional ``torch.cuda.Event`` per handle (or None entries), each
+    recorded when that handle's image is complete.  Returns the list of images; raises
+    :class:`FibarError` naming the first failing handle."""
+    import torch
+    n = len(fibars)
+    if len(t_us) != n:
+        raise ValueError("one read-out time per handle")
+    if outs is None:
+        outs = [torch.empty((f.H, f.W), dtype=torch.float32, device="cuda") for f in fibars]
+    for f, o in zip(fibars, outs):
+        if (o.dtype != torch.float32 or not o.is_cuda or o.numel() != f.W * f.H
+                or not o.is_contiguous()):
+            raise TypeError("outs must be contiguous CUDA float32 tensors of W*H elements")
+    ev_ptrs = None
+    if done_events is not None:
+        ev_ptrs = []
+        for ev in done_events:
+            if ev is None:
+                ev_ptrs.append(None)
+                continue
+            if not ev.cuda_event:  # created lazily by torch: make it exist
+                ev.record()
+            ev_ptrs.append(ev.cuda_event)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    status = (C.c_int * n)()
+    rc = fibar_readout_batch([f.h.value for f in fibars], [int(t) for t in t_us],
+                             [o.data_ptr() for o in outs], ev_ptrs, status, s.cuda_stream)
+    for f in fibars:
+        f._rotate()
+    if rc != 0:
+        for i, f in enumerate(fibars):
+            if status[i] != 0:
+                raise FibarError(status[i], f"handle {i}: {fibar_last_error(f.h)}")
+        raise FibarError(rc, "fibar_readout_batch rejected the arguments")
+    return outs

@@ -51,7 +51,7 @@ void free_all(fibar_t *h)
     Bufs &b = h->b;
     void *ptrs[] = {b.ctrl, b.pbar, b.L, b.last_pix, b.last_tile, b.staging, b.carry[0], b.carry[1],
                     b.dec_status, b.rec[0], b.rec[1], b.sort_hist, b.sort_base, b.sort_rows, b.sort_rowflag, b.sort_gtot, b.sort_gflag, b.sort_gcount,
-                    b.qout, b.ring4, b.ring_pix, b.bucket_start, b.bucket_cnt, b.dMt, b.det_base, b.E0, b.E1, b.E2, b.p2_ids, b.merged, b.unm_bits,
+                    b.qout, b.ring4, b.ring_pix, b.bucket_start, b.bucket_cnt, b.dMt, b.det_base, b.det_prof, b.band_ctr, b.E0, b.E1, b.E2, b.p2_ids, b.merged, b.unm_bits,
                     b.out_staging, b.dbg_cnt, b.plist, b.plnb, b.epos, b.lbl, b.s1_info, b.s1_linit,
                     b.popk, b.blur_ord, b.bk, b.bpix, b.bj, b.bval, b.sel_status, b.beta_pow};
     for (void *p : ptrs)
@@ -80,10 +80,21 @@ extern "C" void fibar_default_params(fibar_params_t *p)
     p->max_pending = 0;
 }
 
-extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fibar_t **out)
+namespace {
+
+// The handle's derived constants: the filter coefficients (Eqs. 16-18), the kernel
+// parameters and the buffer capacities.  Shared by fibar_create and fibar_memory_bytes.
+struct Layout {
+    fibar_params_t p;
+    KParams kp;
+    Bufs b;  // capacities only (no pointers)
+    double alpha, beta;
+    unsigned long long R;
+    uint32_t sort_passes;
+};
+
+int derive_layout(uint32_t W, uint32_t H, const fibar_params_t *pp, Layout &lo)
 {
-    if (!out) return FIBAR_EINVAL;
-    *out = nullptr;
     fibar_params_t p;
     if (pp) p = *pp; else fibar_default_params(&p);
     const unsigned long long npix = (unsigned long long)W * H;
@@ -98,34 +109,29 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     if (qmin > npix || qinit < qmin || qinit > npix) return FIBAR_EINVAL;
     const unsigned long long maxp = p.max_pending ? p.max_pending : (8ull << 20);
     if (maxp > (1ull << 27)) return FIBAR_EINVAL;
-
-    fibar_t *h = new (std::nothrow) fibar_s();
-    if (!h) return FIBAR_ENOMEM;
-    memset(&h->b, 0, sizeof(h->b));
-    h->params = p;
-    h->params.max_pending = (uint32_t)maxp;
-    h->W = W;
-    h->H = H;
-    cudaGetDevice(&h->device);
+    p.max_pending = (uint32_t)maxp;
+    p.q_init = (uint32_t)qinit;
+    lo.p = p;
 
     // Eqs. 16-18 in double, then rounded once to the FP32 filter coefficients
     const double w = 2.0 * M_PI / p.t_cut;
     const double c = cos(w);
-    h->alpha = (1.0 - sin(w)) / c;
-    h->beta = (2.0 - c) - sqrt((2.0 - c) * (2.0 - c) - 1.0);
+    lo.alpha = (1.0 - sin(w)) / c;
+    lo.beta = (2.0 - c) - sqrt((2.0 - c) * (2.0 - c) - 1.0);
 
-    KParams &kp = h->kp;
+    KParams &kp = lo.kp;
+    memset(&kp, 0, sizeof(kp));
     kp.W = W;
     kp.H = H;
     kp.tiles_w = (W + 1) / 2;
     kp.tiles_h = (H + 1) / 2;
     kp.npix = (uint32_t)npix;
     kp.ntiles = kp.tiles_w * kp.tiles_h;
-    kp.a = (float)h->alpha;
-    kp.oma = (float)(1.0 - h->alpha);
-    kp.b = (float)h->beta;
-    kp.g = (float)(0.5 * (1.0 + h->beta));
-    kp.log2b = (float)log2(h->beta);
+    kp.a = (float)lo.alpha;
+    kp.oma = (float)(1.0 - lo.alpha);
+    kp.b = (float)lo.beta;
+    kp.g = (float)(0.5 * (1.0 + lo.beta));
+    kp.log2b = (float)log2(lo.beta);
     kp.c_on = p.c_on;
     kp.c_off = p.c_off;
     kp.q_min = (uint32_t)qmin;
@@ -140,81 +146,140 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     // walk sorts each bucket by the low lb bits in shared memory
     kp.lb = std::min<unsigned>(9u, bits);
     kp.nbuckets = (kp.ntiles + (1u << kp.lb) - 1) >> kp.lb;
-    h->sort_passes = (bits - kp.lb + RADIX_BITS - 1) / RADIX_BITS;
+    lo.sort_passes = (bits - kp.lb + RADIX_BITS - 1) / RADIX_BITS;
     kp.spatial = p.spatial_filter;
     kp.blur_mode = p.blur_mode;
     // event ring: the batch plus everything a window (or a guessed window) can reach back
-    h->R = next_pow2(maxp + npix + 8ull * 256);
-    kp.ring_mask = h->R - 1;
-    kp.live = h->R - maxp;
+    lo.R = next_pow2(maxp + npix + 8ull * 256);
+    kp.ring_mask = lo.R - 1;
+    kp.live = lo.R - maxp;
 
-    Bufs &b = h->b;
+    Bufs &b = lo.b;
+    memset(&b, 0, sizeof(b));
     b.max_dec_tiles = (maxp + DEC_TILE - 1) / DEC_TILE + 1;
     b.max_sort_tiles = (maxp + SORT_TILE - 1) / SORT_TILE + 1;
     b.max_chunks = std::min<unsigned long long>((maxp + CHUNK - 1) / CHUNK, DET_MAX_CHUNKS) + 1;
     b.mt_rows = b.max_chunks;
+    b.n_samples = b.max_chunks / DET_SAMPLE + 2;
+    b.max_pops = maxp + npix + 8;
+    b.max_sel_tiles = (b.max_pops + 4095) / 4096 + 1;
+    return FIBAR_OK;
+}
+
+// Every device buffer of a handle with layout lo, as f(pointer, element count).
+template <class F>
+void for_each_buffer(const Layout &lo, Bufs &b, F &&f)
+{
+    const unsigned long long npix = lo.kp.npix, maxp = lo.kp.max_pending, R = lo.R;
+    const KParams &kp = lo.kp;
+    f(b.ctrl, 1);
+    f(b.pbar, npix);
+    f(b.L, npix);
+    f(b.last_pix, npix);
+    f(b.last_tile, kp.ntiles);
+    f(b.staging, maxp);
+    f(b.carry[0], maxp);
+    f(b.carry[1], maxp);
+    f(b.dec_status, b.max_dec_tiles);
+    f(b.rec[0], maxp);
+    f(b.rec[1], maxp);
+    f(b.sort_hist, SORT_MAX_PASSES * RADIX);
+    f(b.sort_base, SORT_MAX_PASSES * RADIX);
+    f(b.sort_rows, b.max_sort_tiles * RADIX);
+    f(b.sort_rowflag, b.max_sort_tiles);
+    f(b.sort_gtot, (b.max_sort_tiles / LB_GROUP + 1) * RADIX);
+    f(b.sort_gflag, b.max_sort_tiles / LB_GROUP + 1);
+    f(b.sort_gcount, b.max_sort_tiles / LB_GROUP + 1);
+    f(b.out_staging, npix);
+    f(b.bucket_start, kp.nbuckets);
+    f(b.bucket_cnt, kp.nbuckets);
+    if (lo.p.spatial_filter) {
+        f(b.qout, maxp);
+        f(b.ring4, R);
+        f(b.ring_pix, R);
+        f(b.dMt, 2 * b.mt_rows * 256);
+        f(b.det_base, 4 * b.mt_rows);
+        f(b.det_prof, 2 * b.n_samples * 640);
+        f(b.band_ctr, b.n_samples);
+        f(b.E0, b.max_chunks);
+        f(b.E1, b.max_chunks);
+        f(b.E2, b.max_chunks);
+        f(b.p2_ids, b.max_chunks);
+        f(b.merged, b.max_chunks);
+        f(b.unm_bits, b.max_chunks / 32 + 2);
+    }
+    if (lo.p.spatial_filter && lo.p.blur_mode == 0) {
+        f(b.plist, maxp);
+        f(b.plnb, maxp);
+        f(b.epos, maxp);
+        f(b.lbl, maxp);
+        f(b.s1_info, npix);
+        f(b.s1_linit, npix);
+        f(b.popk, b.max_pops);
+        f(b.blur_ord, b.max_pops);
+        f(b.bk, b.max_pops);
+        f(b.bpix, b.max_pops);
+        f(b.bj, b.max_pops);
+        f(b.bval, b.max_pops);
+        f(b.sel_status, b.max_sel_tiles);
+        f(b.beta_pow, 64);
+    }
+}
+
+}  // namespace
+
+extern "C" int fibar_memory_bytes(uint32_t W, uint32_t H, const fibar_params_t *p, uint64_t *bytes)
+{
+    if (!bytes) return FIBAR_EINVAL;
+    Layout lo;
+    const int rc = derive_layout(W, H, p, lo);
+    if (rc) return rc;
+    Bufs b = lo.b;
+    uint64_t total = 0;
+    for_each_buffer(lo, b, [&](auto *ptr, unsigned long long n) {
+        // cudaMalloc hands out whole 512-byte blocks (at least one per buffer)
+        const uint64_t sz = (uint64_t)std::max<unsigned long long>(n, 1) * sizeof(*ptr);
+        total += (sz + 511) & ~uint64_t(511);
+    });
+    *bytes = total;
+    return FIBAR_OK;
+}
+
+extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fibar_t **out)
+{
+    if (!out) return FIBAR_EINVAL;
+    *out = nullptr;
+    Layout lo;
+    if (derive_layout(W, H, pp, lo) != FIBAR_OK) return FIBAR_EINVAL;
+    const fibar_params_t &p = lo.p;
+    const unsigned long long npix = (unsigned long long)W * H;
+    const unsigned long long qinit = p.q_init;
+
+    fibar_t *h = new (std::nothrow) fibar_s();
+    if (!h) return FIBAR_ENOMEM;
+    h->params = p;
+    h->W = W;
+    h->H = H;
+    cudaGetDevice(&h->device);
+    h->alpha = lo.alpha;
+    h->beta = lo.beta;
+    h->kp = lo.kp;
+    const KParams &kp = h->kp;
+    h->sort_passes = lo.sort_passes;
+    h->R = lo.R;
+    h->b = lo.b;
+    Bufs &b = h->b;
+
     cudaError_t e = cudaSuccess;
-#define ALLOC(ptr, n)                                  \
-    if (e == cudaSuccess) e = dalloc(&(ptr), (n));
-    ALLOC(b.ctrl, 1);
+    for_each_buffer(lo, b, [&](auto *&ptr, unsigned long long n) {
+        if (e == cudaSuccess) e = dalloc(&ptr, n);
+    });
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&h->snap_host, 2 * sizeof(unsigned), cudaHostAllocMapped);
     if (e == cudaSuccess) {
         h->snap_host[0] = 0u;
         h->snap_host[1] = 0u;
         e = cudaHostGetDevicePointer((void **)&b.snap, h->snap_host, 0);
     }
-    ALLOC(b.pbar, npix);
-    ALLOC(b.L, npix);
-    ALLOC(b.last_pix, npix);
-    ALLOC(b.last_tile, kp.ntiles);
-    ALLOC(b.staging, maxp);
-    ALLOC(b.carry[0], maxp);
-    ALLOC(b.carry[1], maxp);
-    ALLOC(b.dec_status, b.max_dec_tiles);
-    ALLOC(b.rec[0], maxp);
-    ALLOC(b.rec[1], maxp);
-    ALLOC(b.sort_hist, SORT_MAX_PASSES * RADIX);
-    ALLOC(b.sort_base, SORT_MAX_PASSES * RADIX);
-    ALLOC(b.sort_rows, b.max_sort_tiles * RADIX);
-    ALLOC(b.sort_rowflag, b.max_sort_tiles);
-    ALLOC(b.sort_gtot, (b.max_sort_tiles / LB_GROUP + 1) * RADIX);
-    ALLOC(b.sort_gflag, b.max_sort_tiles / LB_GROUP + 1);
-    ALLOC(b.sort_gcount, b.max_sort_tiles / LB_GROUP + 1);
-    ALLOC(b.out_staging, npix);
-    ALLOC(b.bucket_start, kp.nbuckets);
-    ALLOC(b.bucket_cnt, kp.nbuckets);
-    if (p.spatial_filter) {
-        ALLOC(b.qout, maxp);
-        ALLOC(b.ring4, h->R);
-        ALLOC(b.ring_pix, h->R);
-        ALLOC(b.dMt, 2 * b.mt_rows * 256);
-        ALLOC(b.det_base, 2 * b.mt_rows);
-        ALLOC(b.E0, b.max_chunks);
-        ALLOC(b.E1, b.max_chunks);
-        ALLOC(b.E2, b.max_chunks);
-        ALLOC(b.p2_ids, b.max_chunks);
-        ALLOC(b.merged, b.max_chunks);
-        ALLOC(b.unm_bits, b.max_chunks / 32 + 2);
-    }
-    b.max_pops = maxp + npix + 8;
-    b.max_sel_tiles = (b.max_pops + 4095) / 4096 + 1;
-    if (p.spatial_filter && p.blur_mode == 0) {
-        ALLOC(b.plist, maxp);
-        ALLOC(b.plnb, maxp);
-        ALLOC(b.epos, maxp);
-        ALLOC(b.lbl, maxp);
-        ALLOC(b.s1_info, npix);
-        ALLOC(b.s1_linit, npix);
-        ALLOC(b.popk, b.max_pops);
-        ALLOC(b.blur_ord, b.max_pops);
-        ALLOC(b.bk, b.max_pops);
-        ALLOC(b.bpix, b.max_pops);
-        ALLOC(b.bj, b.max_pops);
-        ALLOC(b.bval, b.max_pops);
-        ALLOC(b.sel_status, b.max_sel_tiles);
-        ALLOC(b.beta_pow, 64);
-    }
-#undef ALLOC
     if (e != cudaSuccess) {
         free_all(h);
         cudaGetLastError();
@@ -236,7 +301,7 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     if (e == cudaSuccess) e = cudaMemsetAsync(b.bucket_cnt, 0, (size_t)kp.nbuckets * 4, s);
     if (e == cudaSuccess && p.spatial_filter) e = cudaMemsetAsync(b.ring_pix, 0, h->R * 4, s);
     if (e == cudaSuccess && b.unm_bits) e = cudaMemsetAsync(b.unm_bits, 0, (b.max_chunks / 32 + 2) * 4, s);
-    if (e == cudaSuccess && b.det_base) e = cudaMemsetAsync(b.det_base, 0, 2 * b.mt_rows * 4, s);
+    if (e == cudaSuccess && b.det_base) e = cudaMemsetAsync(b.det_base, 0, 4 * b.mt_rows * 4, s);
     if (e == cudaSuccess && b.s1_info) e = cudaMemsetAsync(b.s1_info, 0, npix * sizeof(int4), s);
     if (e == cudaSuccess && b.bval) e = cudaMemsetAsync(b.bval, 0, b.max_pops * 8, s);
     if (e == cudaSuccess && b.sel_status) e = cudaMemsetAsync(b.sel_status, 0, b.max_sel_tiles * 8, s);
@@ -548,6 +613,7 @@ extern "C" int fibar_stats(fibar_t *h, fibar_stats_t *st, void *cuda_stream)
     st->s1_blurs = c.s1_blurs;
     st->detector_big_pops = c.big_pops;
     st->detector_ring_misses = c.ring_misses;
+    st->detector_recenters = c.recenters;
     return rc;
 }
 

@@ -41,6 +41,7 @@ constexpr uint32_t CHUNK = 64;                 // minimum detector chunk length 
 constexpr unsigned DET_G = 1023;               // reach of the guessed windows, in chunks
 constexpr unsigned DET_WARM = 32;              // steps a chunk runs from its guess before its own steps
 constexpr unsigned DET_MAX_CHUNKS = 32768;     // chunks per batch at most (S grows beyond)
+constexpr unsigned DET_SAMPLE = 32;            // chunks between sampled regulator windows
 constexpr int LB_WIN = 8;                      // look-back window (predecessor tiles per load round)
 constexpr int LB_GROUP = 32;                   // sort tiles per published group total
 constexpr unsigned SPIN_LIMIT = 1u << 20;      // bounded device waits (~1 s)
@@ -73,7 +74,13 @@ struct Ctrl {
     unsigned int error;
     unsigned int unmerged;       // chunks whose second detector pass did not merge
     unsigned int fixups;         // batches that needed the serial detector fixup
-    unsigned int S, nchunks, g_lo, Gold;  // detector geometry of the batch (k_det_hist)
+    unsigned int S, nchunks, Gold;  // detector geometry of the batch (k_det_hist)
+    unsigned int band_mid0;       // window band: centre at the batch start, in chunks,
+    int band_slope;               //   and its drift per chunk (16.16 fixed point)
+    unsigned int band_mode;       // 0: bands from (mid0, slope); 1: from the sampled centres
+    unsigned long long recenters; // batches whose bands were rebuilt from the samples
+    long long grow_num;           // queue growth over the last batch (events) ...
+    unsigned int grow_den;        //   ... and that batch's length (0: none yet)
     unsigned int batch_no;       // read-outs/flushes committed (epoch of S1 flags)
     DetState det;                // detector state at the batch start (h global)
     long long h_prev;            // global h before the current batch (set by the fixup)
@@ -135,7 +142,10 @@ struct Bufs {
     unsigned int *bucket_cnt;    // [nbuckets] scratch histogram
     // detector chunk data
     unsigned short *dMt;         // [2][mt_rows][256] band of suffix histograms by target chunk
-    unsigned int *det_base;      // [2][mt_rows] window counts below the band (zero between batches)
+    unsigned int *det_base;      // [2 builds][2][mt_rows] window counts below the band (zero between batches)
+    unsigned short *det_prof;    // [2][n_samples][640] window table columns of the sampled chunks
+    unsigned short *band_ctr;    // [n_samples] regulator window (chunks) at the sampled chunks
+    size_t n_samples;
     size_t mt_rows;              // chunk rows per table of dMt
     DetState *E0, *E1, *E2;
     unsigned int *p2_ids;        // [max_chunks] chunks continued by the warp-per-chunk pass 2

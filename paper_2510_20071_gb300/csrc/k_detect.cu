@@ -29,41 +29,94 @@
 
 namespace fibar {
 
-// The window table holds a band of DET_BAND distances [g_lo, g_lo + DET_BAND) starting
-// 64 chunks below the regulator's window at the batch start (q / S chunks, at most
-// DET_G / 2 by the choice of S), so that a queue that grows within the batch still finds
-// its window; distances below g_lo enter only through their sum N(c, g_lo - 1).  A
-// queue that shrinks below the band only makes the guess longer than the regulator's
-// window, which the first steps correct.  While the queue is short (a stream's first
-// read-out, or after it collapsed) S is raised so that the band reaches npix / 16 events.
+// The window table holds, per target chunk c, a band of DET_BAND distances
+// [g_lo(c), g_lo(c) + DET_BAND) centred on the chunk's expected window; distances below
+// g_lo(c) enter only through their sum N(c, g_lo(c) - 1).  First build: the expected
+// queue length starts at the batch's q and drifts at the rate the queue grew (or shrank)
+// over the previous batch.  The same pass stores the whole column of distances 1..639 of
+// every DET_SAMPLE-th chunk, from which k_det_center finds the regulator's window there;
+// if a sampled window falls outside its band (a queue that fills after a stream starts,
+// or jumps with the scene), the table is built a second time with bands centred on the
+// sampled windows, interpolated between samples.  A window that still leaves its band
+// only makes that chunk's guess wrong, which pass 2 and the fixup correct.  While the
+// queue is short S is raised so that the band reaches npix / 16 events (npix / 3 in a
+// stream's first batch, which starts from an empty queue).
 constexpr unsigned DET_BAND = 256;
-constexpr int HB_BINS = 640;  // histogram bins (distances 0..639 >= the band's end)
+constexpr int HB_BINS = 640;  // histogram bins: chunk distances 0..639
+constexpr unsigned GROW_MIN_EVENTS = 2048;  // shorter batches give no growth estimate
+constexpr unsigned BAND_MARGIN = 16;        // sampled windows this close to a band's edge rebuild
 
 struct Geo {
     unsigned long long base;
     unsigned m, S, nchunks, Gold;
-    unsigned g_lo, g_hi;  // band of stored distances [g_lo, g_hi]
+    unsigned mid0;      // first build: band centre at chunk 0 (chunks) ...
+    int slope;          //   ... drifting per chunk, 16.16 fixed point
+    unsigned g_lo_min, g_hi_max;  // union of the first build's bands
 };
 
+__device__ __forceinline__ unsigned band_clamp(long long mid)
+{
+    return (unsigned)max(1ll, min((long long)(HB_BINS - DET_BAND), mid - (long long)(DET_BAND / 2)));
+}
+
+// First distance of chunk c's band in the first build.
+__device__ __forceinline__ unsigned band_lo_lin(unsigned mid0, int slope, long long c)
+{
+    return band_clamp((long long)mid0 + ((long long)slope * c) / 65536);
+}
+
+// First distance of chunk c's band in the second build: the sampled windows at chunks
+// DET_SAMPLE * s (s = 1..ns), linear in between, constant beyond the ends.
+__device__ __forceinline__ unsigned band_lo_tab(const unsigned short *ctr, unsigned ns, long long c)
+{
+    const long long s0 = c / DET_SAMPLE;
+    if (s0 < 1) return band_clamp(ctr[1]);
+    if (s0 >= (long long)ns) return band_clamp(ctr[ns]);
+    const long long a = ctr[s0], b = ctr[s0 + 1], r = c - s0 * DET_SAMPLE;
+    return band_clamp(a + (b - a) * r / (long long)DET_SAMPLE);
+}
+
+__device__ __forceinline__ unsigned n_samples_of(unsigned nchunks)
+{
+    return nchunks > 0 ? (nchunks - 1) / DET_SAMPLE : 0u;
+}
+
 // Chunk length S: at least CHUNK, at most DET_MAX_CHUNKS chunks per batch, and DET_G
-// chunks must cover twice the queue length at the batch start.
+// chunks must cover twice the longest queue expected in the batch.
 __device__ __forceinline__ Geo geometry(const KParams &kp, const Ctrl *ctrl)
 {
     Geo g;
     g.base = ctrl->base;
     g.m = ctrl->m;
     const unsigned long long qprev = g.base - (unsigned long long)ctrl->det.h;
-    unsigned long long S = (2ull * qprev + 4ull * CHUNK + DET_G - 1) / DET_G;
+    // growth per event over the previous batch, within [-1, 1] (16.16)
+    long long slope = 0;
+    if (ctrl->grow_den >= GROW_MIN_EVENTS) {
+        slope = ctrl->grow_num * 65536 / (long long)ctrl->grow_den;
+        slope = max(-65536ll, min(65536ll, slope));
+    }
+    const long long q_end = max((long long)kp.q_min,
+                                min((long long)kp.q_max, (long long)qprev + slope * (long long)g.m / 65536));
+    const unsigned long long q_hi = max(qprev, (unsigned long long)q_end);
+    unsigned long long S = (2ull * q_hi + 4ull * CHUNK + DET_G - 1) / DET_G;
     S = max(S, ((unsigned long long)g.m + DET_MAX_CHUNKS - 1) / DET_MAX_CHUNKS);
-    if (qprev < kp.npix / 32) S = max(S, ((unsigned long long)kp.npix + 16ull * DET_BAND - 1) / (16ull * DET_BAND));
+    if (qprev < kp.npix / 32) {
+        // a short queue: the band must reach npix / 16 events, or npix / 3 in a stream's
+        // first batch (no growth measured yet, and the queue may fill a third of the sensor)
+        const unsigned long long reach = ctrl->grow_den == 0 ? 3ull : 16ull;
+        S = max(S, ((unsigned long long)kp.npix + reach * DET_BAND - 1) / (reach * DET_BAND));
+    }
     S = (S + 15) / 16 * 16;
     g.S = (unsigned)max((unsigned long long)CHUNK, S);
     g.nchunks = (g.m + g.S - 1) / g.S;
-    const unsigned long long mid = qprev / g.S;  // <= 511 by the choice of S
-    g.g_lo = (unsigned)min((unsigned long long)HB_BINS - DET_BAND, mid > 128 ? mid - 128 : 1ull);
-    g.g_hi = g.g_lo + DET_BAND - 1;
+    g.mid0 = (unsigned)(qprev / g.S);  // <= 511 by the choice of S
+    g.slope = (int)slope;
+    const unsigned a = band_lo_lin(g.mid0, g.slope, 0), b = band_lo_lin(g.mid0, g.slope, g.nchunks);
+    g.g_lo_min = min(a, b);
+    g.g_hi_max = max(a, b) + DET_BAND - 1;
+    // old chunks as far back as the sampled columns reach
     const unsigned long long old_chunks = (g.base + g.S - 1) / g.S;
-    g.Gold = (unsigned)min((unsigned long long)g.g_hi, old_chunks);
+    g.Gold = (unsigned)min((unsigned long long)(HB_BINS - 1), old_chunks);
     return g;
 }
 
@@ -94,9 +147,10 @@ __device__ __forceinline__ long long chunk_of(long long x, unsigned S, unsigned 
 //   M(c, g) = #{j in chunk c-g : next(j) >= cS}          (per t = 0 pixels, 1 tiles)
 // i.e. the events of chunk c-g still last of their pixel / tile at the start of chunk c
 // (source chunks reach back to -Gold).  The distinct counts of the aligned window
-// [(c-g)S, cS) are N(c, g) = sum_{g'=1..g} M(c, g').  Stored per target chunk c:
-//   base[t][c]          = N(c, g_lo - 1)               (accumulated with atomics)
-//   Mt[t][c][g - g_lo]  = M(c, g) for g in [g_lo, g_hi]  (a contiguous row)
+// [(c-g)S, cS) are N(c, g) = sum_{g'=1..g} M(c, g').  Stored per target chunk c, with
+// its band [g_lo(c), g_hi(c)]:
+//   base[t][c]             = N(c, g_lo(c) - 1)                (accumulated with atomics)
+//   Mt[t][c][g - g_lo(c)]  = M(c, g) for g in [g_lo(c), g_hi(c)]  (a contiguous row)
 // A block handles HB_CHUNKS consecutive source chunks and one t: the histogram of chunk
 // distances in shared memory (one word of padding per 32 bins and a row pitch of 2 mod
 // 32 words, so that a lane's run of 32 bins and the diagonal reads both spread over the
@@ -113,18 +167,31 @@ struct HistSmem {
     unsigned h[HB_CHUNKS][HB_PITCH];
 };
 
+// kBuild 0: first build, bands from (mid0, slope), plus the sampled columns.
+// kBuild 1: second build, only when k_det_center asked for it (band_mode), bands from the
+//           sampled windows; its below-band sums go to the second set of counters.
+template <int kBuild>
 __global__ void __launch_bounds__(256)
-k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t mt_rows, unsigned *base_cnt)
+k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t mt_rows, unsigned *base_cnt,
+           unsigned short *prof, size_t n_samples, const unsigned short *ctr)
 {
     PDL_ENTRY();
+    if (kBuild == 1 && ctrl->band_mode == 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HistSmem &H = *reinterpret_cast<HistSmem *>(smem_raw);
     const Geo g = geometry(kp, ctrl);
+    const unsigned ns = n_samples_of(g.nchunks);
     const unsigned tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
     const unsigned nwork = g.nchunks + g.Gold;
     const unsigned nunits = 2 * ((nwork + HB_CHUNKS - 1) / HB_CHUNKS);
     const long long lo_exist = -(long long)g.base;
-    const int g_lo = (int)g.g_lo, g_hi = (int)g.g_hi;
+    // distances whose band entries some target may need
+    const int D0 = kBuild ? 1 : (int)g.g_lo_min;
+    const int g_hi_all = kBuild ? HB_BINS - 1 : (int)g.g_hi_max;
+    unsigned *bc = base_cnt + (size_t)kBuild * 2 * mt_rows;
+    auto band_of = [&](long long ct) -> int {
+        return kBuild ? (int)band_lo_tab(ctr, ns, ct) : (int)band_lo_lin(g.mid0, g.slope, ct);
+    };
     for (unsigned unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
         const int t = unit & 1;
         const long long c_lo = (long long)((unit >> 1) * HB_CHUNKS) - (long long)g.Gold;  // first source chunk
@@ -132,18 +199,18 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
         for (unsigned i = tid; i < HB_CHUNKS * HB_PITCH / 4; i += 256) hw[i] = make_uint4(0u, 0u, 0u, 0u);
         __syncthreads();
         // histogram of the chunk distance to the next event of the same pixel / tile
-        // (distances beyond g_hi counted at g_hi)
+        // (distances beyond the table counted at its last one)
         const long long j_lo = c_lo * g.S;
         const unsigned n_hi = (unsigned)min((long long)HB_CHUNKS * g.S, (long long)g.m - j_lo);
         const unsigned n_lo = (unsigned)max(0ll, lo_exist - j_lo);
-        const unsigned long long lim = (unsigned long long)g_hi * g.S;
+        const unsigned long long lim = (unsigned long long)(HB_BINS - 1) * g.S;
         for (unsigned i = n_lo + tid; i < n_hi; i += 256) {
             const unsigned long long j = g.base + (unsigned long long)(j_lo + i);
             const uint2 n = nxt_of(ring, j & kp.ring_mask);
             const unsigned nv = t ? n.y : n.x;
             const unsigned cc = i / g.S, r = i - cc * g.S;
             const unsigned long long rel = (unsigned long long)r + nv;  // from the start of chunk cc
-            const unsigned d = (nv == SAT || rel >= lim) ? (unsigned)g_hi
+            const unsigned d = (nv == SAT || rel >= lim) ? (unsigned)(HB_BINS - 1)
                              : (lim <= 0xFFFFFFFFull ? (unsigned)rel / g.S : (unsigned)(rel / g.S));
             atomicAdd(&H.h[cc][hb_slot((int)d)], 1u);
         }
@@ -171,35 +238,119 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
         }
         __syncthreads();
         // below the band: target c_lo + D gets sum_{cc} M at distance D - cc in [1, g_lo)
-        for (int D = 1 + (int)tid; D < HB_CHUNKS + g_lo - 1; D += 256) {
+        for (int D = 1 + (int)tid; D < HB_CHUNKS + g_hi_all - (int)DET_BAND; D += 256) {
             const long long ct = c_lo + D;
             if (ct < 1 || ct >= (long long)g.nchunks) continue;
+            const int gl = band_of(ct);
             unsigned acc = 0;
 #pragma unroll
             for (int cc = 0; cc < HB_CHUNKS; ++cc) {
                 const int d = D - cc;
-                if (d >= 1 && d < g_lo) acc += H.h[cc][hb_slot(d)];
+                if (d >= 1 && d < gl) acc += H.h[cc][hb_slot(d)];
             }
-            if (acc) atomicAdd(&base_cnt[(size_t)t * mt_rows + ct], acc);
+            if (acc) atomicAdd(&bc[(size_t)t * mt_rows + ct], acc);
         }
-        // the band: target row c_lo + D receives distances D-15 .. D from the block's
+        // the bands: target row c_lo + D receives distances D-15 .. D from the block's
         // sources; HB_CHUNKS threads write one row's run
         unsigned short *base_t = Mt + (size_t)t * mt_rows * MT_PITCH;
-        const int D0 = g_lo, D1 = g_hi + HB_CHUNKS - 1;  // targets with some band distance
+        const int D1 = g_hi_all + HB_CHUNKS - 1;  // targets with some band distance
         for (unsigned i = tid; i < (unsigned)(D1 - D0 + 1) * HB_CHUNKS; i += 256) {
             const int D = D0 + (int)(i / HB_CHUNKS), u = (int)(i % HB_CHUNKS);
             const int cc = HB_CHUNKS - 1 - u, d = D - cc;
             const long long ct = c_lo + D;  // target chunk
-            if (d >= g_lo && d <= g_hi && ct >= 1 && ct < (long long)g.nchunks)
-                base_t[(size_t)ct * MT_PITCH + (d - g_lo)] = (unsigned short)H.h[cc][hb_slot(d)];
+            if (ct < 1 || ct >= (long long)g.nchunks) continue;
+            const int gl = band_of(ct);
+            if (d >= gl && d < gl + (int)DET_BAND)
+                base_t[(size_t)ct * MT_PITCH + (d - gl)] = (unsigned short)H.h[cc][hb_slot(d)];
+        }
+        if (kBuild == 0 && ns > 0) {
+            // columns of the sampled targets DET_SAMPLE * s within reach of the sources:
+            // prof[t][s][d] = M(DET_SAMPLE * s, d), d in 1..639
+            const long long t_lo = c_lo + 1, t_hi = c_lo + HB_CHUNKS - 1 + (HB_BINS - 1);
+            const long long s_lo = max(1ll, (t_lo + DET_SAMPLE - 1 + (long long)DET_SAMPLE * 64) / DET_SAMPLE - 64);
+            const long long s_hi = min((long long)ns, t_hi >= 0 ? t_hi / DET_SAMPLE : -1ll);
+            const long long nsamp = s_hi - s_lo + 1;
+            unsigned short *pt = prof + (size_t)t * n_samples * HB_BINS;
+            for (long long i = tid; i < nsamp * HB_CHUNKS; i += 256) {
+                const long long sidx = s_lo + i / HB_CHUNKS;
+                const int cc = (int)(i % HB_CHUNKS);
+                const long long d = sidx * DET_SAMPLE - (c_lo + cc);
+                if (d >= 1 && d <= HB_BINS - 1)
+                    pt[(size_t)sidx * HB_BINS + d] = (unsigned short)H.h[cc][hb_slot((int)d)];
+            }
         }
         __syncthreads();
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (kBuild == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
         ctrl->S = g.S;
         ctrl->nchunks = g.nchunks;
-        ctrl->g_lo = g.g_lo;
+        ctrl->band_mid0 = g.mid0;
+        ctrl->band_slope = g.slope;
         ctrl->Gold = g.Gold;
+    }
+}
+
+// The regulator's window at every sampled chunk c = DET_SAMPLE * s (one warp each): the
+// shortest aligned window of the column prof[.][s][1..639] that the regulator would
+// shrink (the test of k_det_init), or the longest one that exists.  If one of them lies
+// outside (or within BAND_MARGIN of the edge of) the first build's band, band_mode asks
+// for the second build.
+__global__ void __launch_bounds__(256)
+k_det_center(KParams kp, Ctrl *ctrl, const unsigned short *prof, size_t n_samples, unsigned short *ctr)
+{
+    PDL_ENTRY();
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long base = ctrl->base;
+    const unsigned S = ctrl->S, nch = ctrl->nchunks, Gold = ctrl->Gold;
+    const unsigned mid0 = ctrl->band_mid0;
+    const int slope = ctrl->band_slope;
+    const unsigned ns = n_samples_of(nch);
+    const unsigned warps_total = gridDim.x * (blockDim.x >> 5);
+    constexpr int PER = HB_BINS / 32;  // distances per lane
+    bool out = false;
+    for (unsigned s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) + 1; s <= ns; s += warps_total) {
+        const unsigned c = s * DET_SAMPLE;
+        const unsigned gmax = min((unsigned)(HB_BINS - 1), c + Gold);  // sources that exist
+        const unsigned long long reach = (unsigned long long)c * S + base;
+        const unsigned short *pp = prof + (size_t)s * HB_BINS;
+        const unsigned short *pt = prof + ((size_t)n_samples + s) * HB_BINS;
+        unsigned ap[PER], at[PER], sp = 0, st = 0;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const unsigned gg = lane * PER + u;  // distance 0 is not a window
+            const bool ok = gg >= 1 && gg <= gmax;
+            sp += ok ? pp[gg] : 0u;
+            st += ok ? pt[gg] : 0u;
+            ap[u] = sp;
+            at[u] = st;
+        }
+        unsigned ip = sp, it = st;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned yp = __shfl_up_sync(0xFFFFFFFFu, ip, o), yt = __shfl_up_sync(0xFFFFFFFFu, it, o);
+            if (lane >= (unsigned)o) { ip += yp; it += yt; }
+        }
+        const unsigned op = ip - sp, ot = it - st;
+        unsigned mine = 0;
+#pragma unroll
+        for (int u = PER - 1; u >= 0; --u) {
+            const unsigned gg = lane * PER + u;
+            const unsigned long long np = op + ap[u], nt = ot + at[u];
+            const unsigned long long L = min((unsigned long long)gg * S, reach), q = L + 1;
+            if (gg >= 1 && gg <= gmax && np > 0 && q > kp.q_min &&
+                (q > kp.q_max || q * kp.den * np > L * kp.numA * nt))
+                mine = gg;
+        }
+        const unsigned any = __ballot_sync(0xFFFFFFFFu, mine != 0);
+        const unsigned w = any ? __shfl_sync(0xFFFFFFFFu, mine, __ffs(any) - 1) : gmax;
+        if (lane == 0) {
+            ctr[s] = (unsigned short)w;
+            const unsigned gl = band_lo_lin(mid0, slope, c);
+            out |= (w < gl + BAND_MARGIN || w + BAND_MARGIN > gl + DET_BAND - 1) && band_clamp(w) != gl;
+        }
+    }
+    if (out) {
+        if (atomicOr(&ctrl->band_mode, 1u) == 0u) atomicAdd(&ctrl->recenters, 1ull);
     }
 }
 
@@ -219,8 +370,8 @@ __device__ __forceinline__ unsigned q_target(const KParams &kp, unsigned long lo
 }
 
 // Speculative start of chunk c >= 1, one warp per chunk.
-// (1) The window: among the aligned windows of g in [g_lo, g_hi] chunks ending at cS
-//     (N(c, g_lo - 1) plus a prefix sum of one band row: 8 distances per lane, one
+// (1) The window: among the aligned windows of g in the chunk's band [g_lo, g_hi] of
+//     chunks ending at cS (N(c, g_lo - 1) plus a prefix sum of one band row: 8 distances per lane, one
 //     16-byte load per lane and type), the first that the regulator would shrink at the
 //     next event (Eq. 20); then, inside the chunk where that window starts, the shortest
 //     window, to the event, that would still be shrunk.  Its length is where the
@@ -238,28 +389,37 @@ __device__ __forceinline__ unsigned pick8(const unsigned (&a)[8], unsigned u)
 
 __global__ void __launch_bounds__(256)
 k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short *Mt, size_t mt_rows,
-           unsigned *base_cnt, DetState *E0, unsigned *qout)
+           unsigned *base_cnt, const unsigned short *ctr, DetState *E0, unsigned *qout)
 {
     PDL_ENTRY();
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long base = ctrl->base;
     const unsigned S = ctrl->S, nch = ctrl->nchunks, Gold = ctrl->Gold;
-    const unsigned g_lo = ctrl->g_lo, g_hi = g_lo + DET_BAND - 1;
+    const unsigned mid0 = ctrl->band_mid0;
+    const int slope = ctrl->band_slope;
+    const unsigned mode = ctrl->band_mode, ns = n_samples_of(nch);
+    unsigned *bc = base_cnt + (size_t)mode * 2 * mt_rows;
     const unsigned warps_total = gridDim.x * (blockDim.x >> 5);
     for (unsigned c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) + 1; c < nch; c += warps_total) {
+        const unsigned g_lo = mode ? band_lo_tab(ctr, ns, c) : band_lo_lin(mid0, slope, c);
+        const unsigned g_hi = g_lo + DET_BAND - 1;
         const unsigned short *rp = Mt + (size_t)c * MT_PITCH;
         const unsigned short *rt = Mt + (mt_rows + c) * MT_PITCH;
         const unsigned gmax = min(g_hi, c + Gold);  // sources that exist in the table
         const unsigned long long reach = (unsigned long long)c * S + base;  // events before the chunk
         // N(c, g_lo - 1), then cleared for the next batch's accumulation
-        const unsigned bp = base_cnt[c], bt = base_cnt[mt_rows + c];
+        const unsigned bp = bc[c], bt = bc[mt_rows + c];
         unsigned found = 0, snp = 0, snt = 0, fp1 = bp, ft1 = bt;
         const uint4 wp = *reinterpret_cast<const uint4 *>(rp + 8 * lane);
         const uint4 wt = *reinterpret_cast<const uint4 *>(rt + 8 * lane);
         __syncwarp();
         if (lane == 0) {
-            base_cnt[c] = 0;
-            base_cnt[mt_rows + c] = 0;
+            bc[c] = 0;
+            bc[mt_rows + c] = 0;
+            if (mode) {  // the first build's counters too
+                base_cnt[c] = 0;
+                base_cnt[mt_rows + c] = 0;
+            }
         }
         const unsigned xp[4] = {wp.x, wp.y, wp.z, wp.w}, xt[4] = {wt.x, wt.y, wt.z, wt.w};
         unsigned pp[8], pt[8];
@@ -946,19 +1106,26 @@ __global__ void k_det_fix(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *q
 
 cudaError_t launch_det_counts(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)
 {
-    nl += 2;
+    nl += 4;
     static bool attr_set = false;
     const size_t smem = sizeof(HistSmem);
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_det_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_det_hist<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_det_hist<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (cudaError_t e_ = launch_pdl(k_det_hist, grid_for(2), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
-                                    b.det_base))
+    if (cudaError_t e_ = launch_pdl(k_det_hist<0>, grid_for(2), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
+                                    b.det_base, b.det_prof, b.n_samples, (const unsigned short *)b.band_ctr))
+        return e_;
+    if (cudaError_t e_ = launch_pdl(k_det_center, grid_for(2), 256, 0, s, kp, b.ctrl, (const unsigned short *)b.det_prof,
+                                    b.n_samples, b.band_ctr))
+        return e_;
+    if (cudaError_t e_ = launch_pdl(k_det_hist<1>, grid_for(2), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
+                                    b.det_base, b.det_prof, b.n_samples, (const unsigned short *)b.band_ctr))
         return e_;
     if (cudaError_t e_ = launch_pdl(k_det_init, grid_for(8), 256, 0, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
-                                    b.det_base, b.E0, b.qout))
+                                    b.det_base, (const unsigned short *)b.band_ctr, b.E0, b.qout))
         return e_;
     return cudaGetLastError();
 }

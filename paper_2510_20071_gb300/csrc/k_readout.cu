@@ -66,8 +66,17 @@ __global__ void k_commit(Ctrl *ctrl, unsigned long long *dec_status, size_t n_st
     for (size_t i = threadIdx.x; i < n_status; i += blockDim.x) dec_status[i] = 0ull;
     __syncthreads();
     if (threadIdx.x == 0) {
+        if (ctrl->m > 0) {
+            // the queue's growth over this batch (the detector ran: h_prev is the h at
+            // the batch start), from which the next batch's window band drifts
+            const long long q0 = (long long)(ctrl->base - (unsigned long long)ctrl->h_prev);
+            const long long q1 = (long long)(ctrl->base + ctrl->m - (unsigned long long)ctrl->det.h);
+            ctrl->grow_num = q1 - q0;
+            ctrl->grow_den = ctrl->m;
+        }
         ctrl->base += ctrl->m;
         ctrl->m = 0;
+        ctrl->band_mode = 0;
         ctrl->dec_ticket = 0;
         for (int p = 0; p < SORT_MAX_PASSES; ++p) ctrl->sort_ticket[p] = 0;
         ctrl->unmerged = 0;
@@ -108,6 +117,10 @@ __global__ void k_init(KParams kp, Ctrl *ctrl)
     ctrl->p2_count = 0;
     ctrl->batch_no = 1;
     ctrl->h_prev = 0;
+    ctrl->grow_num = 0;
+    ctrl->grow_den = 0;
+    ctrl->band_mode = 0;
+    ctrl->recenters = 0;
     ctrl->nblur = 0;
     ctrl->blur_ticket = 0;
     ctrl->sel_ticket = 0;

@@ -1,0 +1,176 @@
+"""Serving many FIBAR streams from one process: device-resident state, admission by
+device memory, and read-out requests answered in concurrent batches.
+
+The paper reconstructs one camera and states that an image can be read out at any time
+(Sec. 1).  A server holds one library handle per admitted stream (its filter state, queue
+and rings stay in device memory between calls), pushes each stream's packets as they
+arrive, and answers read-out requests for arbitrary times: the requests that are due are
+issued together through ``fibar_readout_batch``, so the pipelines of different streams run
+side by side on the GPU.  Every request gets a CUDA event recorded when its image is
+complete; its latency is the device time from the batch's start to that event.
+
+:class:`Admission` is the memory accounting alone (host logic, no device), so that its
+rules can be checked without a GPU.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+from .binding import Fibar, FibarError, memory_bytes, readout_batch
+
+# per handle, on top of the library's count: the driver's allocation granularity
+HANDLE_SLACK_BYTES = 8 << 20
+
+
+class Admission:
+    """Admit streams while their device memory fits a budget.
+
+    ``budget``: bytes the server may hold.  ``bytes_fn(W, H, **params)``: the bytes a
+    handle needs (default: the library's ``fibar_memory_bytes``) plus a fixed slack."""
+
+    def __init__(self, budget: int, bytes_fn=None, slack: int = HANDLE_SLACK_BYTES):
+        if budget < 0:
+            raise ValueError("budget must be >= 0")
+        self.budget = int(budget)
+        self.bytes_fn = bytes_fn or memory_bytes
+        self.slack = int(slack)
+        self.held: dict[int, int] = {}
+        self.refused = 0
+        self._next = 0
+
+    @property
+    def used(self) -> int:
+        return sum(self.held.values())
+
+    def need(self, W: int, H: int, **params) -> int:
+        return int(self.bytes_fn(W, H, **params)) + self.slack
+
+    def try_admit(self, W: int, H: int, **params):
+        """The new stream's id, or None (refused) if it does not fit."""
+        need = self.need(W, H, **params)
+        if self.used + need > self.budget:
+            self.refused += 1
+            return None
+        sid = self._next
+        self._next += 1
+        self.held[sid] = need
+        return sid
+
+    def release(self, sid: int) -> None:
+        self.held.pop(sid)
+
+
+@dataclass
+class Request:
+    sid: int
+    t_us: int
+    image: object = None      # CUDA (H, W) float32 tensor, valid once `done` has completed
+    done: object = None       # torch.cuda.Event recorded when the image is complete
+    start: object = None      # torch.cuda.Event recorded before the batch that served it
+
+
+@dataclass
+class _Stream:
+    fib: Fibar
+    W: int
+    H: int
+    last_t: int = -1
+    queue: list = field(default_factory=list)  # pending Requests, in arrival order
+
+
+class Server:
+    """Device-resident FIBAR streams behind one loop.
+
+    ``budget``: device bytes for stream state (default: the free memory reported by
+    ``torch.cuda.mem_get_info`` minus ``reserve``)."""
+
+    def __init__(self, budget: int | None = None, reserve: int = 4 << 30, stream=None):
+        import torch
+        self.torch = torch
+        if budget is None:
+            free, _ = torch.cuda.mem_get_info()
+            budget = max(0, free - reserve)
+        self.admission = Admission(budget)
+        self.streams: dict[int, _Stream] = {}
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.batches = 0
+
+    def admit(self, W: int, H: int, **params):
+        """Create a stream's handle if its memory fits; returns its id or None."""
+        sid = self.admission.try_admit(W, H, **params)
+        if sid is None:
+            return None
+        try:
+            fib = Fibar(W, H, stream=self.stream, **params)
+        except FibarError:
+            self.admission.release(sid)
+            self.admission.refused += 1
+            return None
+        self.streams[sid] = _Stream(fib, W, H)
+        return sid
+
+    def release(self, sid: int) -> None:
+        st = self.streams.pop(sid)
+        st.fib.close()
+        self.admission.release(sid)
+
+    def push(self, sid: int, packet) -> None:
+        """Queue a packet (CUDA (n, 2) int64 event records) for the stream."""
+        self.streams[sid].fib.push(packet)
+
+    def request(self, sid: int, t_us: int) -> Request:
+        """Ask for the stream's image at t_us (not earlier than its previous request)."""
+        st = self.streams[sid]
+        if t_us < st.last_t:
+            raise ValueError(f"stream {sid}: read-out time {t_us} earlier than {st.last_t}")
+        st.last_t = t_us
+        r = Request(sid, int(t_us))
+        st.queue.append(r)
+        return r
+
+    def pending(self) -> int:
+        return sum(len(s.queue) for s in self.streams.values())
+
+    def serve(self) -> list[Request]:
+        """Answer every queued request: each batch takes the oldest request of every stream
+        that has one, so a stream's requests are served in order.  Returns them."""
+        torch = self.torch
+        served = []
+        while True:
+            batch = [(sid, st) for sid, st in self.streams.items() if st.queue]
+            if not batch:
+                return served
+            reqs = [st.queue.pop(0) for _, st in batch]
+            start = torch.cuda.Event(enable_timing=True)
+            start.record(self.stream)
+            for r, (_, st) in zip(reqs, batch):
+                r.image = torch.empty((st.H, st.W), dtype=torch.float32, device="cuda")
+                r.done = torch.cuda.Event(enable_timing=True)
+                r.start = start
+            readout_batch([st.fib for _, st in batch], [r.t_us for r in reqs],
+                          [r.image for r in reqs], [r.done for r in reqs], stream=self.stream)
+            self.batches += 1
+            served.extend(reqs)
+
+    def stats(self) -> dict:
+        out = {"streams": len(self.streams), "bytes_held": self.admission.used,
+               "budget": self.admission.budget, "refused": self.admission.refused,
+               "batches": self.batches, "kernel_launches": 0, "events_applied": 0}
+        for st in self.streams.values():
+            s = st.fib.stats()
+            out["kernel_launches"] += s["kernel_launches"]
+            out["events_applied"] += s["events_applied"]
+        return out
+
+    def close(self) -> None:
+        for sid in list(self.streams):
+            self.release(sid)
+
+
+def latencies_ms(requests) -> list[float]:
+    """Device time from each request's batch start to its image (synchronises)."""
+    out = []
+    for r in requests:
+        r.done.synchronize()
+        out.append(r.start.elapsed_time(r.done))
+    return out

@@ -1,0 +1,166 @@
+"""Batched serving on the GPU: fibar_readout_batch and the Server against the FP64 oracle,
+one stream at a time, on seeded streams of mixed sensors with read-out requests at random
+(Poisson) times."""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import eventsim
+from tests.harness import compare
+
+pytestmark = pytest.mark.gpu
+
+MODES = {
+    "nsf": dict(spatial_filter=0),
+    "s1": dict(spatial_filter=1, blur_mode=0),
+    "s2": dict(spatial_filter=1, blur_mode=1),
+}
+SENSORS = [(64, 48), (96, 72), (120, 90), (33, 17)]
+
+
+def _streams(n, seconds, seed):
+    return eventsim.mixed_streams(n, seconds, seed=seed, sensors=SENSORS, rate_lo=0.5e6, rate_hi=4e6)
+
+
+@pytest.mark.parametrize("mode", ["s2", "s1", "nsf"])
+def test_served_images_match_oracle_per_stream(oracle_mod, mode):
+    from paper_2510_20071_gb300.serving import Server, latencies_ms
+    params = dict(MODES[mode], c_on=0.2, c_off=0.2)
+    streams = _streams(6, 0.008, seed=21)
+    reqs = eventsim.request_times(6, 0.008, rate_hz=2500, seed=22)
+    sched = eventsim.serving_schedule(streams, reqs, tick_us=400)
+    dev = [s["events"].cuda() for s in streams]
+    srv = Server()
+    sids = [srv.admit(s["W"], s["H"], **params) for s in streams]
+    assert None not in sids
+    steps = [[] for _ in streams]
+    served = [[] for _ in streams]
+    try:
+        for T, pushes, reads in sched:
+            for i, lo, hi in pushes:
+                srv.push(sids[i], dev[i][lo:hi])
+                steps[i].append(("push", lo, hi))
+            for i, t in reads:
+                served[i].append(srv.request(sids[i], t))
+                steps[i].append(("read", t))
+            srv.serve()
+        assert srv.pending() == 0
+        torch.cuda.synchronize()
+        lat = latencies_ms([r for rs in served for r in rs])
+        assert all(x > 0 for x in lat)
+        for i, s in enumerate(streams):
+            W, H = s["W"], s["H"]
+            o = oracle_mod.Oracle(W, H, **params)
+            o_imgs = []
+            for st in steps[i]:
+                if st[0] == "push":
+                    o.push(s["events"][st[1]:st[2]])
+                else:
+                    o_imgs.append(o.readout(st[1]))
+            g_imgs = [r.image.cpu().numpy().astype(np.float64) for r in served[i]]
+            g_state = srv.streams[sids[i]].fib.state()
+            compare(W, H, o_imgs, [o.state()], g_imgs, [g_state], spatial=params["spatial_filter"] == 1)
+        st = srv.stats()
+        assert st["batches"] >= max(len(r) for r in reqs)
+        assert st["events_applied"] == sum(s["events"].shape[0] for s in streams)
+    finally:
+        srv.close()
+
+
+def _pushed_handles(streams, params):
+    from paper_2510_20071_gb300 import Fibar
+    hs = []
+    for s in streams:
+        f = Fibar(s["W"], s["H"], **params)
+        f.push(s["events"].cuda())
+        hs.append(f)
+    return hs
+
+
+def test_batch_status_isolates_a_failing_handle():
+    from paper_2510_20071_gb300 import binding, FIBAR_EORDER
+    params = dict(MODES["s2"], c_on=0.2, c_off=0.2)
+    streams = _streams(3, 0.004, seed=31)
+    a = _pushed_handles(streams, params)   # batched
+    b = _pushed_handles(streams, params)   # one at a time
+    try:
+        t1 = [1000, 1500, 2000]
+        outs = [torch.empty((s["H"], s["W"]), device="cuda") for s in streams]
+        binding.readout_batch(a, t1, outs)
+        ref = [f.readout(t) for f, t in zip(b, t1)]
+        torch.cuda.synchronize()
+        for o, r in zip(outs, ref):
+            assert torch.equal(o, r)
+        # handle 1 asks for a time before its previous read-out: only it fails
+        t2 = [3000, 1200, 4000]
+        status = (C.c_int * 3)()
+        outs2 = [torch.empty_like(o) for o in outs]
+        rc = binding.fibar_readout_batch([f.h.value for f in a], t2, [o.data_ptr() for o in outs2], None,
+                                         status, torch.cuda.current_stream().cuda_stream)
+        assert rc == FIBAR_EORDER and list(status) == [0, FIBAR_EORDER, 0]
+        assert "earlier" in binding.fibar_last_error(a[1].h)
+        ref2 = [b[0].readout(3000), None, b[2].readout(4000)]
+        torch.cuda.synchronize()
+        assert torch.equal(outs2[0], ref2[0]) and torch.equal(outs2[2], ref2[2])
+        for fa, fb in zip(a, b):
+            sa, sb = fa.state(), fb.state()
+            assert sa["k"] == sb["k"] and sa["h"] == sb["h"]
+            np.testing.assert_array_equal(sa["L"], sb["L"])
+    finally:
+        for f in a + b:
+            f.close()
+
+
+def test_batch_rejects_bad_arguments_before_any_work():
+    from paper_2510_20071_gb300 import binding, FIBAR_EINVAL
+    params = dict(MODES["s2"], c_on=0.2, c_off=0.2)
+    streams = _streams(2, 0.002, seed=41)
+    a = _pushed_handles(streams, params)
+    try:
+        outs = [torch.empty((s["H"], s["W"]), device="cuda") for s in streams]
+        s = torch.cuda.current_stream().cuda_stream
+        status = (C.c_int * 2)(7, 7)
+        dup = [a[0].h.value, a[0].h.value]
+        rc = binding.fibar_readout_batch(dup, [10, 20], [o.data_ptr() for o in outs], None, status, s)
+        assert rc == FIBAR_EINVAL and list(status) == [7, 7]
+        assert all(f.state()["k"] == 0 for f in a)
+        rc = binding.load_library().fibar_readout_batch(None, None, None, 2, None, None, s)
+        assert rc == FIBAR_EINVAL
+        assert binding.fibar_readout_batch([], [], [], None, None, s) == 0
+    finally:
+        for f in a:
+            f.close()
+
+
+def test_memory_bytes_matches_the_allocation():
+    from paper_2510_20071_gb300 import Fibar, memory_bytes
+    for W, H, p in [(1280, 720, dict(blur_mode=1)), (346, 260, dict(blur_mode=0, max_pending=1 << 20))]:
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        f = Fibar(W, H, **p)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        try:
+            mb = f.memory_bytes()
+            assert mb == memory_bytes(W, H, **p)
+            delta = free0 - free1
+            assert 0.9 * mb <= delta <= mb + (160 << 20), (W, H, mb, delta)
+        finally:
+            f.close()
+
+
+def test_server_admits_by_memory():
+    from paper_2510_20071_gb300.serving import Server, HANDLE_SLACK_BYTES
+    from paper_2510_20071_gb300 import memory_bytes
+    need = memory_bytes(64, 48, max_pending=1 << 16) + HANDLE_SLACK_BYTES
+    srv = Server(budget=2 * need + need // 2)
+    try:
+        ids = [srv.admit(64, 48, max_pending=1 << 16) for _ in range(3)]
+        assert ids[:2] == [0, 1] and ids[2] is None
+        assert srv.stats()["refused"] == 1
+        srv.release(ids[0])
+        assert srv.admit(64, 48, max_pending=1 << 16) is not None
+    finally:
+        srv.close()
