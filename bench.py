@@ -444,7 +444,8 @@ def main():
         "gpu_launches": int(launches),
         "detector": {k: st[k] - det0[k] for k in ["detector_fixups", "detector_unmerged",
                                                    "detector_pass2_steps", "detector_fix_steps", "s1_blurs",
-                                                   "detector_big_pops", "detector_ring_misses"]},
+                                                   "detector_big_pops", "detector_ring_misses",
+                                                   "detector_recenters"]},
     }
 
     if not args.no_e2e:

@@ -41,7 +41,7 @@ constexpr uint32_t CHUNK = 64;                 // minimum detector chunk length 
 constexpr unsigned DET_G = 1023;               // reach of the guessed windows, in chunks
 constexpr unsigned DET_WARM = 32;              // steps a chunk runs from its guess before its own steps
 constexpr unsigned DET_MAX_CHUNKS = 32768;     // chunks per batch at most (S grows beyond)
-constexpr unsigned DET_SAMPLE = 32;            // chunks between sampled regulator windows
+constexpr unsigned DET_SAMPLE = 64;            // chunks between sampled regulator windows
 constexpr int LB_WIN = 8;                      // look-back window (predecessor tiles per load round)
 constexpr int LB_GROUP = 32;                   // sort tiles per published group total
 constexpr unsigned SPIN_LIMIT = 1u << 20;      // bounded device waits (~1 s)

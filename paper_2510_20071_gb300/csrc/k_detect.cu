@@ -32,8 +32,8 @@ namespace fibar {
 // The window table holds, per target chunk c, a band of DET_BAND distances
 // [g_lo(c), g_lo(c) + DET_BAND) centred on the chunk's expected window; distances below
 // g_lo(c) enter only through their sum N(c, g_lo(c) - 1).  First build: the expected
-// queue length starts at the batch's q and drifts at the rate the queue grew (or shrank)
-// over the previous batch.  The same pass stores the whole column of distances 1..639 of
+// queue length starts at the batch's q and, if the queue grew (or shrank) by more than an
+// eighth over the previous batch, drifts at that rate.  The same pass stores the whole column of distances 1..639 of
 // every DET_SAMPLE-th chunk, from which k_det_center finds the regulator's window there;
 // if a sampled window falls outside its band (a queue that fills after a stream starts,
 // or jumps with the scene), the table is built a second time with bands centred on the
@@ -89,9 +89,12 @@ __device__ __forceinline__ Geo geometry(const KParams &kp, const Ctrl *ctrl)
     g.base = ctrl->base;
     g.m = ctrl->m;
     const unsigned long long qprev = g.base - (unsigned long long)ctrl->det.h;
-    // growth per event over the previous batch, within [-1, 1] (16.16)
+    // growth per event over the previous batch, within [-1, 1] (16.16), when the queue
+    // changed by more than an eighth over it (a stream filling up); a queue that only
+    // wanders keeps a flat band, and the sampled windows catch the rest
     long long slope = 0;
-    if (ctrl->grow_den >= GROW_MIN_EVENTS) {
+    const long long dq = ctrl->grow_num < 0 ? -ctrl->grow_num : ctrl->grow_num;
+    if (ctrl->grow_den >= GROW_MIN_EVENTS && dq * 8 > (long long)qprev) {
         slope = ctrl->grow_num * 65536 / (long long)ctrl->grow_den;
         slope = max(-65536ll, min(65536ll, slope));
     }
@@ -265,18 +268,17 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
         }
         if (kBuild == 0 && ns > 0) {
             // columns of the sampled targets DET_SAMPLE * s within reach of the sources:
-            // prof[t][s][d] = M(DET_SAMPLE * s, d), d in 1..639
-            const long long t_lo = c_lo + 1, t_hi = c_lo + HB_CHUNKS - 1 + (HB_BINS - 1);
-            const long long s_lo = max(1ll, (t_lo + DET_SAMPLE - 1 + (long long)DET_SAMPLE * 64) / DET_SAMPLE - 64);
-            const long long s_hi = min((long long)ns, t_hi >= 0 ? t_hi / DET_SAMPLE : -1ll);
-            const long long nsamp = s_hi - s_lo + 1;
+            // prof[t][s][d] = M(DET_SAMPLE * s, d), d in 1..639 (16 threads write the 16
+            // consecutive distances one sample takes from the block's sources)
+            const int t_lo = (int)c_lo + 1, t_hi = (int)c_lo + HB_CHUNKS - 1 + (HB_BINS - 1);
+            const int s_lo = t_lo <= (int)DET_SAMPLE ? 1 : (t_lo + (int)DET_SAMPLE - 1) / (int)DET_SAMPLE;
+            const int s_hi = min((int)ns, t_hi / (int)DET_SAMPLE);
             unsigned short *pt = prof + (size_t)t * n_samples * HB_BINS;
-            for (long long i = tid; i < nsamp * HB_CHUNKS; i += 256) {
-                const long long sidx = s_lo + i / HB_CHUNKS;
-                const int cc = (int)(i % HB_CHUNKS);
-                const long long d = sidx * DET_SAMPLE - (c_lo + cc);
+            for (int i = (int)tid; i < (s_hi - s_lo + 1) * HB_CHUNKS; i += 256) {
+                const int sidx = s_lo + i / HB_CHUNKS, cc = i % HB_CHUNKS;
+                const int d = sidx * (int)DET_SAMPLE - ((int)c_lo + cc);
                 if (d >= 1 && d <= HB_BINS - 1)
-                    pt[(size_t)sidx * HB_BINS + d] = (unsigned short)H.h[cc][hb_slot((int)d)];
+                    pt[(size_t)sidx * HB_BINS + d] = (unsigned short)H.h[cc][hb_slot(d)];
             }
         }
         __syncthreads();
@@ -387,21 +389,24 @@ __device__ __forceinline__ unsigned pick8(const unsigned (&a)[8], unsigned u)
     return r;
 }
 
-__global__ void __launch_bounds__(256)
-k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short *Mt, size_t mt_rows,
-           unsigned *base_cnt, const unsigned short *ctr, DetState *E0, unsigned *qout)
+// kMode: the table build in use (0: bands from (mid0, slope); 1: from the sampled
+// windows, below-band counts in the second set).  One copy of the body per build keeps
+// the loads at the top of each chunk independent of the mode.
+template <int kMode>
+__device__ __forceinline__ void init_chunks(const KParams &kp, const Ctrl *ctrl, const uint4 *ring,
+                                            const unsigned short *Mt, size_t mt_rows, unsigned *base_cnt,
+                                            const unsigned short *ctr, DetState *E0, unsigned *qout)
 {
-    PDL_ENTRY();
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long base = ctrl->base;
     const unsigned S = ctrl->S, nch = ctrl->nchunks, Gold = ctrl->Gold;
     const unsigned mid0 = ctrl->band_mid0;
     const int slope = ctrl->band_slope;
-    const unsigned mode = ctrl->band_mode, ns = n_samples_of(nch);
-    unsigned *bc = base_cnt + (size_t)mode * 2 * mt_rows;
+    const unsigned ns = n_samples_of(nch);
+    unsigned *bc = base_cnt + (size_t)kMode * 2 * mt_rows;
     const unsigned warps_total = gridDim.x * (blockDim.x >> 5);
     for (unsigned c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) + 1; c < nch; c += warps_total) {
-        const unsigned g_lo = mode ? band_lo_tab(ctr, ns, c) : band_lo_lin(mid0, slope, c);
+        const unsigned g_lo = kMode ? band_lo_tab(ctr, ns, c) : band_lo_lin(mid0, slope, c);
         const unsigned g_hi = g_lo + DET_BAND - 1;
         const unsigned short *rp = Mt + (size_t)c * MT_PITCH;
         const unsigned short *rt = Mt + (mt_rows + c) * MT_PITCH;
@@ -416,7 +421,7 @@ k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short
         if (lane == 0) {
             bc[c] = 0;
             bc[mt_rows + c] = 0;
-            if (mode) {  // the first build's counters too
+            if (kMode) {  // the first build's counters too
                 base_cnt[c] = 0;
                 base_cnt[mt_rows + c] = 0;
             }
@@ -542,6 +547,17 @@ k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short
             qout[k0] = (unsigned)qn;
         }
     }
+}
+
+__global__ void __launch_bounds__(256)
+k_det_init(KParams kp, const Ctrl *ctrl, const uint4 *ring, const unsigned short *Mt, size_t mt_rows,
+           unsigned *base_cnt, const unsigned short *ctr, DetState *E0, unsigned *qout)
+{
+    PDL_ENTRY();
+    if (ctrl->band_mode)
+        init_chunks<1>(kp, ctrl, ring, Mt, mt_rows, base_cnt, ctr, E0, qout);
+    else
+        init_chunks<0>(kp, ctrl, ring, Mt, mt_rows, base_cnt, ctr, E0, qout);
 }
 
 // Run the detector over chunks with groups of GW lanes, 32/GW chunks per warp.  All lanes
