@@ -435,3 +435,58 @@ def serving_schedule(streams: list[dict], requests: list[list[int]], tick_us: in
             reads.extend((i, int(x)) for x in r[a:b])
         out.append((T, pushes, reads))
     return out
+
+
+# threshold calibration recordings ---------------------------------------------------
+
+def threshold_recording(W: int, H: int, *, periods: int = 20, amplitude: float = 1.0,
+                        period_s: float = 1.0, c_mean: float = 0.2, spread: float = 0.15,
+                        imbalance: float = 0.25, steps_per_half: int = 64, seed: int = 5):
+    """A sensor with per-pixel ON / OFF thresholds watching a spatially uniform log
+    brightness that follows a triangle wave (the setup of the paper's appendix on
+    relative thresholds: an exponentially ramped illumination gives a linear triangle
+    in log brightness).  Thresholds: c_mean * exp(N(0, spread) +- N(0, imbalance) / 2)
+    for ON / OFF.  Each pixel starts at a random level within its thresholds; an event
+    fires whenever the brightness moves a threshold away from the pixel's reference,
+    stamped at the linear crossing time.  Returns dict(events, c_on, c_off) with (H, W)
+    float64 threshold arrays."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    n = W * H
+    base = rng.normal(0.0, spread, n)
+    imb = rng.normal(0.0, imbalance, n)
+    c_on = c_mean * np.exp(base + imb / 2)
+    c_off = c_mean * np.exp(base - imb / 2)
+    # step must move the brightness less than any threshold: at most one event per step
+    dl = amplitude / steps_per_half
+    if dl >= min(c_on.min(), c_off.min()):
+        raise ValueError("steps_per_half too small for the thresholds")
+    ref = rng.uniform(-c_off, c_on)  # level of the last event relative to the start
+    dt_us = period_s / 2 / steps_per_half * 1e6
+    level = 0.0
+    ts, pix, pol = [], [], []
+    idx = np.arange(n)
+    nsteps = 2 * steps_per_half * periods
+    for st in range(nsteps):
+        up = (st // steps_per_half) % 2 == 0
+        new = level + (dl if up else -dl)
+        if up:
+            hit = new - ref >= c_on
+            cross = ref + c_on
+        else:
+            hit = ref - new >= c_off
+            cross = ref - c_off
+        k = idx[hit]
+        if k.size:
+            frac = (cross[k] - level) / (new - level)
+            ts.append(np.floor((st + frac) * dt_us).astype(np.int64))
+            pix.append(k)
+            pol.append(np.full(k.size, 1 if up else -1, dtype=np.int64))
+            ref[k] = cross[k]
+        level = new
+    t = np.concatenate(ts) if ts else np.zeros(0, np.int64)
+    p_ = np.concatenate(pix) if pix else np.zeros(0, np.int64)
+    s_ = np.concatenate(pol) if pol else np.zeros(0, np.int64)
+    order = np.lexsort((p_, t))
+    t, p_, s_ = t[order], p_[order], s_[order]
+    ev = pack_events(torch.from_numpy(p_ % W), torch.from_numpy(p_ // W), torch.from_numpy(s_), torch.from_numpy(t))
+    return dict(events=ev, c_on=c_on.reshape(H, W), c_off=c_off.reshape(H, W))

@@ -5,5 +5,5 @@ Plain CPU restatement of the paper's per-event procedure (C source in
 benchmark's CPU-baseline leg may import this package; the CUDA library never does.
 """
 from .oracle import (  # noqa: F401
-    Oracle, build, coefficients, blur_image, default_params, lib_path,
+    Oracle, build, coefficients, blur_image, default_params, lib_path, relative_thresholds,
 )

@@ -22,6 +22,15 @@
  *   Sec. 4.2, Eq. 19 : r_k = N_ap / (N_at * A), 2x2 tiles, A = 4
  *   Sec. 4.2, Eq. 20 : q_targ_{k+1} = floor(q_k * r_fill / r_k), in integers from
  *                      N_ap and N_at, bounded below.
+ *   Sec. 5.2         : inter-pixel threshold correction - the right-hand side of Eq. 6
+ *                      multiplied by the pixel's relative threshold C'_i (an optional
+ *                      per-pixel gain, 1 when unset).
+ *   Appendix (relative contrast thresholds): from a recording of a stationary signal,
+ *                      N_on,i C_on,i = N_off,i C_off,i = |dL|; C_i is the harmonic mean
+ *                      of C_on,i and C_off,i and C the harmonic mean of the C_i, so with
+ *                      Nbar the mean of N_on,i + N_off,i over all pixels
+ *                      C'_on,i = Nbar / (2 N_on,i), C'_off,i = Nbar / (2 N_off,i),
+ *                      C'_i = Nbar / (N_on,i + N_off,i).
  *
  * Readings of points the paper leaves open (each one is a parameter or a fixed rule):
  *   - the queue is FIFO (push back, pop front), although the text once calls it LIFO;
@@ -42,6 +51,8 @@
  *     (1, 1 = the paper's units);
  *   - read-out at time t applies the longest prefix of pushed events whose time
  *     stamps are all <= t; read-out times must not decrease;
+ *   - a relative threshold whose count is zero (no ON, no OFF or no events at the
+ *     pixel) is undefined and returned as NaN;
  *   - blur_mode 0 ("S1") blurs in place when the pixel goes stale (the paper);
  *     blur_mode 1 ("S2") never changes L and instead replaces, in the read-out image
  *     only, every pixel that has had an event and has no event in the queue by the
@@ -97,6 +108,7 @@ typedef struct {
     uint64_t fill_num, fill_den, q_min, q_max, q_init;
     /* per-pixel state */
     double *pbar, *L;
+    double *gain;          /* Sec. 5.2 per-pixel factor on Eq. 6, NULL = 1 */
     uint32_t *cnt;
     uint8_t *ever;
     uint64_t *last;        /* global index of the pixel's last event, UINT64_MAX if none */
@@ -190,7 +202,50 @@ void fibar_ref_destroy(ref_t *o)
 {
     if (!o) return;
     free(o->pbar); free(o->L); free(o->cnt); free(o->ever); free(o->last);
-    free(o->tcnt); free(o->queue); free(o->pend); free(o);
+    free(o->tcnt); free(o->queue); free(o->pend); free(o->gain); free(o);
+}
+
+/* Sec. 5.2: multiply the right-hand side of Eq. 6 of pixel i by gain[i] for every later
+ * event (gain NULL: back to 1). */
+int fibar_ref_set_gain(ref_t *o, const double *gain)
+{
+    if (!gain) {
+        free(o->gain);
+        o->gain = NULL;
+        return REF_OK;
+    }
+    if (!o->gain) o->gain = (double *)malloc(o->npix * sizeof(double));
+    if (!o->gain) return REF_NOMEM;
+    memcpy(o->gain, gain, o->npix * sizeof(double));
+    return REF_OK;
+}
+
+/* Appendix (relative contrast thresholds): per-pixel ON / OFF counts of a recording and
+ * the relative thresholds they give.  Records outside the sensor are skipped. */
+int fibar_ref_relative_thresholds(uint32_t W, uint32_t H, const ref_event_t *ev, uint64_t n,
+                                  double *c_on, double *c_off, double *c)
+{
+    uint64_t npix = (uint64_t)W * H;
+    if (W == 0 || H == 0) return REF_INVAL;
+    uint64_t *n_on = (uint64_t *)calloc(npix, sizeof(uint64_t));
+    uint64_t *n_off = (uint64_t *)calloc(npix, sizeof(uint64_t));
+    if (!n_on || !n_off) { free(n_on); free(n_off); return REF_NOMEM; }
+    uint64_t total = 0;
+    for (uint64_t k = 0; k < n; k++) {
+        if (ev[k].x >= W || ev[k].y >= H) continue;
+        uint64_t i = (uint64_t)ev[k].y * W + ev[k].x;
+        if (ev[k].p > 0) n_on[i]++; else n_off[i]++;
+        total++;
+    }
+    /* Nbar: the mean number of events per pixel, over all W*H pixels */
+    double nbar = (double)total / (double)npix;
+    for (uint64_t i = 0; i < npix; i++) {
+        c_on[i] = n_on[i] ? nbar / (2.0 * (double)n_on[i]) : NAN;
+        c_off[i] = n_off[i] ? nbar / (2.0 * (double)n_off[i]) : NAN;
+        c[i] = n_on[i] + n_off[i] ? nbar / (double)(n_on[i] + n_off[i]) : NAN;
+    }
+    free(n_on); free(n_off);
+    return REF_OK;
 }
 
 void fibar_ref_set_trace(ref_t *o, ref_trace_t *tr)
@@ -236,6 +291,7 @@ static void apply_event(ref_t *o, uint64_t i, int p)
      * updated average, then Eq. 10. */
     o->pbar[i] = o->alpha * o->pbar[i] + (1.0 - o->alpha) * s;
     double dl_det = s - o->pbar[i];
+    if (o->gain) dl_det *= o->gain[i];  /* Sec. 5.2 */
     o->L[i] = o->beta * o->L[i] + 0.5 * (1.0 + o->beta) * dl_det;
     o->ever[i] = 1;
 

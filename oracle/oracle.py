@@ -81,6 +81,10 @@ def _load():
             lib.fibar_ref_info.restype = None
             lib.fibar_ref_blur_image.argtypes = [C.c_uint32, C.c_uint32, vp, vp]
             lib.fibar_ref_blur_image.restype = None
+            lib.fibar_ref_set_gain.argtypes = [vp, vp]
+            lib.fibar_ref_set_gain.restype = C.c_int
+            lib.fibar_ref_relative_thresholds.argtypes = [C.c_uint32, C.c_uint32, vp, C.c_uint64, vp, vp, vp]
+            lib.fibar_ref_relative_thresholds.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -101,6 +105,20 @@ def blur_image(img: np.ndarray) -> np.ndarray:
     out = np.empty_like(img)
     lib.fibar_ref_blur_image(W, H, img.ctypes.data, out.ctypes.data)
     return out
+
+
+def relative_thresholds(W: int, H: int, ev):
+    """Relative contrast thresholds (C'_on, C'_off, C') of every pixel from a calibration
+    recording, as (H, W) float64 arrays (NaN where undefined)."""
+    lib = _load()
+    rec = _as_records(ev)
+    n = W * H
+    out = [np.empty(n, np.float64) for _ in range(3)]
+    rc = lib.fibar_ref_relative_thresholds(W, H, rec.ctypes.data, rec.shape[0],
+                                           *[o.ctypes.data for o in out])
+    if rc != 0:
+        raise ValueError(f"fibar_ref_relative_thresholds failed: {rc}")
+    return tuple(o.reshape(H, W) for o in out)
 
 
 def default_params(**over) -> dict:
@@ -156,6 +174,17 @@ class Oracle:
             self.close()
         except Exception:
             pass
+
+    def set_gain(self, gain) -> None:
+        """Sec. 5.2 correction: per-pixel factor on Eq. 6 (None removes it)."""
+        if gain is None:
+            self.lib.fibar_ref_set_gain(self.h, None)
+            return
+        g = np.ascontiguousarray(np.asarray(gain, dtype=np.float64).reshape(-1))
+        if g.size != self.W * self.H:
+            raise ValueError("one gain per pixel")
+        if self.lib.fibar_ref_set_gain(self.h, g.ctypes.data) != 0:
+            raise MemoryError("fibar_ref_set_gain")
 
     def push(self, ev) -> None:
         rec = _as_records(ev)
