@@ -269,6 +269,78 @@ def run_batch(args, rank, world, local):
         print(json.dumps(result), flush=True)
 
 
+CALIB_EVENTS = 100_000_000
+
+
+def run_calib(args, rank, world, local):
+    """Relative contrast thresholds (fibar_relative_thresholds) of a 640x480 recording of
+    100 M events (uniform random pixels and polarities, seeded): a step is one call over
+    the whole recording, events resident on the device (16 B read per event; inputs far
+    larger than L2).  e2e: the same call from pinned host memory (copies inside)."""
+    import torch
+    import torch.distributed as dist
+    import eventsim
+    from paper_2510_20071_gb300 import relative_thresholds
+
+    W, H = 640, 480
+    ev = eventsim.random_events(W, H, CALIB_EVENTS, seed=21 + rank, p_on=0.52)
+    dev = ev.to(f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        relative_thresholds(dev, W, H)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.4)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        relative_thresholds(dev, W, H)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    time.sleep(0.3)
+    clocks = sampler.stop()
+    ms_all = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_all, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_all.item())
+    per = ms_max / args.steps
+    value = world * CALIB_EVENTS / (per / 1e3) / 1e6
+    # e2e: pinned host events through the host path of the same call
+    pinned = ev.pin_memory()
+    n_e2e = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        relative_thresholds(pinned, W, H)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
+    peak, peak_kind = load_peaks()
+    alg = 16.0 * CALIB_EVENTS + 12.0 * W * H + 8.0 * W * H
+    gbs = alg / (per / 1e3) / 1e9
+    result = {
+        "metric": "calibration events/s (M/s) on 1 GB300, % of HBM roofline", "value": round(value, 3),
+        "unit": "Mevents/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(per, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 counts, f32 thresholds", "data": "synthetic (uniform random 640x480 events, seeded)",
+        "config": {"workload": "relative contrast thresholds of a 640x480 recording, 100 M events",
+                   "l2": "inputs larger than L2: 1.6 GB of records per step"},
+        "roofline": {"bound": "hbm", "kernel": "k_calib_count + k_calib_finish", "achieved": round(gbs, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4), "traffic": None,
+                     "peak_kind": peak_kind,
+                     "alg_bytes": "16 B per record read, 8 B per pixel of counts, 12 B per pixel written"},
+        "e2e": {"value": round(CALIB_EVENTS / (e2e_ms / 1e3) / 1e6, 3), "unit": "Mevents/s",
+                "h2d_bytes_per_step": 16 * CALIB_EVENTS, "d2h_bytes_per_step": 12 * W * H},
+        "clocks": clocks,
+        "gpu_launches": 2 * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -280,9 +352,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stream-events", type=int, default=None,
                     help="simulate a shorter stream (profiling runs); default: the 200 M workload")
-    ap.add_argument("--workload", default="stream", choices=["stream", "batch32"],
+    ap.add_argument("--workload", default="stream", choices=["stream", "batch32", "calib"],
                     help="stream: one 1280x720 stream (the headline); batch32: 32 mixed streams served "
-                         "in concurrent batches")
+                         "in concurrent batches; calib: relative thresholds of a 640x480 recording")
     ap.add_argument("--batch-seconds", type=float, default=0.2,
                     help="batch32: stream time simulated per stream")
     args = ap.parse_args()
@@ -303,6 +375,8 @@ def main():
         dist.init_process_group("nccl")
     if args.workload == "batch32":
         return run_batch(args, rank, world, local)
+    if args.workload == "calib":
+        return run_calib(args, rank, world, local)
     from paper_2510_20071_gb300 import Fibar
 
     n_lat = min(args.steps, 50)     # read-out latency pass

@@ -193,6 +193,34 @@ int fibar_readout_batch(fibar_t *const *hs, const uint64_t *t_us, float *const *
  * that fibar_create rejects as EINVAL). */
 int fibar_memory_bytes(uint32_t W, uint32_t H, const fibar_params_t *p, uint64_t *bytes);
 
+/* Relative contrast thresholds of every pixel from a calibration recording (the paper's
+ * appendix on relative contrast thresholds): with N_on,i and N_off,i the pixel's ON and
+ * OFF event counts and Nbar the mean of N_on,i + N_off,i over all W*H pixels,
+ *   c_on[i] = Nbar / (2 N_on,i),  c_off[i] = Nbar / (2 N_off,i),  c[i] = Nbar / (N_on,i + N_off,i)
+ * (row-major W*H floats each; NaN where the count in the denominator is 0).  These are
+ * C_on,i / C, C_off,i / C and C_i / C, C_i being the harmonic mean of a pixel's two
+ * thresholds and C the harmonic mean of the C_i, when the recording is of a spatially
+ * uniform, stationary signal.  Records outside the sensor are skipped.
+ *   on_device = 1: ev and the outputs are device memory (ev 16-byte aligned); the call
+ *                  returns without waiting.
+ *   on_device = 0: host memory; events are copied in chunks of 4 Mi records; the call
+ *                  returns after the results are in place.
+ * Workspace (8 bytes per pixel, plus staging for host data) is allocated and released on
+ * `cuda_stream` (stream-ordered allocation).  Needs no handle.  The paper has no code
+ * for this; it derives the formulas.  Errors: EINVAL (W or H = 0, W*H > 2^24, a NULL
+ * pointer, misaligned device events), ENOMEM, ECUDA. */
+int fibar_relative_thresholds(const fibar_event_t *ev, size_t n, uint32_t W, uint32_t H, int on_device,
+                              float *c_on, float *c_off, float *c, void *cuda_stream);
+
+/* Sec. 5.2 threshold correction: from the next read-out on, the right-hand side of
+ * Eq. 6 (the detrended increment p_k - pbar_k) of pixel i is multiplied by gain[i]
+ * (Sec. 5.2 uses the relative threshold c[i] of fibar_relative_thresholds).  gain: W*H
+ * floats, row-major, copied into the handle (the first call allocates W*H*4 bytes);
+ * NULL removes the correction.  on_device = 0: host memory, every value must be finite
+ * and > 0 (else EINVAL, nothing changes); on_device = 1: device memory, copied on
+ * `cuda_stream` without checking.  Errors: EINVAL, ENOMEM, ECUDA. */
+int fibar_set_pixel_gain(fibar_t *h, const float *gain, int on_device, void *cuda_stream);
+
 /* Apply every pending event (as a read-out at t = +inf without output; does not
  * change the read-out time order). */
 int fibar_flush(fibar_t *h, void *cuda_stream);

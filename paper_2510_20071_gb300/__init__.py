@@ -11,5 +11,6 @@ from .binding import (  # noqa: F401
     fibar_default_params, fibar_create, fibar_push_events, fibar_readout, fibar_flush,
     fibar_debug_state, fibar_stats, fibar_set_timing, fibar_stage_times, fibar_last_error,
     fibar_destroy, fibar_queue_counts_noalloc, fibar_readout_batch, fibar_memory_bytes,
-    memory_bytes, readout_batch, EXPORTED, STAGES, FibarStageTimes,
+    memory_bytes, readout_batch, relative_thresholds, fibar_relative_thresholds, fibar_set_pixel_gain,
+    EXPORTED, STAGES, FibarStageTimes,
 )

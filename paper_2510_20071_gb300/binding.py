@@ -24,7 +24,8 @@ FIBAR_ETIMEOUT = -5
 EXPORTED = ["fibar_default_params", "fibar_create", "fibar_push_events", "fibar_readout",
             "fibar_flush", "fibar_debug_state", "fibar_stats", "fibar_set_timing",
             "fibar_stage_times", "fibar_last_error", "fibar_destroy", "fibar_queue_counts_noalloc",
-            "fibar_readout_batch", "fibar_memory_bytes"]
+            "fibar_readout_batch", "fibar_memory_bytes", "fibar_relative_thresholds",
+            "fibar_set_pixel_gain"]
 
 STAGES = ["decode", "sort", "walk", "det_counts", "det_pass1", "det_pass2", "det_fix", "s1_blur",
           "readout", "commit"]
@@ -110,6 +111,10 @@ def load_library(build_if_missing: bool = True):
             lib.fibar_readout_batch.restype = C.c_int
             lib.fibar_memory_bytes.argtypes = [C.c_uint32, C.c_uint32, C.POINTER(FibarParams), C.POINTER(C.c_uint64)]
             lib.fibar_memory_bytes.restype = C.c_int
+            lib.fibar_relative_thresholds.argtypes = [vp, C.c_size_t, C.c_uint32, C.c_uint32, C.c_int, vp, vp, vp, vp]
+            lib.fibar_relative_thresholds.restype = C.c_int
+            lib.fibar_set_pixel_gain.argtypes = [vp, vp, C.c_int, vp]
+            lib.fibar_set_pixel_gain.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -183,6 +188,15 @@ def fibar_memory_bytes(W: int, H: int, params: FibarParams | None):
     b = C.c_uint64()
     rc = load_library().fibar_memory_bytes(W, H, C.byref(params) if params is not None else None, C.byref(b))
     return rc, int(b.value)
+
+
+def fibar_relative_thresholds(ev_ptr: int, n: int, W: int, H: int, on_device: int, c_on_ptr: int,
+                              c_off_ptr: int, c_ptr: int, stream: int) -> int:
+    return load_library().fibar_relative_thresholds(ev_ptr, n, W, H, on_device, c_on_ptr, c_off_ptr, c_ptr, stream)
+
+
+def fibar_set_pixel_gain(h, gain_ptr, on_device: int, stream: int) -> int:
+    return load_library().fibar_set_pixel_gain(h, gain_ptr, on_device, stream)
 
 
 # --- convenience wrapper ---------------------------------------------------------------
@@ -290,6 +304,19 @@ class Fibar:
         self._check(fibar_queue_counts_noalloc(self.h, out.data_ptr(), 1 if out.is_cuda else 0, self._s))
         return out
 
+    def set_pixel_gain(self, gain) -> None:
+        """Sec. 5.2 correction: multiply Eq. 6's right-hand side of every pixel by its gain
+        (a W*H float32 tensor, CUDA or CPU); None removes it."""
+        t = self.torch
+        if gain is None:
+            self._check(fibar_set_pixel_gain(self.h, None, 0, self._s))
+            return
+        if gain.dtype != t.float32 or gain.numel() != self.W * self.H or not gain.is_contiguous():
+            raise TypeError("gain must be a contiguous float32 tensor with W*H elements")
+        self._check(fibar_set_pixel_gain(self.h, gain.data_ptr(), 1 if gain.is_cuda else 0, self._s))
+        if gain.is_cuda:
+            self._keep.append(gain)
+
     def memory_bytes(self) -> int:
         """Device bytes this handle allocated (fibar_memory_bytes of its parameters)."""
         rc, b = fibar_memory_bytes(self.W, self.H, self.params)
@@ -363,3 +390,20 @@ def readout_batch(fibars, t_us, outs=None, done_events=None, stream=None):
                 raise FibarError(status[i], f"handle {i}: {fibar_last_error(f.h)}")
         raise FibarError(rc, "fibar_readout_batch rejected the arguments")
     return outs
+
+
+def relative_thresholds(ev, W: int, H: int, stream=None):
+    """(c_on, c_off, c) relative thresholds of a calibration recording, as (H, W) float32
+    tensors on the events' device (``fibar_relative_thresholds``)."""
+    import torch
+    if ev.dtype != torch.int64 or ev.dim() != 2 or ev.shape[1] != 2 or not ev.is_contiguous():
+        raise TypeError("events must be a contiguous (n, 2) int64 tensor")
+    outs = [torch.empty((H, W), dtype=torch.float32, device=ev.device) for _ in range(3)]
+    s = 0
+    if ev.is_cuda:
+        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+    rc = fibar_relative_thresholds(ev.data_ptr(), ev.shape[0], int(W), int(H), 1 if ev.is_cuda else 0,
+                                   *[o.data_ptr() for o in outs], s)
+    if rc != 0:
+        raise FibarError(rc, "fibar_relative_thresholds failed")
+    return tuple(outs)

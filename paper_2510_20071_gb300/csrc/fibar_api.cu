@@ -58,6 +58,8 @@ void free_all(fibar_t *h)
         if (p) cudaFree(p);
     if (h->snap_host) cudaFreeHost(h->snap_host);
     h->snap_host = nullptr;
+    if (h->gain_buf) cudaFree(h->gain_buf);
+    h->gain_buf = nullptr;
     memset(&h->b, 0, sizeof(h->b));
 }
 
@@ -342,6 +344,38 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     memset(h->stage_ms, 0, sizeof(h->stage_ms));
     h->stage_calls = 0;
     *out = h;
+    return FIBAR_OK;
+}
+
+extern "C" int fibar_set_pixel_gain(fibar_t *h, const float *gain, int on_device, void *cuda_stream)
+{
+    if (!h) return FIBAR_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!gain) {
+        h->b.gain = nullptr;
+        return FIBAR_OK;
+    }
+    const size_t npix = h->kp.npix;
+    if (!on_device) {
+        for (size_t i = 0; i < npix; ++i)
+            if (!(gain[i] > 0.f) || !isfinite(gain[i]))
+                return fail(h, FIBAR_EINVAL, "set_pixel_gain: every gain must be finite and > 0");
+    } else if (((uintptr_t)gain & 3) != 0) {
+        return fail(h, FIBAR_EINVAL, "set_pixel_gain: misaligned device array");
+    }
+    if (!h->gain_buf) {
+        cudaError_t e = cudaMalloc((void **)&h->gain_buf, npix * sizeof(float));
+        if (e != cudaSuccess) {
+            h->gain_buf = nullptr;
+            cudaGetLastError();
+            return fail(h, FIBAR_ENOMEM, "set_pixel_gain: device allocation failed");
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(h->gain_buf, gain, npix * sizeof(float),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_pixel_gain: copy");
+    h->b.gain = h->gain_buf;
     return FIBAR_OK;
 }
 

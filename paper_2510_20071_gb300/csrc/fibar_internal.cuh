@@ -153,6 +153,7 @@ struct Bufs {
     unsigned char *merged;
     unsigned *unm_bits;          // [chunks / 32] chunks that did not merge in pass 2
     float *out_staging;
+    float *gain;                 // [npix] factor on Eq. 6 per pixel (Sec. 5.2), nullptr = none
     unsigned int *dbg_cnt;
     // S1 (blur in place when a pixel goes stale)
     unsigned int *plist;         // [maxp] batch events grouped by pixel (tile-major), in order
@@ -189,6 +190,7 @@ struct fibar_s {
     unsigned long long staging_used;
     unsigned long long pending_upper;   // upper bound of records not yet applied
     unsigned int *snap_host;            // host view of Bufs::snap (written by k_commit)
+    float *gain_buf;                    // per-pixel gains, allocated by the first fibar_set_pixel_gain
     unsigned long long commits;         // read-outs and flushes launched
     unsigned long long pushed_since;    // records pushed since the last read-out or flush
     int carry_slot;

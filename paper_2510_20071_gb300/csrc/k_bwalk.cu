@@ -77,7 +77,7 @@ __device__ __forceinline__ unsigned bw_scan(unsigned v, unsigned *s_warp, unsign
     return r;
 }
 
-template <bool kLinks, bool kS1>
+template <bool kLinks, bool kS1, bool kGain>
 __global__ void __launch_bounds__(BW_THREADS, 2)
 k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
 {
@@ -114,6 +114,7 @@ k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
         unsigned pix[4];
         bool ok[4];
         float pb[4], lv[4], l0[4];
+        float gq[4];  // (1 + beta) / 2, times the pixel's gain on Eq. 6 (Sec. 5.2) if set
         unsigned long long lp0[4];
         unsigned ord[4], soff[4], seen = 0;  // seen: sub-pixels with an event in the bucket
 #pragma unroll
@@ -124,6 +125,7 @@ k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
             pb[s] = ok[s] ? b.pbar[pix[s]] : 0.f;
             lv[s] = ok[s] ? b.L[pix[s]] : 0.f;
             l0[s] = lv[s];
+            gq[s] = kGain ? (ok[s] ? kp.g * b.gain[pix[s]] : 0.f) : kp.g;
             lp0[s] = ok[s] ? b.last_pix[pix[s]] : NONE64;
             S.plast[4 * threadIdx.x + s] = lp0[s];
             ord[s] = 0;
@@ -241,14 +243,16 @@ k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
                 const unsigned k = (unsigned)(r >> 3) & 0x1FFFFFFFu;
                 const int s = (int)(r >> 1) & 3;
                 const bool off_ev = r & 1u;
-                float pbs = pb[0], lvs = lv[0];
+                float pbs = pb[0], lvs = lv[0], gs = gq[0];
 #pragma unroll
                 for (int qq = 1; qq < 4; ++qq)
-                    if (qq == s) { pbs = pb[qq]; lvs = lv[qq]; }
-                // Eqs. 2-3: increment C_p p; Eq. 7 then Eq. 6 (updated average) and Eq. 10
+                    if (qq == s) { pbs = pb[qq]; lvs = lv[qq]; gs = gq[qq]; }
+                if (!kGain) gs = kp.g;
+                // Eqs. 2-3: increment C_p p; Eq. 7 then Eq. 6 (updated average, times the
+                // pixel's gain when one is set) and Eq. 10
                 const float inc = off_ev ? -kp.c_off : kp.c_on;
                 pbs = kp.a * pbs + kp.oma * inc;
-                lvs = kp.b * lvs + kp.g * (inc - pbs);
+                lvs = kp.b * lvs + gs * (inc - pbs);
                 if (kS1) {
                     unsigned os = ord[0], ps0 = soff[0];
 #pragma unroll
@@ -300,28 +304,32 @@ k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
 
 size_t bwalk_smem() { return sizeof(BwSmem); }
 
+template <bool kLinks, bool kS1, bool kGain>
+static cudaError_t walk_variant(const KParams &kp, const Bufs &b, const unsigned long long *sorted, cudaStream_t s)
+{
+    static bool attr_set = false;
+    const size_t smem = sizeof(BwSmem);
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_bwalk<kLinks, kS1, kGain>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    return launch_pdl(k_bwalk<kLinks, kS1, kGain>, grid_for(2), BW_THREADS, smem, s, kp, b, sorted);
+}
+
 cudaError_t launch_walk(const KParams &kp, const Bufs &b, const unsigned long long *sorted,
                         cudaStream_t s, unsigned long long &nl)
 {
     nl += 1;
-    static bool attr_set = false;
-    const size_t smem = sizeof(BwSmem);
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_bwalk<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_bwalk<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_bwalk<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    const bool gain = b.gain != nullptr;
     cudaError_t e;
     if (kp.spatial && kp.blur_mode == 0)
-        e = launch_pdl(k_bwalk<true, true>, grid_for(2), BW_THREADS, smem, s, kp, b, sorted);
+        e = gain ? walk_variant<true, true, true>(kp, b, sorted, s) : walk_variant<true, true, false>(kp, b, sorted, s);
     else if (kp.spatial)
-        e = launch_pdl(k_bwalk<true, false>, grid_for(2), BW_THREADS, smem, s, kp, b, sorted);
+        e = gain ? walk_variant<true, false, true>(kp, b, sorted, s) : walk_variant<true, false, false>(kp, b, sorted, s);
     else
-        e = launch_pdl(k_bwalk<false, false>, grid_for(2), BW_THREADS, smem, s, kp, b, sorted);
+        e = gain ? walk_variant<false, false, true>(kp, b, sorted, s) : walk_variant<false, false, false>(kp, b, sorted, s);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
