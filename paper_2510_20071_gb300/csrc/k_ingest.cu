@@ -163,6 +163,11 @@ __device__ __forceinline__ int4 fetch_rec_from(const SegTable &T, const int4 *co
     return __ldg(s_ptr[sg] + (pos - s_start[sg]));
 }
 
+// Shared-memory index of tile position r: one word of padding per 16, so that a thread's
+// run of 16 consecutive positions (thread t at 16 t) and a warp's 32 consecutive
+// positions both fall in distinct banks.
+__device__ __forceinline__ unsigned dpad(unsigned r) { return r + (r >> 4); }
+
 __global__ void __launch_bounds__(DEC_THREADS)
 k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigned long long *rec_out,
          unsigned *ring_pix)
@@ -172,8 +177,8 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
     __shared__ __align__(8) unsigned long long s_bar;
     __shared__ unsigned s_start[MAXSEG + 1];
     __shared__ const int4 *s_ptr[MAXSEG];
-    __shared__ unsigned s_info[DEC_TILE];
-    __shared__ unsigned s_pix[DEC_TILE];
+    __shared__ unsigned s_info[DEC_TILE + DEC_TILE / 16];  // indexed by dpad()
+    __shared__ unsigned s_pix[DEC_TILE + DEC_TILE / 16];
     __shared__ unsigned s_warp[16];
     __shared__ unsigned s_tile, s_vmin, s_pre_s, s_pre_c, s_drop;
     __shared__ unsigned s_red_s[DEC_THREADS / 32], s_red_c[DEC_THREADS / 32];
@@ -246,9 +251,9 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
                 const unsigned tid_ = valid ? (y >> 1) * kp.tiles_w + (x >> 1) : 0u;
                 const unsigned sub = valid ? (((y & 1u) << 1) | (x & 1u)) : 0u;
                 info = (valid ? 0x80000000u : 0u) | (tid_ << 3) | (sub << 1) | (p > 0 ? 0u : 1u);
-                s_pix[r] = valid ? y * kp.W + x : 0u;
+                s_pix[dpad(r)] = valid ? y * kp.W + x : 0u;
             }
-            s_info[r] = info;
+            s_info[dpad(r)] = info;
         }
         if (vloc != S_NONE) atomicMin(&s_vmin, vloc);
         __syncthreads();
@@ -259,7 +264,7 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
 #pragma unroll
         for (int j = 0; j < DEC_PER_THREAD; ++j) {
             const unsigned r = threadIdx.x * DEC_PER_THREAD + j;
-            const unsigned info = s_info[r];
+            const unsigned info = s_info[dpad(r)];
             if (info != NOREC && r < vfirst) {
                 if (info >> 31) { ++cnt; keep |= 1u << j; }
                 else ++drop;
@@ -322,25 +327,25 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
             unsigned my_info[DEC_PER_THREAD], my_pix[DEC_PER_THREAD];
 #pragma unroll
             for (int j = 0; j < DEC_PER_THREAD; ++j) {
-                my_info[j] = s_info[threadIdx.x * DEC_PER_THREAD + j];
-                my_pix[j] = s_pix[threadIdx.x * DEC_PER_THREAD + j];
+                my_info[j] = s_info[dpad(threadIdx.x * DEC_PER_THREAD + j)];
+                my_pix[j] = s_pix[dpad(threadIdx.x * DEC_PER_THREAD + j)];
             }
             __syncthreads();
             unsigned li = excl;
 #pragma unroll
             for (int j = 0; j < DEC_PER_THREAD; ++j) {
                 if (keep >> j & 1u) {
-                    s_info[li] = my_info[j];
-                    s_pix[li] = my_pix[j];
+                    s_info[dpad(li)] = my_info[j];
+                    s_pix[dpad(li)] = my_pix[j];
                     ++li;
                 }
             }
             __syncthreads();
             for (unsigned i = threadIdx.x; i < tile_cnt; i += DEC_THREADS) {
-                const unsigned k = pre_c + i, info = s_info[i];
+                const unsigned k = pre_c + i, info = s_info[dpad(i)];
                 rec_out[k] = ((unsigned long long)((info >> 3) & 0x0FFFFFFFu) << 32) |
                              ((unsigned long long)k << 3) | (info & 7u);
-                if (ring_pix) ring_pix[(base + k) & kp.ring_mask] = s_pix[i];
+                if (ring_pix) ring_pix[(base + k) & kp.ring_mask] = s_pix[dpad(i)];
             }
             if (threadIdx.x == 0 && s_drop) atomicAdd(&ctrl->dropped, (unsigned long long)s_drop);
             if (vfirst != S_NONE) {
