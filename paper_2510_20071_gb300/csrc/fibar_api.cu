@@ -502,7 +502,7 @@ int process(fibar_t *h, unsigned long long t_read, float *out, cudaStream_t s)
     StageMarks mk(h, s);
 
     mk.mark(FIBAR_STAGE_DECODE);
-    cudaError_t e = launch_decode(kp, b, T, s, nl);
+    cudaError_t e = launch_decode(kp, b, T, h->sort_passes, s, nl);
     if (e != cudaSuccess) return cuda_fail(h, e, "decode");
     mk.mark(FIBAR_STAGE_SORT);
     e = launch_sort(kp, b, h->sort_passes, h->epoch, s, nl);

@@ -255,7 +255,7 @@ __device__ __forceinline__ unsigned warp_peers(unsigned v)
 
 // launchers (kernels live in their own translation units); `nl` counts kernel launches
 cudaError_t launch_init(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
-cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, cudaStream_t s,
+cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, unsigned sort_passes, cudaStream_t s,
                           unsigned long long &nl);
 cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsigned epoch,
                         cudaStream_t s, unsigned long long &nl);

@@ -168,9 +168,17 @@ __device__ __forceinline__ int4 fetch_rec_from(const SegTable &T, const int4 *co
 // positions both fall in distinct banks.
 __device__ __forceinline__ unsigned dpad(unsigned r) { return r + (r >> 4); }
 
+// With a one-pass sort the decode also counts the kept records per bucket (the sort's
+// only digit) and the block that completes the last tile turns the counts into the
+// sort's digit offsets and the walk's bucket starts (otherwise k_sort_hist does).
+struct DecHist {
+    unsigned *ghist, *gbase, *bucket_start;  // ghist == nullptr: off
+    unsigned nbuckets, lb;
+};
+
 __global__ void __launch_bounds__(DEC_THREADS)
 k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigned long long *rec_out,
-         unsigned *ring_pix)
+         unsigned *ring_pix, DecHist dh)
 {
     PDL_ENTRY();
     extern __shared__ __align__(128) int4 s_rec[];  // the tile's records (DEC_TILE)
@@ -182,6 +190,8 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
     __shared__ unsigned s_warp[16];
     __shared__ unsigned s_tile, s_vmin, s_pre_s, s_pre_c, s_drop;
     __shared__ unsigned s_red_s[DEC_THREADS / 32], s_red_c[DEC_THREADS / 32];
+    __shared__ unsigned s_hb[RADIX];  // kept records per bucket (this tile)
+    __shared__ bool s_hlast;
 
     const unsigned carry_n = ctrl->carry_n[T.carry_slot];
     if (threadIdx.x == 0) {
@@ -199,6 +209,22 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
     const unsigned total = s_start[T.nseg];
     const unsigned ntiles = (total + DEC_TILE - 1) / DEC_TILE;
     unsigned phase = 0;
+    const bool hist = dh.ghist != nullptr;
+    // digit offsets and bucket starts of the last tile's block (all zero without tiles)
+    auto hist_finish = [&]() {
+        const unsigned d0 = 2 * threadIdx.x;
+        const unsigned v0 = atomicExch(&dh.ghist[d0], 0u), v1 = atomicExch(&dh.ghist[d0 + 1], 0u);
+        unsigned tot;
+        const unsigned ex = block_excl_scan256(v0 + v1, s_warp, &tot);
+        dh.gbase[d0] = ex;
+        dh.gbase[d0 + 1] = ex + v0;
+        if (d0 < dh.nbuckets) dh.bucket_start[d0] = ex;
+        if (d0 + 1 < dh.nbuckets) dh.bucket_start[d0 + 1] = ex + v0;
+    };
+    if (hist && ntiles == 0) {
+        if (blockIdx.x == 0) hist_finish();
+        return;
+    }
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -206,6 +232,8 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
             s_vmin = S_NONE;
             s_drop = 0;
         }
+        if (hist)
+            for (unsigned i = threadIdx.x; i < RADIX; i += DEC_THREADS) s_hb[i] = 0u;
         __syncthreads();
         const unsigned tile = s_tile;
         if (tile >= ntiles) break;
@@ -345,6 +373,7 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
                 const unsigned k = pre_c + i, info = s_info[dpad(i)];
                 rec_out[k] = ((unsigned long long)((info >> 3) & 0x0FFFFFFFu) << 32) |
                              ((unsigned long long)k << 3) | (info & 7u);
+                if (hist) atomicAdd(&s_hb[((info >> 3) & 0x0FFFFFFFu) >> dh.lb], 1u);
                 if (ring_pix) ring_pix[(base + k) & kp.ring_mask] = s_pix[dpad(i)];
             }
             if (threadIdx.x == 0 && s_drop) atomicAdd(&ctrl->dropped, (unsigned long long)s_drop);
@@ -361,6 +390,20 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
                 const unsigned r = i * DEC_THREADS + threadIdx.x;
                 const unsigned pos = pos0 + r;
                 if (pos < total) T.carry_out[pos - pre_s] = s_rec[r];
+            }
+        }
+        if (hist) {
+            __syncthreads();
+            for (unsigned d = threadIdx.x; d < dh.nbuckets; d += DEC_THREADS)
+                if (s_hb[d]) atomicAdd(&dh.ghist[d], s_hb[d]);
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) s_hlast = atomicAdd(&ctrl->hist_done, 1u) == ntiles - 1;
+            __syncthreads();
+            if (s_hlast) {
+                __threadfence();
+                hist_finish();
+                if (threadIdx.x == 0) ctrl->hist_done = 0;
             }
         }
         __syncthreads();
@@ -645,8 +688,8 @@ int grid_for(int mult)
     return g_sms * mult;
 }
 
-cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, cudaStream_t s,
-                          unsigned long long &nl)
+cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, unsigned sort_passes,
+                          cudaStream_t s, unsigned long long &nl)
 {
     nl += 1;
     static bool attr_set = false;
@@ -655,15 +698,21 @@ cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, c
         if (cudaError_t e = cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) return e;
         attr_set = true;
     }
+    DecHist dh{nullptr, nullptr, nullptr, kp.nbuckets, kp.lb};
+    if (sort_passes == 1) {
+        dh.ghist = b.sort_hist;
+        dh.gbase = b.sort_base;
+        dh.bucket_start = b.bucket_start;
+    }
     if (cudaError_t e_ = launch_pdl(k_decode, grid_for(2), DEC_THREADS, smem, s, kp, t, b.ctrl, b.dec_status, b.rec[0],
-                                    kp.spatial ? b.ring_pix : nullptr)) return e_;
+                                    kp.spatial ? b.ring_pix : nullptr, dh)) return e_;
     return cudaGetLastError();
 }
 
 cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsigned epoch,
                         cudaStream_t s, unsigned long long &nl)
 {
-    nl += 1 + passes;  // the histogram kernel also produces the bucket starts
+    nl += (passes == 1 ? 0 : 1) + passes;  // one pass: the decode counted the digits
     static bool attr_set = false;
     const size_t smem = sizeof(SortSmem);
     if (!attr_set) {
@@ -674,9 +723,10 @@ cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsig
     }
     const unsigned bucket_bits = kp.key_bits - kp.lb;
     const unsigned dbits = passes ? (bucket_bits + passes - 1) / passes : 1u;
-    if (cudaError_t e_ = launch_pdl(k_sort_hist, grid_for(2), 256, 0, s, b.ctrl, b.rec[0], passes, dbits, kp.lb,
-                                    kp.nbuckets, b.sort_hist, b.sort_base, b.bucket_cnt, b.bucket_start))
-        return e_;
+    if (passes != 1)
+        if (cudaError_t e_ = launch_pdl(k_sort_hist, grid_for(2), 256, 0, s, b.ctrl, b.rec[0], passes, dbits, kp.lb,
+                                        kp.nbuckets, b.sort_hist, b.sort_base, b.bucket_cnt, b.bucket_start))
+            return e_;
     for (unsigned p = 0; p < passes; ++p) {
         if (cudaError_t e_ = launch_pdl(k_sort_pass, grid_for(2), SORT_THREADS, smem, s, b.ctrl, b.rec[p & 1],
                                         b.rec[(p + 1) & 1], p, dbits, kp.lb, epoch + p, b.sort_base, b.sort_rows,
