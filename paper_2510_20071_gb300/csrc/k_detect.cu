@@ -168,6 +168,23 @@ __device__ __forceinline__ int hb_slot(int d) { return d + (d >> 5); }
 
 struct HistSmem {
     unsigned h[HB_CHUNKS][HB_PITCH];
+    short gl[HB_CHUNKS + HB_BINS];  // first band distance of target c_lo + D (0: no target)
+};
+
+// floor(n / S) for the histogram's small quotients (n < 640 S): a single-precision
+// estimate from a reciprocal, then made exact with integer products (the estimate is
+// within one of the quotient since n / S < 2^10 and n is converted with 24 bits).
+struct ChunkDiv {
+    unsigned S;
+    float r;
+    __device__ explicit ChunkDiv(unsigned S_) : S(S_), r(1.0f / (float)S_) {}
+    __device__ __forceinline__ unsigned operator()(unsigned n) const
+    {
+        unsigned q = (unsigned)((float)n * r);
+        if (q * S > n) --q;
+        if ((q + 1) * S <= n) ++q;
+        return q;
+    }
 };
 
 // kBuild 0: first build, bands from (mid0, slope), plus the sampled columns.
@@ -195,11 +212,16 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
     auto band_of = [&](long long ct) -> int {
         return kBuild ? (int)band_lo_tab(ctr, ns, ct) : (int)band_lo_lin(g.mid0, g.slope, ct);
     };
+    const ChunkDiv div_S(g.S);
     for (unsigned unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
         const int t = unit & 1;
         const long long c_lo = (long long)((unit >> 1) * HB_CHUNKS) - (long long)g.Gold;  // first source chunk
         uint4 *hw = reinterpret_cast<uint4 *>(&H.h[0][0]);
         for (unsigned i = tid; i < HB_CHUNKS * HB_PITCH / 4; i += 256) hw[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (unsigned D = tid; D < HB_CHUNKS + HB_BINS; D += 256) {
+            const long long ct = c_lo + D;
+            H.gl[D] = (short)(ct >= 1 && ct < (long long)g.nchunks ? band_of(ct) : 0);
+        }
         __syncthreads();
         // histogram of the chunk distance to the next event of the same pixel / tile
         // (distances beyond the table counted at its last one)
@@ -211,10 +233,9 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
             const unsigned long long j = g.base + (unsigned long long)(j_lo + i);
             const uint2 n = nxt_of(ring, j & kp.ring_mask);
             const unsigned nv = t ? n.y : n.x;
-            const unsigned cc = i / g.S, r = i - cc * g.S;
+            const unsigned cc = div_S(i), r = i - cc * g.S;
             const unsigned long long rel = (unsigned long long)r + nv;  // from the start of chunk cc
-            const unsigned d = (nv == SAT || rel >= lim) ? (unsigned)(HB_BINS - 1)
-                             : (lim <= 0xFFFFFFFFull ? (unsigned)rel / g.S : (unsigned)(rel / g.S));
+            const unsigned d = (nv == SAT || rel >= lim) ? (unsigned)(HB_BINS - 1) : div_S((unsigned)rel);
             atomicAdd(&H.h[cc][hb_slot((int)d)], 1u);
         }
         __syncthreads();
@@ -243,8 +264,8 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
         // below the band: target c_lo + D gets sum_{cc} M at distance D - cc in [1, g_lo)
         for (int D = 1 + (int)tid; D < HB_CHUNKS + g_hi_all - (int)DET_BAND; D += 256) {
             const long long ct = c_lo + D;
-            if (ct < 1 || ct >= (long long)g.nchunks) continue;
-            const int gl = band_of(ct);
+            const int gl = H.gl[D];
+            if (gl == 0) continue;
             unsigned acc = 0;
 #pragma unroll
             for (int cc = 0; cc < HB_CHUNKS; ++cc) {
@@ -261,9 +282,8 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
             const int D = D0 + (int)(i / HB_CHUNKS), u = (int)(i % HB_CHUNKS);
             const int cc = HB_CHUNKS - 1 - u, d = D - cc;
             const long long ct = c_lo + D;  // target chunk
-            if (ct < 1 || ct >= (long long)g.nchunks) continue;
-            const int gl = band_of(ct);
-            if (d >= gl && d < gl + (int)DET_BAND)
+            const int gl = H.gl[D];
+            if (gl != 0 && d >= gl && d < gl + (int)DET_BAND)
                 base_t[(size_t)ct * MT_PITCH + (d - gl)] = (unsigned short)H.h[cc][hb_slot(d)];
         }
         if (kBuild == 0 && ns > 0) {
