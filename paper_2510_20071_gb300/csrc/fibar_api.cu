@@ -162,7 +162,7 @@ int derive_layout(uint32_t W, uint32_t H, const fibar_params_t *pp, Layout &lo)
     b.max_sort_tiles = (maxp + SORT_TILE - 1) / SORT_TILE + 1;
     b.max_chunks = std::min<unsigned long long>((maxp + CHUNK - 1) / CHUNK, DET_MAX_CHUNKS) + 1;
     b.mt_rows = b.max_chunks;
-    b.n_samples = b.max_chunks / DET_SAMPLE + 2;
+    b.n_samples = b.max_chunks / DET_SAMPLE + 18;  // short batches take up to 16 samples
     b.max_pops = maxp + npix + 8;
     b.max_sel_tiles = (b.max_pops + 4095) / 4096 + 1;
     return FIBAR_OK;

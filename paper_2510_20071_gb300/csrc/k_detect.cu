@@ -33,8 +33,9 @@ namespace fibar {
 // [g_lo(c), g_lo(c) + DET_BAND) centred on the chunk's expected window; distances below
 // g_lo(c) enter only through their sum N(c, g_lo(c) - 1).  First build: the expected
 // queue length starts at the batch's q and, if the queue grew (or shrank) by more than an
-// eighth over the previous batch, drifts at that rate.  The same pass stores the whole column of distances 1..639 of
-// every DET_SAMPLE-th chunk, from which k_det_center finds the regulator's window there;
+// eighth over the previous batch, drifts at that rate.  The same pass stores the whole
+// column of distances 1..639 of every DET_SAMPLE-th chunk (about 16 columns in a short
+// batch), from which k_det_center finds the regulator's window there;
 // if a sampled window falls outside its band (a queue that fills after a stream starts,
 // or jumps with the scene), the table is built a second time with bands centred on the
 // sampled windows, interpolated between samples.  A window that still leaves its band
@@ -65,20 +66,26 @@ __device__ __forceinline__ unsigned band_lo_lin(unsigned mid0, int slope, long l
     return band_clamp((long long)mid0 + ((long long)slope * c) / 65536);
 }
 
-// First distance of chunk c's band in the second build: the sampled windows at chunks
-// DET_SAMPLE * s (s = 1..ns), linear in between, constant beyond the ends.
-__device__ __forceinline__ unsigned band_lo_tab(const unsigned short *ctr, unsigned ns, long long c)
+// Chunks between sampled windows: DET_SAMPLE, or fewer in a short batch so that it still
+// has about 16 samples.
+__device__ __forceinline__ unsigned sample_step(unsigned nchunks)
 {
-    const long long s0 = c / DET_SAMPLE;
-    if (s0 < 1) return band_clamp(ctr[1]);
-    if (s0 >= (long long)ns) return band_clamp(ctr[ns]);
-    const long long a = ctr[s0], b = ctr[s0 + 1], r = c - s0 * DET_SAMPLE;
-    return band_clamp(a + (b - a) * r / (long long)DET_SAMPLE);
+    return nchunks >= 16 * DET_SAMPLE ? DET_SAMPLE : max(1u, nchunks / 16);
 }
-
 __device__ __forceinline__ unsigned n_samples_of(unsigned nchunks)
 {
-    return nchunks > 0 ? (nchunks - 1) / DET_SAMPLE : 0u;
+    return nchunks > 0 ? (nchunks - 1) / sample_step(nchunks) : 0u;
+}
+
+// First distance of chunk c's band in the second build: the sampled windows at chunks
+// step * s (s = 1..ns), linear in between, constant beyond the ends.
+__device__ __forceinline__ unsigned band_lo_tab(const unsigned short *ctr, unsigned ns, unsigned step, long long c)
+{
+    const long long s0 = c / step;
+    if (s0 < 1) return band_clamp(ctr[1]);
+    if (s0 >= (long long)ns) return band_clamp(ctr[ns]);
+    const long long a = ctr[s0], b = ctr[s0 + 1], r = c - s0 * step;
+    return band_clamp(a + (b - a) * r / (long long)step);
 }
 
 // Chunk length S: at least CHUNK, at most DET_MAX_CHUNKS chunks per batch, and DET_G
@@ -89,18 +96,22 @@ __device__ __forceinline__ Geo geometry(const KParams &kp, const Ctrl *ctrl)
     g.base = ctrl->base;
     g.m = ctrl->m;
     const unsigned long long qprev = g.base - (unsigned long long)ctrl->det.h;
-    // growth per event over the previous batch, within [-1, 1] (16.16), when the queue
-    // changed by more than an eighth over it (a stream filling up); a queue that only
-    // wanders keeps a flat band, and the sampled windows catch the rest
-    long long slope = 0;
-    const long long dq = ctrl->grow_num < 0 ? -ctrl->grow_num : ctrl->grow_num;
-    if (ctrl->grow_den >= GROW_MIN_EVENTS && dq * 8 > (long long)qprev) {
-        slope = ctrl->grow_num * 65536 / (long long)ctrl->grow_den;
-        slope = max(-65536ll, min(65536ll, slope));
+    // growth per event over the previous batch, within [-1, 1] (16.16)
+    long long rate = 0;
+    if (ctrl->grow_den >= GROW_MIN_EVENTS) {
+        rate = ctrl->grow_num * 65536 / (long long)ctrl->grow_den;
+        rate = max(-65536ll, min(65536ll, rate));
     }
+    // the band drifts at that rate only when the queue changed by more than an eighth over
+    // the previous batch (a stream filling up); a queue that only wanders keeps a flat
+    // band, and the sampled windows catch the rest
+    const long long dq = ctrl->grow_num < 0 ? -ctrl->grow_num : ctrl->grow_num;
+    const long long slope = dq * 8 > (long long)qprev ? rate : 0;
+    // the table reaches 1.25 times the queue at the batch start (639 of DET_G / 2
+    // chunks); a queue expected to grow beyond 1.2 times it sizes the chunks instead
     const long long q_end = max((long long)kp.q_min,
-                                min((long long)kp.q_max, (long long)qprev + slope * (long long)g.m / 65536));
-    const unsigned long long q_hi = max(qprev, (unsigned long long)q_end);
+                                min((long long)kp.q_max, (long long)qprev + rate * (long long)g.m / 65536));
+    const unsigned long long q_hi = (unsigned long long)q_end * 5 > qprev * 6 ? (unsigned long long)q_end : qprev;
     unsigned long long S = (2ull * q_hi + 4ull * CHUNK + DET_G - 1) / DET_G;
     S = max(S, ((unsigned long long)g.m + DET_MAX_CHUNKS - 1) / DET_MAX_CHUNKS);
     if (qprev < kp.npix / 32) {
@@ -200,7 +211,7 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HistSmem &H = *reinterpret_cast<HistSmem *>(smem_raw);
     const Geo g = geometry(kp, ctrl);
-    const unsigned ns = n_samples_of(g.nchunks);
+    const unsigned ns = n_samples_of(g.nchunks), sstep = sample_step(g.nchunks);
     const unsigned tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
     const unsigned nwork = g.nchunks + g.Gold;
     const unsigned nunits = 2 * ((nwork + HB_CHUNKS - 1) / HB_CHUNKS);
@@ -210,7 +221,7 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
     const int g_hi_all = kBuild ? HB_BINS - 1 : (int)g.g_hi_max;
     unsigned *bc = base_cnt + (size_t)kBuild * 2 * mt_rows;
     auto band_of = [&](long long ct) -> int {
-        return kBuild ? (int)band_lo_tab(ctr, ns, ct) : (int)band_lo_lin(g.mid0, g.slope, ct);
+        return kBuild ? (int)band_lo_tab(ctr, ns, sstep, ct) : (int)band_lo_lin(g.mid0, g.slope, ct);
     };
     const ChunkDiv div_S(g.S);
     for (unsigned unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
@@ -287,16 +298,17 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
                 base_t[(size_t)ct * MT_PITCH + (d - gl)] = (unsigned short)H.h[cc][hb_slot(d)];
         }
         if (kBuild == 0 && ns > 0) {
-            // columns of the sampled targets DET_SAMPLE * s within reach of the sources:
-            // prof[t][s][d] = M(DET_SAMPLE * s, d), d in 1..639 (16 threads write the 16
+            // columns of the sampled targets sstep * s within reach of the sources:
+            // prof[t][s][d] = M(sstep * s, d), d in 1..639 (16 threads write the 16
             // consecutive distances one sample takes from the block's sources)
             const int t_lo = (int)c_lo + 1, t_hi = (int)c_lo + HB_CHUNKS - 1 + (HB_BINS - 1);
-            const int s_lo = t_lo <= (int)DET_SAMPLE ? 1 : (t_lo + (int)DET_SAMPLE - 1) / (int)DET_SAMPLE;
-            const int s_hi = min((int)ns, t_hi / (int)DET_SAMPLE);
+            const int st = (int)sstep;
+            const int s_lo = t_lo <= st ? 1 : (t_lo + st - 1) / st;
+            const int s_hi = min((int)ns, t_hi / st);
             unsigned short *pt = prof + (size_t)t * n_samples * HB_BINS;
             for (int i = (int)tid; i < (s_hi - s_lo + 1) * HB_CHUNKS; i += 256) {
                 const int sidx = s_lo + i / HB_CHUNKS, cc = i % HB_CHUNKS;
-                const int d = sidx * (int)DET_SAMPLE - ((int)c_lo + cc);
+                const int d = sidx * st - ((int)c_lo + cc);
                 if (d >= 1 && d <= HB_BINS - 1)
                     pt[(size_t)sidx * HB_BINS + d] = (unsigned short)H.h[cc][hb_slot(d)];
             }
@@ -312,7 +324,7 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
     }
 }
 
-// The regulator's window at every sampled chunk c = DET_SAMPLE * s (one warp each): the
+// The regulator's window at every sampled chunk c = step * s (one warp each): the
 // shortest aligned window of the column prof[.][s][1..639] that the regulator would
 // shrink (the test of k_det_init), or the longest one that exists.  If one of them lies
 // outside (or within BAND_MARGIN of the edge of) the first build's band, band_mode asks
@@ -326,12 +338,12 @@ k_det_center(KParams kp, Ctrl *ctrl, const unsigned short *prof, size_t n_sample
     const unsigned S = ctrl->S, nch = ctrl->nchunks, Gold = ctrl->Gold;
     const unsigned mid0 = ctrl->band_mid0;
     const int slope = ctrl->band_slope;
-    const unsigned ns = n_samples_of(nch);
+    const unsigned ns = n_samples_of(nch), sstep = sample_step(nch);
     const unsigned warps_total = gridDim.x * (blockDim.x >> 5);
     constexpr int PER = HB_BINS / 32;  // distances per lane
     bool out = false;
     for (unsigned s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) + 1; s <= ns; s += warps_total) {
-        const unsigned c = s * DET_SAMPLE;
+        const unsigned c = s * sstep;
         const unsigned gmax = min((unsigned)(HB_BINS - 1), c + Gold);  // sources that exist
         const unsigned long long reach = (unsigned long long)c * S + base;
         const unsigned short *pp = prof + (size_t)s * HB_BINS;
@@ -422,11 +434,11 @@ __device__ __forceinline__ void init_chunks(const KParams &kp, const Ctrl *ctrl,
     const unsigned S = ctrl->S, nch = ctrl->nchunks, Gold = ctrl->Gold;
     const unsigned mid0 = ctrl->band_mid0;
     const int slope = ctrl->band_slope;
-    const unsigned ns = n_samples_of(nch);
+    const unsigned ns = n_samples_of(nch), sstep = sample_step(nch);
     unsigned *bc = base_cnt + (size_t)kMode * 2 * mt_rows;
     const unsigned warps_total = gridDim.x * (blockDim.x >> 5);
     for (unsigned c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) + 1; c < nch; c += warps_total) {
-        const unsigned g_lo = kMode ? band_lo_tab(ctr, ns, c) : band_lo_lin(mid0, slope, c);
+        const unsigned g_lo = kMode ? band_lo_tab(ctr, ns, sstep, c) : band_lo_lin(mid0, slope, c);
         const unsigned g_hi = g_lo + DET_BAND - 1;
         const unsigned short *rp = Mt + (size_t)c * MT_PITCH;
         const unsigned short *rt = Mt + (mt_rows + c) * MT_PITCH;
