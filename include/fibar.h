@@ -246,6 +246,14 @@ int fibar_debug_state(fibar_t *h, fibar_state_view_t *v, void *cuda_stream);
  * ordered. */
 int fibar_queue_counts_noalloc(fibar_t *h, uint32_t *cnt, int on_device, void *cuda_stream);
 
+/* Failure-detection check (no counterpart in the paper): runs, on the device, the bounded
+ * wait that the pipeline's look-back and dataflow kernels use, on a flag that nothing
+ * sets, with a limit of max_spins polls (1..2^20, each followed by a ~64 ns back-off).
+ * The wait gives up, records its flag in the handle's error word and returns; this call
+ * synchronises, clears that flag again (the handle stays usable) and returns ETIMEOUT,
+ * with a message.  Errors: EINVAL, ENOMEM, ECUDA. */
+int fibar_debug_wait_timeout(fibar_t *h, uint32_t max_spins, void *cuda_stream);
+
 /* Synchronise and fill counters.  Reports ETIMEOUT if a device wait gave up. */
 int fibar_stats(fibar_t *h, fibar_stats_t *s, void *cuda_stream);
 

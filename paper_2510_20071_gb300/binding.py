@@ -25,7 +25,7 @@ EXPORTED = ["fibar_default_params", "fibar_create", "fibar_push_events", "fibar_
             "fibar_flush", "fibar_debug_state", "fibar_stats", "fibar_set_timing",
             "fibar_stage_times", "fibar_last_error", "fibar_destroy", "fibar_queue_counts_noalloc",
             "fibar_readout_batch", "fibar_memory_bytes", "fibar_relative_thresholds",
-            "fibar_set_pixel_gain"]
+            "fibar_set_pixel_gain", "fibar_debug_wait_timeout"]
 
 STAGES = ["decode", "sort", "walk", "det_counts", "det_pass1", "det_pass2", "det_fix", "s1_blur",
           "readout", "commit"]
@@ -115,6 +115,8 @@ def load_library(build_if_missing: bool = True):
             lib.fibar_relative_thresholds.restype = C.c_int
             lib.fibar_set_pixel_gain.argtypes = [vp, vp, C.c_int, vp]
             lib.fibar_set_pixel_gain.restype = C.c_int
+            lib.fibar_debug_wait_timeout.argtypes = [vp, C.c_uint32, vp]
+            lib.fibar_debug_wait_timeout.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -197,6 +199,10 @@ def fibar_relative_thresholds(ev_ptr: int, n: int, W: int, H: int, on_device: in
 
 def fibar_set_pixel_gain(h, gain_ptr, on_device: int, stream: int) -> int:
     return load_library().fibar_set_pixel_gain(h, gain_ptr, on_device, stream)
+
+
+def fibar_debug_wait_timeout(h, max_spins: int, stream: int) -> int:
+    return load_library().fibar_debug_wait_timeout(h, max_spins, stream)
 
 
 # --- convenience wrapper ---------------------------------------------------------------

@@ -276,10 +276,11 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     for_each_buffer(lo, b, [&](auto *&ptr, unsigned long long n) {
         if (e == cudaSuccess) e = dalloc(&ptr, n);
     });
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&h->snap_host, 2 * sizeof(unsigned), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&h->snap_host, 4 * sizeof(unsigned), cudaHostAllocMapped);
     if (e == cudaSuccess) {
         h->snap_host[0] = 0u;
         h->snap_host[1] = 0u;
+        h->snap_host[2] = 0u;
         e = cudaHostGetDevicePointer((void **)&b.snap, h->snap_host, 0);
     }
     if (e != cudaSuccess) {
@@ -344,6 +345,34 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     memset(h->stage_ms, 0, sizeof(h->stage_ms));
     h->stage_calls = 0;
     *out = h;
+    return FIBAR_OK;
+}
+
+extern "C" int fibar_debug_wait_timeout(fibar_t *h, uint32_t max_spins, void *cuda_stream)
+{
+    if (!h || max_spins == 0 || max_spins > (1u << 20)) return FIBAR_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    unsigned *flag = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&flag, sizeof(unsigned), s);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(h, FIBAR_ENOMEM, "debug_wait_timeout: allocation"); }
+    e = cudaMemsetAsync(flag, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = launch_probe_wait(h->b, flag, max_spins, s, h->launches);
+    unsigned err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &h->b.ctrl->error, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    // clear this probe's flag again (the pipeline's own flags stay as they were)
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && (err & ERR_PROBE_WAIT)) {
+        const unsigned keep = err & ~ERR_PROBE_WAIT;
+        e = cudaMemcpyAsync(&h->b.ctrl->error, &keep, sizeof(unsigned), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    cudaFreeAsync(flag, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "debug_wait_timeout");
+    if (err & ERR_PROBE_WAIT) {
+        char msg[128];
+        snprintf(msg, sizeof msg, "a bounded device wait gave up after %u polls (flags 0x%x)", max_spins, err);
+        return fail(h, FIBAR_ETIMEOUT, msg);
+    }
     return FIBAR_OK;
 }
 
@@ -544,11 +573,11 @@ int process(fibar_t *h, unsigned long long t_read, float *out, cudaStream_t s)
     return FIBAR_OK;
 }
 
+// After a synchronisation that covered the last commit: its copy of the error flags
+// (mapped host memory, no device round trip).
 int check_device_error(fibar_t *h)
 {
-    unsigned err = 0;
-    cudaError_t e = cudaMemcpy(&err, &h->b.ctrl->error, 4, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(h, e, "error flag");
+    const unsigned err = __atomic_load_n(&h->snap_host[2], __ATOMIC_ACQUIRE);
     if (err) {
         char msg[128];
         snprintf(msg, sizeof msg, "a bounded device wait gave up (flags 0x%x)", err);

@@ -32,6 +32,9 @@ constexpr int DEC_TILE = DEC_THREADS * DEC_PER_THREAD;   // records per decode t
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_PER_THREAD = 16;
 constexpr int SORT_TILE = SORT_THREADS * SORT_PER_THREAD;
+constexpr int SORT_WARP_RANGE = SORT_TILE / (SORT_THREADS / 32);  // records ranked by one warp
+constexpr int SORT_BLOCKS_PER_SM = 2;
+constexpr int DEC_BLOCKS_PER_SM = 2;
 constexpr int SORT_MAX_PASSES = 4;
 constexpr int RADIX_BITS = 9;                  // sort digit width (max)
 constexpr int RADIX = 1 << RADIX_BITS;
@@ -51,6 +54,7 @@ constexpr unsigned ERR_DEC_WAIT = 1u;
 constexpr unsigned ERR_SORT_WAIT = 2u;
 constexpr unsigned ERR_BAD_STATE = 4u;
 constexpr unsigned ERR_S1_WAIT = 8u;
+constexpr unsigned ERR_PROBE_WAIT = 16u;  // fibar_debug_wait_timeout
 
 // Detector state after some step: window [h, k] (h batch-relative or global, see use),
 // distinct pixels / tiles in the window, and q_targ for the next step as the ratio
@@ -149,7 +153,7 @@ struct Bufs {
     size_t mt_rows;              // chunk rows per table of dMt
     DetState *E0, *E1, *E2;
     unsigned int *p2_ids;        // [max_chunks] chunks continued by the warp-per-chunk pass 2
-    unsigned int *snap;          // mapped host memory: {records left pending, commits} after a commit
+    unsigned int *snap;          // mapped host memory: {records left pending, commits, error flags} after a commit
     unsigned char *merged;
     unsigned *unm_bits;          // [chunks / 32] chunks that did not merge in pass 2
     float *out_staging;
@@ -255,6 +259,8 @@ __device__ __forceinline__ unsigned warp_peers(unsigned v)
 
 // launchers (kernels live in their own translation units); `nl` counts kernel launches
 cudaError_t launch_init(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
+cudaError_t launch_probe_wait(const Bufs &b, const unsigned *flag, unsigned max_spins, cudaStream_t s,
+                              unsigned long long &nl);
 cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, unsigned sort_passes, cudaStream_t s,
                           unsigned long long &nl);
 cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsigned epoch,

@@ -163,10 +163,10 @@ __device__ __forceinline__ int4 fetch_rec_from(const SegTable &T, const int4 *co
     return __ldg(s_ptr[sg] + (pos - s_start[sg]));
 }
 
-// Shared-memory index of tile position r: one word of padding per 16, so that a thread's
-// run of 16 consecutive positions (thread t at 16 t) and a warp's 32 consecutive
-// positions both fall in distinct banks.
-__device__ __forceinline__ unsigned dpad(unsigned r) { return r + (r >> 4); }
+// Shared-memory index of tile position r: one word of padding per DEC_PER_THREAD, so that
+// a thread's run of consecutive positions (thread t at DEC_PER_THREAD t) and a warp's 32
+// consecutive positions both fall in distinct banks.
+__device__ __forceinline__ unsigned dpad(unsigned r) { return r + r / DEC_PER_THREAD; }
 
 // With a one-pass sort the decode also counts the kept records per bucket (the sort's
 // only digit) and the block that completes the last tile turns the counts into the
@@ -185,8 +185,8 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
     __shared__ __align__(8) unsigned long long s_bar;
     __shared__ unsigned s_start[MAXSEG + 1];
     __shared__ const int4 *s_ptr[MAXSEG];
-    __shared__ unsigned s_info[DEC_TILE + DEC_TILE / 16];  // indexed by dpad()
-    __shared__ unsigned s_pix[DEC_TILE + DEC_TILE / 16];
+    __shared__ unsigned s_info[DEC_TILE + DEC_TILE / DEC_PER_THREAD];  // indexed by dpad()
+    __shared__ unsigned s_pix[DEC_TILE + DEC_TILE / DEC_PER_THREAD];
     __shared__ unsigned s_warp[16];
     __shared__ unsigned s_tile, s_vmin, s_pre_s, s_pre_c, s_drop;
     __shared__ unsigned s_red_s[DEC_THREADS / 32], s_red_c[DEC_THREADS / 32];
@@ -287,7 +287,7 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
         __syncthreads();
         const unsigned vfirst = s_vmin;
 
-        // 16 contiguous records per thread, in arrival order
+        // DEC_PER_THREAD contiguous records per thread, in arrival order
         unsigned cnt = 0, drop = 0, keep = 0;
 #pragma unroll
         for (int j = 0; j < DEC_PER_THREAD; ++j) {
@@ -557,9 +557,10 @@ k_sort_pass(Ctrl *ctrl, const unsigned long long *in, unsigned long long *out, u
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         __syncthreads();
-        // stable rank within (warp range, digit): warp w owns records [w*512, w*512+512)
-        for (int q = 0; q < 16; ++q) {
-            const unsigned r = w * 512 + q * 32 + lane;
+        // stable rank within (warp range, digit): warp w owns records
+        // [w * SORT_WARP_RANGE, (w + 1) * SORT_WARP_RANGE)
+        for (int q = 0; q < SORT_WARP_RANGE / 32; ++q) {
+            const unsigned r = w * SORT_WARP_RANGE + q * 32 + lane;
             const bool valid = r < n_here;
             const unsigned d = valid ? (unsigned)(S.key[r] >> shift) & dmask : RADIX;
             const unsigned peers = warp_peers<10>(d);  // digit < 512, or RADIX (none)
@@ -657,7 +658,7 @@ k_sort_pass(Ctrl *ctrl, const unsigned long long *in, unsigned long long *out, u
             if (r < n_here) {
                 const unsigned long long k = S.key[r];
                 const unsigned dd = (unsigned)(k >> shift) & dmask;
-                const unsigned ww = r >> 9;
+                const unsigned ww = r / SORT_WARP_RANGE;
                 S.out[S.tdig[dd] + S.whist[ww][dd] + S.rank[r]] = k;
             }
         }
@@ -704,7 +705,7 @@ cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, u
         dh.gbase = b.sort_base;
         dh.bucket_start = b.bucket_start;
     }
-    if (cudaError_t e_ = launch_pdl(k_decode, grid_for(2), DEC_THREADS, smem, s, kp, t, b.ctrl, b.dec_status, b.rec[0],
+    if (cudaError_t e_ = launch_pdl(k_decode, grid_for(DEC_BLOCKS_PER_SM), DEC_THREADS, smem, s, kp, t, b.ctrl, b.dec_status, b.rec[0],
                                     kp.spatial ? b.ring_pix : nullptr, dh)) return e_;
     return cudaGetLastError();
 }
@@ -728,7 +729,7 @@ cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsig
                                         kp.nbuckets, b.sort_hist, b.sort_base, b.bucket_cnt, b.bucket_start))
             return e_;
     for (unsigned p = 0; p < passes; ++p) {
-        if (cudaError_t e_ = launch_pdl(k_sort_pass, grid_for(2), SORT_THREADS, smem, s, b.ctrl, b.rec[p & 1],
+        if (cudaError_t e_ = launch_pdl(k_sort_pass, grid_for(SORT_BLOCKS_PER_SM), SORT_THREADS, smem, s, b.ctrl, b.rec[p & 1],
                                         b.rec[(p + 1) & 1], p, dbits, kp.lb, epoch + p, b.sort_base, b.sort_rows,
                                         b.sort_rowflag, b.sort_gtot, b.sort_gflag, b.sort_gcount))
             return e_;

@@ -89,10 +89,28 @@ __global__ void k_commit(Ctrl *ctrl, unsigned long long *dec_status, size_t n_st
         ctrl->batch_no += 1;
         // the carry slot just consumed becomes the output slot of the next decode
         ctrl->carry_n[1 - next_carry_slot] = 0;
-        // for the host: the records left pending, then (ordered after it) this commit's number
+        // for the host: the records left pending and the error flags, then (ordered after
+        // them) this commit's number
         snap[0] = ctrl->carry_n[next_carry_slot];
+        snap[2] = ctrl->error;
         __threadfence_system();
         *(volatile unsigned *)&snap[1] = ctrl->batch_no - 1u;
+    }
+}
+
+// The bounded wait of the pipeline's look-back and dataflow kernels, on a flag that
+// nothing sets: after max_spins polls (with the same back-off) it records ERR_PROBE_WAIT
+// in the error flags and returns, as a wait that gives up does.
+__global__ void k_probe_wait(Ctrl *ctrl, const unsigned *flag, unsigned max_spins)
+{
+    if (threadIdx.x != 0) return;
+    unsigned spins = 0;
+    while (*(volatile const unsigned *)flag == 0u) {
+        if (++spins > max_spins) {
+            atomicOr(&ctrl->error, ERR_PROBE_WAIT);
+            return;
+        }
+        __nanosleep(64);
     }
 }
 
@@ -167,6 +185,14 @@ cudaError_t launch_readout(const KParams &kp, const Bufs &b, float *out, cudaStr
             return cudaMemcpyAsync(out, b.L, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
         }
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe_wait(const Bufs &b, const unsigned *flag, unsigned max_spins, cudaStream_t s,
+                              unsigned long long &nl)
+{
+    nl += 1;
+    k_probe_wait<<<1, 32, 0, s>>>(b.ctrl, flag, max_spins);
     return cudaGetLastError();
 }
 

@@ -209,3 +209,28 @@ def test_determinism(oracle_mod):
         b = run_gpu(W, H, ev, steps, **MODES[mode])
         for x, y in zip(a[0], b[0]):
             np.testing.assert_array_equal(x, y)
+
+
+def test_bounded_device_wait_reports_timeout_and_handle_recovers(oracle_mod):
+    """A bounded device wait on a flag that nothing sets gives up after its poll limit and
+    the host reads ETIMEOUT (no trap, no hang); the handle keeps working afterwards."""
+    from paper_2510_20071_gb300 import Fibar, FIBAR_ETIMEOUT, binding
+    W, H = 32, 24
+    ev = eventsim.random_events(W, H, 4000, seed=12)
+    f = Fibar(W, H, spatial_filter=1, blur_mode=1, q_min=4)
+    try:
+        f.push(ev[:2000].cuda())
+        f.readout(int(ev[1999, 1]))
+        rc = binding.fibar_debug_wait_timeout(f.h, 2000, f._s)
+        assert rc == FIBAR_ETIMEOUT
+        assert "gave up" in binding.fibar_last_error(f.h)
+        assert binding.fibar_debug_wait_timeout(f.h, 0, f._s) == binding.FIBAR_EINVAL
+        f.push(ev[2000:].cuda())
+        out = torch.empty((H, W), dtype=torch.float32).pin_memory()
+        f.readout(int(ev[-1, 1]), out)  # host read-out checks the error flags: none left
+        o = oracle_mod.Oracle(W, H, spatial_filter=1, blur_mode=1, q_min=4)
+        o.push(ev[:2000]); o.readout(int(ev[1999, 1])); o.push(ev[2000:])
+        np.testing.assert_allclose(out.numpy(), o.readout(int(ev[-1, 1])), atol=1e-4, rtol=0)
+        assert f.stats()["events_applied"] == 4000
+    finally:
+        f.close()
