@@ -165,7 +165,7 @@ __device__ __forceinline__ long long chunk_of(long long x, unsigned S, unsigned 
 // its band [g_lo(c), g_hi(c)]:
 //   base[t][c]             = N(c, g_lo(c) - 1)                (accumulated with atomics)
 //   Mt[t][c][g - g_lo(c)]  = M(c, g) for g in [g_lo(c), g_hi(c)]  (a contiguous row)
-// A block handles HB_CHUNKS consecutive source chunks and one t: the histogram of chunk
+// A block handles HB_CHUNKS consecutive source chunks and both t: the histograms of chunk
 // distances in shared memory (one word of padding per 32 bins and a row pitch of 2 mod
 // 32 words, so that a lane's run of 32 bins and the diagonal reads both spread over the
 // banks), suffix sums in registers, then per target the sum of its distances below the
@@ -178,7 +178,7 @@ constexpr int MT_PITCH = DET_BAND;  // u16 per target row (512 B: 16-byte aligne
 __device__ __forceinline__ int hb_slot(int d) { return d + (d >> 5); }
 
 struct HistSmem {
-    unsigned h[HB_CHUNKS][HB_PITCH];
+    unsigned h[2][HB_CHUNKS][HB_PITCH];  // [pixel, tile][source chunk][distance]
     short gl[HB_CHUNKS + HB_BINS];  // first band distance of target c_lo + D (0: no target)
 };
 
@@ -214,7 +214,7 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
     const unsigned ns = n_samples_of(g.nchunks), sstep = sample_step(g.nchunks);
     const unsigned tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
     const unsigned nwork = g.nchunks + g.Gold;
-    const unsigned nunits = 2 * ((nwork + HB_CHUNKS - 1) / HB_CHUNKS);
+    const unsigned nunits = (nwork + HB_CHUNKS - 1) / HB_CHUNKS;
     const long long lo_exist = -(long long)g.base;
     // distances whose band entries some target may need
     const int D0 = kBuild ? 1 : (int)g.g_lo_min;
@@ -225,17 +225,16 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
     };
     const ChunkDiv div_S(g.S);
     for (unsigned unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
-        const int t = unit & 1;
-        const long long c_lo = (long long)((unit >> 1) * HB_CHUNKS) - (long long)g.Gold;  // first source chunk
-        uint4 *hw = reinterpret_cast<uint4 *>(&H.h[0][0]);
-        for (unsigned i = tid; i < HB_CHUNKS * HB_PITCH / 4; i += 256) hw[i] = make_uint4(0u, 0u, 0u, 0u);
+        const long long c_lo = (long long)(unit * HB_CHUNKS) - (long long)g.Gold;  // first source chunk
+        uint4 *hw = reinterpret_cast<uint4 *>(&H.h[0][0][0]);
+        for (unsigned i = tid; i < 2 * HB_CHUNKS * HB_PITCH / 4; i += 256) hw[i] = make_uint4(0u, 0u, 0u, 0u);
         for (unsigned D = tid; D < HB_CHUNKS + HB_BINS; D += 256) {
             const long long ct = c_lo + D;
             H.gl[D] = (short)(ct >= 1 && ct < (long long)g.nchunks ? band_of(ct) : 0);
         }
         __syncthreads();
-        // histogram of the chunk distance to the next event of the same pixel / tile
-        // (distances beyond the table counted at its last one)
+        // histograms of the chunk distance to the next event of the same pixel and of the
+        // same tile (distances beyond the table counted at its last one)
         const long long j_lo = c_lo * g.S;
         const unsigned n_hi = (unsigned)min((long long)HB_CHUNKS * g.S, (long long)g.m - j_lo);
         const unsigned n_lo = (unsigned)max(0ll, lo_exist - j_lo);
@@ -243,17 +242,19 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
         for (unsigned i = n_lo + tid; i < n_hi; i += 256) {
             const unsigned long long j = g.base + (unsigned long long)(j_lo + i);
             const uint2 n = nxt_of(ring, j & kp.ring_mask);
-            const unsigned nv = t ? n.y : n.x;
             const unsigned cc = div_S(i), r = i - cc * g.S;
-            const unsigned long long rel = (unsigned long long)r + nv;  // from the start of chunk cc
-            const unsigned d = (nv == SAT || rel >= lim) ? (unsigned)(HB_BINS - 1) : div_S((unsigned)rel);
-            atomicAdd(&H.h[cc][hb_slot((int)d)], 1u);
+            // distances from the start of chunk cc, in chunks
+            const unsigned long long rp = (unsigned long long)r + n.x, rt = (unsigned long long)r + n.y;
+            const unsigned dp = (n.x == SAT || rp >= lim) ? (unsigned)(HB_BINS - 1) : div_S((unsigned)rp);
+            const unsigned dt = (n.y == SAT || rt >= lim) ? (unsigned)(HB_BINS - 1) : div_S((unsigned)rt);
+            atomicAdd(&H.h[0][cc][hb_slot((int)dp)], 1u);
+            atomicAdd(&H.h[1][cc][hb_slot((int)dt)], 1u);
         }
         __syncthreads();
-        // suffix sums over d: warp per chunk, lane l owns bins 32l .. 32l+31
-        for (unsigned cc = wl; cc < HB_CHUNKS; cc += 8) {
+        // suffix sums over d: warp per (type, chunk) row, lane l owns bins 32l .. 32l+31
+        for (unsigned rw = wl; rw < 2 * HB_CHUNKS; rw += 8) {
             const bool own = lane < HB_BINS / 32;
-            unsigned *row = &H.h[cc][33 * (own ? lane : 0)];
+            unsigned *row = &H.h[rw / HB_CHUNKS][rw % HB_CHUNKS][33 * (own ? lane : 0)];
             unsigned v[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = own ? row[i] : 0u;
@@ -277,25 +278,31 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
             const long long ct = c_lo + D;
             const int gl = H.gl[D];
             if (gl == 0) continue;
-            unsigned acc = 0;
+            unsigned acc0 = 0, acc1 = 0;
 #pragma unroll
             for (int cc = 0; cc < HB_CHUNKS; ++cc) {
                 const int d = D - cc;
-                if (d >= 1 && d < gl) acc += H.h[cc][hb_slot(d)];
+                if (d >= 1 && d < gl) {
+                    acc0 += H.h[0][cc][hb_slot(d)];
+                    acc1 += H.h[1][cc][hb_slot(d)];
+                }
             }
-            if (acc) atomicAdd(&bc[(size_t)t * mt_rows + ct], acc);
+            if (acc0) atomicAdd(&bc[ct], acc0);
+            if (acc1) atomicAdd(&bc[mt_rows + ct], acc1);
         }
         // the bands: target row c_lo + D receives distances D-15 .. D from the block's
-        // sources; HB_CHUNKS threads write one row's run
-        unsigned short *base_t = Mt + (size_t)t * mt_rows * MT_PITCH;
+        // sources; HB_CHUNKS threads write one row's run (both types)
         const int D1 = g_hi_all + HB_CHUNKS - 1;  // targets with some band distance
         for (unsigned i = tid; i < (unsigned)(D1 - D0 + 1) * HB_CHUNKS; i += 256) {
             const int D = D0 + (int)(i / HB_CHUNKS), u = (int)(i % HB_CHUNKS);
             const int cc = HB_CHUNKS - 1 - u, d = D - cc;
             const long long ct = c_lo + D;  // target chunk
             const int gl = H.gl[D];
-            if (gl != 0 && d >= gl && d < gl + (int)DET_BAND)
-                base_t[(size_t)ct * MT_PITCH + (d - gl)] = (unsigned short)H.h[cc][hb_slot(d)];
+            if (gl != 0 && d >= gl && d < gl + (int)DET_BAND) {
+                const size_t at = (size_t)ct * MT_PITCH + (d - gl);
+                Mt[at] = (unsigned short)H.h[0][cc][hb_slot(d)];
+                Mt[(size_t)mt_rows * MT_PITCH + at] = (unsigned short)H.h[1][cc][hb_slot(d)];
+            }
         }
         if (kBuild == 0 && ns > 0) {
             // columns of the sampled targets sstep * s within reach of the sources:
@@ -305,12 +312,13 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
             const int st = (int)sstep;
             const int s_lo = t_lo <= st ? 1 : (t_lo + st - 1) / st;
             const int s_hi = min((int)ns, t_hi / st);
-            unsigned short *pt = prof + (size_t)t * n_samples * HB_BINS;
             for (int i = (int)tid; i < (s_hi - s_lo + 1) * HB_CHUNKS; i += 256) {
                 const int sidx = s_lo + i / HB_CHUNKS, cc = i % HB_CHUNKS;
                 const int d = sidx * st - ((int)c_lo + cc);
-                if (d >= 1 && d <= HB_BINS - 1)
-                    pt[(size_t)sidx * HB_BINS + d] = (unsigned short)H.h[cc][hb_slot(d)];
+                if (d >= 1 && d <= HB_BINS - 1) {
+                    prof[(size_t)sidx * HB_BINS + d] = (unsigned short)H.h[0][cc][hb_slot(d)];
+                    prof[((size_t)n_samples + sidx) * HB_BINS + d] = (unsigned short)H.h[1][cc][hb_slot(d)];
+                }
             }
         }
         __syncthreads();
