@@ -1040,16 +1040,23 @@ k_det_pass2(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *qout,
         }
         unsigned steps = 0;
         const bool mg = lane_run<true>(kp, base, ring, qout, k0, k1, k0, st, sm, ctrl, &steps);
+        // one atomic per warp for the step count and for the list of continuing chunks
+        const unsigned wsteps = warp_sum(real ? steps : 0u);
+        const bool cont = real && !mg && k1 < kend;  // continues in k_det_pass2w from k1
+        const unsigned cb = __ballot_sync(0xFFFFFFFFu, cont);
+        unsigned slot0 = 0;
+        if (lane == 0) {
+            if (wsteps) atomicAdd(&ctrl->pass2_steps, (unsigned long long)wsteps);
+            if (cb) slot0 = atomicAdd(&ctrl->p2_count, (unsigned)__popc(cb));
+        }
+        slot0 = __shfl_sync(0xFFFFFFFFu, slot0, 0);
         if (real) {
-            atomicAdd(&ctrl->pass2_steps, (unsigned long long)steps);
             merged[c] = mg;
-            if (!mg) {
-                if (k1 < kend) {  // continue in k_det_pass2w from the state at k1
-                    E2[c] = st;
-                    p2_ids[atomicAdd(&ctrl->p2_count, 1u)] = c;
-                } else {
-                    p2_unmerged(ctrl, st, c, E2, unm_bits);
-                }
+            if (cont) {
+                E2[c] = st;
+                p2_ids[slot0 + __popc(cb & ((1u << lane) - 1u))] = c;
+            } else if (!mg) {
+                p2_unmerged(ctrl, st, c, E2, unm_bits);
             }
         }
     }
