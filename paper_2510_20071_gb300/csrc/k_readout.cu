@@ -3,49 +3,61 @@
 // k_readout_s2 - masked separable 3x3 Gaussian ([1,2,1] x [1,2,1] / 16, weights of taps
 //   outside the sensor dropped and the rest renormalised, Sec. 4.2's 3x3 Gaussian):
 //   out_i = blur(L)_i where pixel i is stale (had an event, none queued: last_pix < h),
-//   L_i elsewhere.  Each block stages a (32+2) x (8+2) halo of L in shared memory and
-//   applies the horizontal then the vertical [1,2,1] pass.
+//   L_i elsewhere.  Each block stages a (32+2) x (32+2) halo of L in shared memory and
+//   applies the horizontal then the vertical [1,2,1] pass; a thread owns four rows.
 // k_commit     - advances the batch base and resets the per-read-out counters.
 #include "fibar_internal.cuh"
 
 namespace fibar {
 
-constexpr int RB_X = 32, RB_Y = 8;
+constexpr int RB_X = 32, RB_Y = 8;  // threads per block
+constexpr int RB_ROWS = 4;          // rows per thread: a block covers 32 x 32 pixels
+constexpr int RB_TY = RB_Y * RB_ROWS;
 
 __global__ void __launch_bounds__(RB_X *RB_Y)
 k_readout_s2(KParams kp, const Ctrl *ctrl, const float *__restrict__ L,
              const unsigned long long *__restrict__ last_pix, float *__restrict__ out)
 {
     PDL_ENTRY();
-    __shared__ float t[RB_Y + 2][RB_X + 2];
-    __shared__ float hs[RB_Y + 2][RB_X];
-    const int x0 = blockIdx.x * RB_X, y0 = blockIdx.y * RB_Y;
+    __shared__ float t[RB_TY + 2][RB_X + 2];
+    __shared__ float hs[RB_TY + 2][RB_X];
+    const int x0 = blockIdx.x * RB_X, y0 = blockIdx.y * RB_TY;
     const int W = (int)kp.W, H = (int)kp.H;
-    for (int i = threadIdx.x; i < (RB_Y + 2) * (RB_X + 2); i += RB_X * RB_Y) {
-        const int ly = i / (RB_X + 2), lx = i % (RB_X + 2);
-        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-        t[ly][lx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? L[(size_t)gy * W + gx] : 0.f;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < (RB_Y + 2) * RB_X; i += RB_X * RB_Y) {
-        const int ly = i / RB_X, lx = i % RB_X;
-        hs[ly][lx] = t[ly][lx] + 2.f * t[ly][lx + 1] + t[ly][lx + 2];
-    }
-    __syncthreads();
     const int lx = threadIdx.x % RB_X, ly = threadIdx.x / RB_X;
-    const int x = x0 + lx, y = y0 + ly;
-    if (x >= W || y >= H) return;
-    const size_t i = (size_t)y * W + x;
+    const int x = x0 + lx;
+    // the mask inputs first, so that their loads overlap the halo's
     const unsigned long long h = (unsigned long long)ctrl->det.h;
-    const unsigned long long lp = last_pix[i];
-    const bool stale = lp != NONE64 && lp < h;
-    float v = t[ly + 1][lx + 1];
-    if (stale) {
-        const float wx = 4.f - (x == 0 ? 1.f : 0.f) - (x == W - 1 ? 1.f : 0.f);
-        const float wy = 4.f - (y == 0 ? 1.f : 0.f) - (y == H - 1 ? 1.f : 0.f);
-        v = (hs[ly][lx] + 2.f * hs[ly + 1][lx] + hs[ly + 2][lx]) / (wx * wy);
+    unsigned long long lp[RB_ROWS];
+#pragma unroll
+    for (int r = 0; r < RB_ROWS; ++r) {
+        const int y = y0 + ly + r * RB_Y;
+        lp[r] = (x < W && y < H) ? last_pix[(size_t)y * W + x] : NONE64;
     }
-    out[i] = v;
+    for (int i = threadIdx.x; i < (RB_TY + 2) * (RB_X + 2); i += RB_X * RB_Y) {
+        const int ty = i / (RB_X + 2), tx = i % (RB_X + 2);
+        const int gx = x0 + tx - 1, gy = y0 + ty - 1;
+        t[ty][tx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? L[(size_t)gy * W + gx] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (RB_TY + 2) * RB_X; i += RB_X * RB_Y) {
+        const int ty = i / RB_X, tx = i % RB_X;
+        hs[ty][tx] = t[ty][tx] + 2.f * t[ty][tx + 1] + t[ty][tx + 2];
+    }
+    __syncthreads();
+    if (x >= W) return;
+    const float wx = 4.f - (x == 0 ? 1.f : 0.f) - (x == W - 1 ? 1.f : 0.f);
+#pragma unroll
+    for (int r = 0; r < RB_ROWS; ++r) {
+        const int ty = ly + r * RB_Y, y = y0 + ty;
+        if (y >= H) break;
+        const bool stale = lp[r] != NONE64 && lp[r] < h;
+        float v = t[ty + 1][lx + 1];
+        if (stale) {
+            const float wy = 4.f - (y == 0 ? 1.f : 0.f) - (y == H - 1 ? 1.f : 0.f);
+            v = (hs[ty][lx] + 2.f * hs[ty + 1][lx] + hs[ty + 2][lx]) / (wx * wy);
+        }
+        out[(size_t)y * W + x] = v;
+    }
 }
 
 __global__ void k_copy(const float4 *__restrict__ in, float4 *__restrict__ out, size_t n4,
@@ -172,7 +184,7 @@ cudaError_t launch_readout(const KParams &kp, const Bufs &b, float *out, cudaStr
 {
     nl += 1;
     if (kp.spatial && kp.blur_mode == 1) {
-        dim3 grid((kp.W + RB_X - 1) / RB_X, (kp.H + RB_Y - 1) / RB_Y);
+        dim3 grid((kp.W + RB_X - 1) / RB_X, (kp.H + RB_TY - 1) / RB_TY);
         if (cudaError_t e_ = launch_pdl(k_readout_s2, grid, RB_X * RB_Y, 0, s, kp, b.ctrl, b.L, b.last_pix, out)) return e_;
     } else {
         const size_t n = kp.npix;
