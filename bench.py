@@ -552,8 +552,8 @@ def run_e2e(args, ev, plan, params, torch):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for pk, t in plan[args.warmup:]:
-        for lo, hi in pk:
-            f.push(host[lo - lo_all:hi - lo_all])
+        # the step's packets in one call (adjacent packets: one host-to-device copy)
+        f.push_many([host[lo - lo_all:hi - lo_all] for lo, hi in pk])
         f.readout(t, out)  # host image: waits for the result
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0

@@ -157,6 +157,16 @@ int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *p, fibar_t **out)
 int fibar_push_events(fibar_t *h, const fibar_event_t *ev, size_t n, int on_device,
                       void *cuda_stream);
 
+/* Queue several packets in one call: for i < count, what fibar_push_events(h, evs[i],
+ * ns[i], on_device, cuda_stream) does, in order.  Packets that follow each other in
+ * memory (evs[i] + ns[i] == evs[i + 1]) are queued as one: one host-to-device copy for
+ * host packets, one pending segment for device packets.  The paper has no counterpart;
+ * this saves a call and a copy per packet for callers that receive packets in bursts.
+ * Stops at the first run that fails (the earlier ones stay queued) and returns its error
+ * (as fibar_push_events). */
+int fibar_push_events_many(fibar_t *h, const fibar_event_t *const *evs, const size_t *ns, size_t count,
+                           int on_device, void *cuda_stream);
+
 /* Apply the longest prefix of pending events whose time stamps are all <= t_us
  * (Eq. 4's t_k <= t, in push order), then write the W*H float image (row-major) to
  * `out`: L for S1 and NSF (Sec. 1: no work at read-out), or the masked 3x3 blur of

@@ -25,7 +25,7 @@ EXPORTED = ["fibar_default_params", "fibar_create", "fibar_push_events", "fibar_
             "fibar_flush", "fibar_debug_state", "fibar_stats", "fibar_set_timing",
             "fibar_stage_times", "fibar_last_error", "fibar_destroy", "fibar_queue_counts_noalloc",
             "fibar_readout_batch", "fibar_memory_bytes", "fibar_relative_thresholds",
-            "fibar_set_pixel_gain", "fibar_debug_wait_timeout"]
+            "fibar_set_pixel_gain", "fibar_debug_wait_timeout", "fibar_push_events_many"]
 
 STAGES = ["decode", "sort", "walk", "det_counts", "det_pass1", "det_pass2", "det_fix", "s1_blur",
           "readout", "commit"]
@@ -117,6 +117,8 @@ def load_library(build_if_missing: bool = True):
             lib.fibar_set_pixel_gain.restype = C.c_int
             lib.fibar_debug_wait_timeout.argtypes = [vp, C.c_uint32, vp]
             lib.fibar_debug_wait_timeout.restype = C.c_int
+            lib.fibar_push_events_many.argtypes = [vp, C.POINTER(vp), C.POINTER(C.c_size_t), C.c_size_t, C.c_int, vp]
+            lib.fibar_push_events_many.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -201,6 +203,12 @@ def fibar_set_pixel_gain(h, gain_ptr, on_device: int, stream: int) -> int:
     return load_library().fibar_set_pixel_gain(h, gain_ptr, on_device, stream)
 
 
+def fibar_push_events_many(h, ev_ptrs, ns, on_device: int, stream: int) -> int:
+    n = len(ev_ptrs)
+    return load_library().fibar_push_events_many(h, (C.c_void_p * n)(*ev_ptrs), (C.c_size_t * n)(*ns), n,
+                                                 on_device, stream)
+
+
 def fibar_debug_wait_timeout(h, max_spins: int, stream: int) -> int:
     return load_library().fibar_debug_wait_timeout(h, max_spins, stream)
 
@@ -260,6 +268,22 @@ class Fibar:
             self._keep.append(ev)
         else:
             self._check(fibar_push_events(self.h, ev.data_ptr(), n, 0, self._s))
+
+    def push_many(self, packets) -> None:
+        """Push several packets in one call (``fibar_push_events_many``): all CUDA or all CPU
+        contiguous (n, 2) int64 tensors; packets adjacent in memory go in as one."""
+        t = self.torch
+        if not packets:
+            return
+        cuda = packets[0].is_cuda
+        for ev in packets:
+            if (ev.dtype != t.int64 or ev.dim() != 2 or ev.shape[1] != 2 or not ev.is_contiguous()
+                    or ev.is_cuda != cuda):
+                raise TypeError("packets must be contiguous (n, 2) int64 tensors on one device type")
+        self._check(fibar_push_events_many(self.h, [ev.data_ptr() for ev in packets],
+                                           [ev.shape[0] for ev in packets], 1 if cuda else 0, self._s))
+        if cuda:
+            self._keep.extend(packets)
 
     def _rotate(self):
         self._keep_prev = self._keep

@@ -475,6 +475,26 @@ extern "C" int fibar_push_events(fibar_t *h, const fibar_event_t *ev, size_t n, 
     return FIBAR_OK;
 }
 
+extern "C" int fibar_push_events_many(fibar_t *h, const fibar_event_t *const *evs, const size_t *ns, size_t count,
+                                      int on_device, void *cuda_stream)
+{
+    if (!h) return FIBAR_EINVAL;
+    if (count == 0) return FIBAR_OK;
+    if (!evs || !ns) return fail(h, FIBAR_EINVAL, "push_many: null array");
+    // runs of packets that follow each other in memory go in as one packet
+    size_t i = 0;
+    while (i < count) {
+        const fibar_event_t *p = evs[i];
+        size_t n = ns[i];
+        size_t j = i + 1;
+        while (j < count && p && evs[j] == p + n) n += ns[j++];
+        const int rc = fibar_push_events(h, p, n, on_device, cuda_stream);
+        if (rc != FIBAR_OK) return rc;
+        i = j;
+    }
+    return FIBAR_OK;
+}
+
 namespace {
 
 constexpr unsigned EV_SETS = 4096;  // read-outs whose stage events are kept

@@ -234,3 +234,50 @@ def test_bounded_device_wait_reports_timeout_and_handle_recovers(oracle_mod):
         assert f.stats()["events_applied"] == 4000
     finally:
         f.close()
+
+
+@pytest.mark.parametrize("device", [True, False])
+def test_push_many_equals_single_pushes(device):
+    """fibar_push_events_many (adjacent packets merged into one copy or segment, others kept
+    apart) gives the same images and state as one fibar_push_events per packet."""
+    from paper_2510_20071_gb300 import Fibar
+    W, H = 64, 48
+    ev = eventsim.random_events(W, H, 30_000, seed=17)
+    other = eventsim.random_events(W, H, 30_000, seed=18)  # a second buffer: not adjacent
+    src = (ev.cuda(), other.cuda()) if device else (ev.pin_memory(), other.pin_memory())
+    cuts = [0, 3000, 3001, 9000, 15000, 15000, 22000, 30000]
+    packets = [(0, a, b) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+    # a copy of one packet from the other buffer (same records) breaks adjacency
+    mixed = []
+    for i, (_, a, b) in enumerate(packets):
+        if i == 2:
+            alt = src[1][:b - a]
+            alt.copy_(src[0][a:b])
+            mixed.append(alt)
+        else:
+            mixed.append(src[0][a:b])
+    t_mid, t_end = int(ev[14_999, 1]), int(ev[-1, 1])
+    outs = []
+    for many in (False, True):
+        f = Fibar(W, H, spatial_filter=1, blur_mode=1, q_min=4)
+        if many:
+            f.push_many(mixed[:3])
+            imgs = [f.readout(t_mid).cpu()]
+            f.push_many(mixed[3:])
+        else:
+            for p in mixed[:3]:
+                f.push(p)
+            imgs = [f.readout(t_mid).cpu()]
+            for p in mixed[3:]:
+                f.push(p)
+        imgs.append(f.readout(t_end).cpu())
+        st = f.state()
+        outs.append((imgs, st))
+        f.close()
+    (a_imgs, a_st), (b_imgs, b_st) = outs
+    for x, y in zip(a_imgs, b_imgs):
+        assert torch.equal(x, y)
+    for k in ["k", "h", "q", "q_targ", "n_ap", "n_at"]:
+        assert a_st[k] == b_st[k]
+    np.testing.assert_array_equal(a_st["L"], b_st["L"])
+    np.testing.assert_array_equal(a_st["cnt"], b_st["cnt"])
