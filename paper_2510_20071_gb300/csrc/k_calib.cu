@@ -10,9 +10,9 @@
 // C'_i is the per-pixel factor that Sec. 5.2 applies to the right-hand side of Eq. 6
 // (fibar_set_pixel_gain).
 //
-// Two kernels: per-pixel ON / OFF counts with global atomics (one 16-byte record per
-// thread and iteration, the total per block reduced in shared memory), then one thread
-// per pixel for the three quotients.
+// Two kernels: per-pixel ON / OFF counts with global atomics (four 16-byte records per
+// thread and iteration in flight, the total per block reduced in shared memory), then
+// one thread per pixel for the three quotients.
 #include "fibar_internal.cuh"
 
 namespace fibar {
@@ -27,15 +27,26 @@ __global__ void __launch_bounds__(256) k_calib_count(const int4 *__restrict__ ev
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
     unsigned mine = 0;
-    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        const int4 r = __ldcs(&ev[k]);  // read once: do not keep in L2
+    auto count = [&](const int4 r) {
         const unsigned x = (unsigned)r.x & 0xFFFFu, y = (unsigned)r.x >> 16;
         const int p = (int)(signed char)(r.y & 0xFF);
         if (x < W && y < H) {
             atomicAdd(p > 0 ? &n_on[y * W + x] : &n_off[y * W + x], 1u);
             ++mine;
         }
+    };
+    // four records in flight per thread (read once: not kept in L2)
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    for (; k + 3 * stride < n; k += 4 * stride) {
+        const int4 r0 = __ldcs(&ev[k]), r1 = __ldcs(&ev[k + stride]);
+        const int4 r2 = __ldcs(&ev[k + 2 * stride]), r3 = __ldcs(&ev[k + 3 * stride]);
+        count(r0);
+        count(r1);
+        count(r2);
+        count(r3);
     }
+    for (; k < n; k += stride) count(__ldcs(&ev[k]));
     // block total of the counted records
 #pragma unroll
     for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xFFFFFFFFu, mine, o);
