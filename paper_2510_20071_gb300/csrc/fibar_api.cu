@@ -51,7 +51,7 @@ void free_all(fibar_t *h)
     Bufs &b = h->b;
     void *ptrs[] = {b.ctrl, b.pbar, b.L, b.last_pix, b.last_tile, b.staging, b.carry[0], b.carry[1],
                     b.dec_status, b.rec[0], b.rec[1], b.sort_hist, b.sort_base, b.sort_rows, b.sort_rowflag, b.sort_gtot, b.sort_gflag, b.sort_gcount,
-                    b.qout, b.ring4, b.ring_pix, b.bucket_start, b.bucket_cnt, b.dMt, b.det_base, b.det_prof, b.band_ctr, b.E0, b.E1, b.E2, b.p2_ids, b.merged, b.unm_bits,
+                    b.qout, b.ring4, b.ring_pix, b.bucket_start, b.bucket_cnt, b.bucket_order, b.dMt, b.det_base, b.det_prof, b.band_ctr, b.E0, b.E1, b.E2, b.p2_ids, b.merged, b.unm_bits,
                     b.out_staging, b.dbg_cnt, b.plist, b.plnb, b.epos, b.lbl, b.s1_info, b.s1_linit,
                     b.popk, b.blur_ord, b.bk, b.bpix, b.bj, b.bval, b.sel_status, b.beta_pow};
     for (void *p : ptrs)
@@ -195,6 +195,7 @@ void for_each_buffer(const Layout &lo, Bufs &b, F &&f)
     f(b.out_staging, npix);
     f(b.bucket_start, kp.nbuckets);
     f(b.bucket_cnt, kp.nbuckets);
+    f(b.bucket_order, kp.nbuckets);
     if (lo.p.spatial_filter) {
         f(b.qout, maxp);
         f(b.ring4, R);
@@ -559,7 +560,7 @@ int process(fibar_t *h, unsigned long long t_read, float *out, cudaStream_t s)
     if (e != cudaSuccess) return cuda_fail(h, e, "sort");
     const unsigned long long *sorted = b.rec[h->sort_passes & 1];
     mk.mark(FIBAR_STAGE_WALK);
-    e = launch_walk(kp, b, sorted, s, nl);
+    e = launch_walk(kp, b, sorted, h->sort_passes, s, nl);
     if (e != cudaSuccess) return cuda_fail(h, e, "walk");
     mk.mark(FIBAR_STAGE_DET_COUNTS);
     if (kp.spatial) e = launch_det_counts(kp, b, s, nl);

@@ -144,6 +144,7 @@ struct Bufs {
     unsigned int *ring_pix;
     unsigned int *bucket_start;  // [nbuckets] first sorted position of each bucket
     unsigned int *bucket_cnt;    // [nbuckets] scratch histogram
+    unsigned int *bucket_order;  // [nbuckets] walk order, largest buckets first (one-pass sorts)
     // detector chunk data
     unsigned short *dMt;         // [2][mt_rows][256] band of suffix histograms by target chunk
     unsigned int *det_base;      // [2 builds][2][mt_rows] window counts below the band (zero between batches)
@@ -265,7 +266,7 @@ cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, u
                           unsigned long long &nl);
 cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsigned epoch,
                         cudaStream_t s, unsigned long long &nl);
-cudaError_t launch_walk(const KParams &kp, const Bufs &b, const unsigned long long *sorted,
+cudaError_t launch_walk(const KParams &kp, const Bufs &b, const unsigned long long *sorted, unsigned sort_passes,
                         cudaStream_t s, unsigned long long &nl);
 cudaError_t launch_det_counts(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
 cudaError_t launch_det_pass1(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);

@@ -99,8 +99,9 @@ k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
     for (;;) {
         if (threadIdx.x == 0) S.bucket = atomicAdd(&ctrl->walk_ticket, 1u);
         __syncthreads();
-        const unsigned bk = S.bucket;
-        if (bk >= nbuckets) break;
+        if (S.bucket >= nbuckets) break;
+        // largest buckets first when the decode ordered them (fewer CTAs idle at the end)
+        const unsigned bk = b.bucket_order ? b.bucket_order[S.bucket] : S.bucket;
         const unsigned bs = b.bucket_start[bk];
         const unsigned be = bk + 1 < nbuckets ? b.bucket_start[bk + 1] : m;
         if (bs >= be) {
@@ -318,10 +319,12 @@ static cudaError_t walk_variant(const KParams &kp, const Bufs &b, const unsigned
     return launch_pdl(k_bwalk<kLinks, kS1, kGain>, grid_for(2), BW_THREADS, smem, s, kp, b, sorted);
 }
 
-cudaError_t launch_walk(const KParams &kp, const Bufs &b, const unsigned long long *sorted,
+cudaError_t launch_walk(const KParams &kp, const Bufs &b_in, const unsigned long long *sorted, unsigned sort_passes,
                         cudaStream_t s, unsigned long long &nl)
 {
     nl += 1;
+    Bufs b = b_in;
+    if (sort_passes != 1) b.bucket_order = nullptr;  // only a one-pass sort's decode orders them
     const bool gain = b.gain != nullptr;
     cudaError_t e;
     if (kp.spatial && kp.blur_mode == 0)

@@ -173,6 +173,7 @@ __device__ __forceinline__ unsigned dpad(unsigned r) { return r + r / DEC_PER_TH
 // sort's digit offsets and the walk's bucket starts (otherwise k_sort_hist does).
 struct DecHist {
     unsigned *ghist, *gbase, *bucket_start;  // ghist == nullptr: off
+    unsigned *order;                         // buckets by decreasing size, for the walk
     unsigned nbuckets, lb;
 };
 
@@ -218,8 +219,39 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
         const unsigned ex = block_excl_scan256(v0 + v1, s_warp, &tot);
         dh.gbase[d0] = ex;
         dh.gbase[d0 + 1] = ex + v0;
-        if (d0 < dh.nbuckets) dh.bucket_start[d0] = ex;
-        if (d0 + 1 < dh.nbuckets) dh.bucket_start[d0 + 1] = ex + v0;
+        const bool ok0 = d0 < dh.nbuckets, ok1 = d0 + 1 < dh.nbuckets;
+        if (ok0) dh.bucket_start[d0] = ex;
+        if (ok1) dh.bucket_start[d0 + 1] = ex + v0;
+        // the walk's order: buckets by decreasing size, in 64 size classes (a counting
+        // sort; the order within a class does not matter, the buckets are independent)
+        __syncthreads();
+        if (threadIdx.x < 65) s_hb[threadIdx.x] = 0u;
+        __syncthreads();
+        const unsigned c0 = ok0 ? v0 : 0u, c1 = ok1 ? v1 : 0u;
+        const unsigned wmax = __reduce_max_sync(0xFFFFFFFFu, max(c0, c1));
+        if ((threadIdx.x & 31) == 0) atomicMax(&s_hb[64], wmax);
+        __syncthreads();
+        const unsigned mx = max(1u, s_hb[64]);
+        const unsigned k0 = 63u - (unsigned)((unsigned long long)c0 * 63u / mx);
+        const unsigned k1 = 63u - (unsigned)((unsigned long long)c1 * 63u / mx);
+        if (ok0) atomicAdd(&s_hb[k0], 1u);
+        if (ok1) atomicAdd(&s_hb[k1], 1u);
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const unsigned a = s_hb[2 * threadIdx.x], bb = s_hb[2 * threadIdx.x + 1];
+            unsigned x = a + bb;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (threadIdx.x >= (unsigned)o) x += y;
+            }
+            const unsigned excl = x - a - bb;
+            s_hb[2 * threadIdx.x] = excl;
+            s_hb[2 * threadIdx.x + 1] = excl + a;
+        }
+        __syncthreads();
+        if (ok0) dh.order[atomicAdd(&s_hb[k0], 1u)] = d0;
+        if (ok1) dh.order[atomicAdd(&s_hb[k1], 1u)] = d0 + 1;
     };
     if (hist && ntiles == 0) {
         if (blockIdx.x == 0) hist_finish();
@@ -699,11 +731,12 @@ cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, u
         if (cudaError_t e = cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) return e;
         attr_set = true;
     }
-    DecHist dh{nullptr, nullptr, nullptr, kp.nbuckets, kp.lb};
+    DecHist dh{nullptr, nullptr, nullptr, nullptr, kp.nbuckets, kp.lb};
     if (sort_passes == 1) {
         dh.ghist = b.sort_hist;
         dh.gbase = b.sort_base;
         dh.bucket_start = b.bucket_start;
+        dh.order = b.bucket_order;
     }
     if (cudaError_t e_ = launch_pdl(k_decode, grid_for(DEC_BLOCKS_PER_SM), DEC_THREADS, smem, s, kp, t, b.ctrl, b.dec_status, b.rec[0],
                                     kp.spatial ? b.ring_pix : nullptr, dh)) return e_;
