@@ -170,7 +170,8 @@ __device__ __forceinline__ long long chunk_of(long long x, unsigned S, unsigned 
 // 32 words, so that a lane's run of 32 bins and the diagonal reads both spread over the
 // banks), suffix sums in registers, then per target the sum of its distances below the
 // band and, per target row, a run of HB_CHUNKS consecutive band distances.
-constexpr int HB_CHUNKS = 16;
+constexpr int HB_CHUNKS = 12;
+constexpr int HB_BLOCKS_PER_SM = 3;  // resident table-build blocks per SM (shared memory)
 constexpr int HB_PITCH = 674;   // >= HB_BINS + HB_BINS / 32 words with padding, = 2 (mod 32)
 constexpr int MT_PITCH = DET_BAND;  // u16 per target row (512 B: 16-byte aligned rows)
 
@@ -306,7 +307,7 @@ k_det_hist(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned short *Mt, size_t
         }
         if (kBuild == 0 && ns > 0) {
             // columns of the sampled targets sstep * s within reach of the sources:
-            // prof[t][s][d] = M(sstep * s, d), d in 1..639 (16 threads write the 16
+            // prof[t][s][d] = M(sstep * s, d), d in 1..639 (HB_CHUNKS threads write the
             // consecutive distances one sample takes from the block's sources)
             const int t_lo = (int)c_lo + 1, t_hi = (int)c_lo + HB_CHUNKS - 1 + (HB_BINS - 1);
             const int st = (int)sstep;
@@ -1178,13 +1179,13 @@ cudaError_t launch_det_counts(const KParams &kp, const Bufs &b, cudaStream_t s, 
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (cudaError_t e_ = launch_pdl(k_det_hist<0>, grid_for(2), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
+    if (cudaError_t e_ = launch_pdl(k_det_hist<0>, grid_for(HB_BLOCKS_PER_SM), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
                                     b.det_base, b.det_prof, b.n_samples, (const unsigned short *)b.band_ctr))
         return e_;
     if (cudaError_t e_ = launch_pdl(k_det_center, grid_for(2), 256, 0, s, kp, b.ctrl, (const unsigned short *)b.det_prof,
                                     b.n_samples, b.band_ctr))
         return e_;
-    if (cudaError_t e_ = launch_pdl(k_det_hist<1>, grid_for(2), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
+    if (cudaError_t e_ = launch_pdl(k_det_hist<1>, grid_for(HB_BLOCKS_PER_SM), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
                                     b.det_base, b.det_prof, b.n_samples, (const unsigned short *)b.band_ctr))
         return e_;
     if (cudaError_t e_ = launch_pdl(k_det_init, grid_for(8), 256, 0, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
