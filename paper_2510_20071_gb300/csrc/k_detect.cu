@@ -902,16 +902,20 @@ __device__ bool lane_run(const KParams &kp, unsigned long long base, const uint4
                 }
                 __syncwarp();
             }
-            // the lane's own pops, links from its ring, two per iteration (from global
+            // the lane's own pops, links from its ring, four per iteration (from global
             // memory past the landed entries: rare, a separate loop)
             if (!__any_sync(0xFFFFFFFFu, h + (int)P > v)) {
                 const unsigned hu = (unsigned)h, kh = k - hu;  // k - e = kh - u for e = h + u
-                for (unsigned u = 0; u < P; u += 2) {
+                for (unsigned u = 0; u < P; u += 4) {
+                    // four pops per iteration: the four ring loads in flight together
                     const uint2 n0 = rg[(hu + u) & (LR_R - 1)];
                     const uint2 n1 = rg[(hu + u + 1) & (LR_R - 1)];
-                    const bool two = u + 1 < P;
-                    nap -= (n0.x > kh - u) + (two && n1.x > kh - u - 1);
-                    nat -= (n0.y > kh - u) + (two && n1.y > kh - u - 1);
+                    const uint2 n2 = rg[(hu + u + 2) & (LR_R - 1)];
+                    const uint2 n3 = rg[(hu + u + 3) & (LR_R - 1)];
+                    const unsigned r = P - u;  // pops left (>= 1)
+                    const unsigned d0 = kh - u;
+                    nap -= (n0.x > d0) + (r > 1 && n1.x > d0 - 1) + (r > 2 && n2.x > d0 - 2) + (r > 3 && n3.x > d0 - 3);
+                    nat -= (n0.y > d0) + (r > 1 && n1.y > d0 - 1) + (r > 2 && n2.y > d0 - 2) + (r > 3 && n3.y > d0 - 3);
                 }
                 h += (int)P;
             } else {
