@@ -47,6 +47,20 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def whole_job(ms: float, events: float, world: int, device: str = "cuda"):
+    """(max time over ranks in ms, events summed over ranks, whole-job Mevents/s): each
+    rank times its own replica; the job takes as long as the slowest one."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, events], dtype=torch.float64, device=device)
+    ms_t, ev_t = t[0:1].clone(), t[1:2].clone()
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(ev_t, op=dist.ReduceOp.SUM)
+    ms_max, total = float(ms_t.item()), float(ev_t.item())
+    return ms_max, total, total / (ms_max / 1e3) / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -225,13 +239,7 @@ def run_batch(args, rank, world, local):
     if applied != expect:
         raise RuntimeError(f"timed region applied {applied} events, expected {expect}")
 
-    ms_all = torch.tensor([ms], device="cuda")
-    ev_all = torch.tensor([float(applied)], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_all, op=dist.ReduceOp.MAX)
-        dist.all_reduce(ev_all, op=dist.ReduceOp.SUM)
-    ms_max = float(ms_all.item())
-    value = float(ev_all.item()) / (ms_max / 1e3) / 1e6
+    ms_max, _, value = whole_job(ms, float(applied), world)
     peak, peak_kind = load_peaks()
     px = sum(s["W"] * s["H"] for s in streams)
     img_bytes = 8.0 * sum(s["W"] * s["H"] * len([r for r in served if r.sid == sids[i]])
@@ -305,12 +313,9 @@ def run_calib(args, rank, world, local):
     ms = e0.elapsed_time(e1)
     time.sleep(0.3)
     clocks = sampler.stop()
-    ms_all = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_all, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_all.item())
+    ms_max, total, _ = whole_job(ms, float(n_ev) * args.steps, world)
     per = ms_max / args.steps
-    value = world * n_ev / (per / 1e3) / 1e6
+    value = total / args.steps / (per / 1e3) / 1e6
     # e2e: pinned host events through the host path of the same call
     pinned = ev.pin_memory()
     n_e2e = max(1, min(args.steps, 5))
@@ -458,14 +463,7 @@ def main():
     f.set_timing(False)
     stage_pass_ms = s0.elapsed_time(s1) / max(n_stage, 1)
 
-    ms_all = torch.tensor([ms], device="cuda")
-    ev_all = torch.tensor([float(applied)], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_all, op=dist.ReduceOp.MAX)
-        dist.all_reduce(ev_all, op=dist.ReduceOp.SUM)
-    ms_max = float(ms_all.item())
-    total_events = float(ev_all.item())
-    value = total_events / (ms_max / 1e3) / 1e6  # Mevents/s, whole job
+    ms_max, total_events, value = whole_job(ms, float(applied), world)  # Mevents/s, whole job
 
     # roofline of the dominant kernel stage, from its CUDA-event time in the stage pass
     peak, peak_kind = load_peaks()
