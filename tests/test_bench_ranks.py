@@ -31,7 +31,7 @@ def _rank(rank, world, port, out):
 
 def test_whole_job_is_max_time_and_summed_events():
     world, port = 2, _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork: the parent may hold threads
         out = m.dict()
         mp.start_processes(_rank, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
         got = dict(out)
