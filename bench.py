@@ -38,8 +38,7 @@ METRIC = "events/s (M/s) on 1 GB300, % of HBM roofline; p50/p99 read-out latency
 UNIT = "Mevents/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) per launch of the stage's kernel, from one ncu capture of the
-# current kernel on this workload (profiles/pipeline_perlin_1280x720_1M.md); a stage
-# missing here has no capture of its current code.
+# current kernel on this workload; a stage missing here has no capture of its current code.
 DRAM_TRAFFIC = {"det_pass1": 16.99e6, "walk": None, "decode": None, "det_counts": None}  # None: changed since the capture
 
 

@@ -238,22 +238,23 @@ int fibar_flush(fibar_t *h, void *cuda_stream);
 /* Synchronise and copy the state (see fibar_state_view_t). */
 int fibar_debug_state(fibar_t *h, fibar_state_view_t *v, void *cuda_stream);
 
-/* The number of queued events of every pixel (the per-pixel counter of Sec. 5.4 whose
- * return to zero makes the pixel stale), written to cnt[W*H] in row-major order: device
- * memory when on_device is non-zero (asynchronous on cuda_stream), else host memory
- * (returns after the copy).  The same values as fibar_debug_state's cnt, computed
- * without allocating any memory: the paper has no counterpart; this exists for callers
- * that must not allocate device memory once they run (a process sharing the GPU under a
- * fixed memory budget, where an allocation can fail, or a latency-bound loop that cannot
- * afford the implicit device synchronisation an allocation may cause).
- * fibar_debug_state allocates its counter buffer on first use; this call counts into a
- * fixed buffer of 1,048,576 32-bit counters (4 MiB) built into the library, one per
- * device, cleared by every call before it counts.
+/* The number of queued events of every pixel (the per-pixel queued-event count that
+ * fibar_debug_state reports as cnt; a pixel whose count is zero after it had an event is
+ * stale), written to cnt[W*H] in row-major order: device memory when on_device is
+ * non-zero (asynchronous on cuda_stream), else host memory (returns after the copy).
+ * The paper has no counterpart; this exists for callers that must not allocate device
+ * memory once they run (a process sharing the GPU under a fixed memory budget, where an
+ * allocation can fail, or a latency-bound loop that cannot afford the implicit device
+ * synchronisation an allocation may cause).  fibar_debug_state allocates its counter
+ * buffer on first use; this call counts into a fixed buffer of 1,048,576 32-bit counters
+ * (4 MiB) built into the library, one per device, cleared by every call before it counts.
  * Errors: EINVAL (h or cnt NULL, W*H > 1,048,576, or the handle's device not current),
- * ECUDA.  The first call on a device looks up that buffer's address; make it before any
- * stream capture.  Calls that overlap in time on other streams or threads, with this or
- * another handle on the same device, share the buffer and race; calls on one stream are
- * ordered. */
+ * ECUDA, and, with host output only, ETIMEOUT when a bounded device wait of the pipeline
+ * gave up (with device output, fibar_stats reports that flag).  Every call looks up the
+ * buffer's device address (no allocation); the first call in a process may load the
+ * library's device code, so make it before any stream capture.  Calls that overlap in
+ * time on other streams or threads, with this or another handle on the same device,
+ * share the buffer and race; calls on one stream are ordered. */
 int fibar_queue_counts_noalloc(fibar_t *h, uint32_t *cnt, int on_device, void *cuda_stream);
 
 /* Failure-detection check (no counterpart in the paper): runs, on the device, the bounded

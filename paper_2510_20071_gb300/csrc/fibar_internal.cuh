@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <utility>
 #include <vector>
@@ -256,6 +257,30 @@ __device__ __forceinline__ unsigned warp_peers(unsigned v)
         peers &= bit ? bal : ~bal;
     }
     return peers;
+}
+
+// One-time set-up per device, safe under concurrent callers: `done` holds one bit per
+// device ordinal (< 64) whose set-up succeeded; devices beyond 63 redo it every call.
+// Two threads may both run `setup` for the same device; it must be idempotent.
+template <class F>
+inline cudaError_t once_per_device(std::atomic<unsigned long long> &done, F &&setup)
+{
+    int dev = 0;
+    if (cudaError_t e = cudaGetDevice(&dev)) return e;
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    const cudaError_t e = setup();
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
+
+// Raise a kernel's dynamic shared memory limit once per device.
+template <typename... KArgs>
+inline cudaError_t smem_attr_once(std::atomic<unsigned long long> &done, void (*kern)(KArgs...), size_t smem)
+{
+    return once_per_device(done, [&] {
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
 }
 
 // launchers (kernels live in their own translation units); `nl` counts kernel launches

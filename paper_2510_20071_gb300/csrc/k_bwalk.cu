@@ -308,14 +308,9 @@ size_t bwalk_smem() { return sizeof(BwSmem); }
 template <bool kLinks, bool kS1, bool kGain>
 static cudaError_t walk_variant(const KParams &kp, const Bufs &b, const unsigned long long *sorted, cudaStream_t s)
 {
-    static bool attr_set = false;
+    static std::atomic<unsigned long long> attr_done{0};
     const size_t smem = sizeof(BwSmem);
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_bwalk<kLinks, kS1, kGain>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    if (cudaError_t e = smem_attr_once(attr_done, k_bwalk<kLinks, kS1, kGain>, smem)) return e;
     return launch_pdl(k_bwalk<kLinks, kS1, kGain>, grid_for(2), BW_THREADS, smem, s, kp, b, sorted);
 }
 

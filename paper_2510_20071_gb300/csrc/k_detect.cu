@@ -1175,14 +1175,10 @@ __global__ void k_det_fix(KParams kp, Ctrl *ctrl, const uint4 *ring, unsigned *q
 cudaError_t launch_det_counts(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)
 {
     nl += 4;
-    static bool attr_set = false;
+    static std::atomic<unsigned long long> attr_done0{0}, attr_done1{0};
     const size_t smem = sizeof(HistSmem);
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_det_hist<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_det_hist<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    if (cudaError_t e = smem_attr_once(attr_done0, k_det_hist<0>, smem)) return e;
+    if (cudaError_t e = smem_attr_once(attr_done1, k_det_hist<1>, smem)) return e;
     if (cudaError_t e_ = launch_pdl(k_det_hist<0>, grid_for(HB_BLOCKS_PER_SM), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
                                     b.det_base, b.det_prof, b.n_samples, (const unsigned short *)b.band_ctr))
         return e_;
@@ -1200,13 +1196,10 @@ cudaError_t launch_det_counts(const KParams &kp, const Bufs &b, cudaStream_t s, 
 
 static cudaError_t lane_smem_attr()
 {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    const int smem = (int)(sizeof(LaneSmem) * LR_WARPS);
-    cudaError_t e = cudaFuncSetAttribute(k_det_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_det_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) done = true;
-    return e;
+    static std::atomic<unsigned long long> done1{0}, done2{0};
+    const size_t smem = sizeof(LaneSmem) * LR_WARPS;
+    if (cudaError_t e = smem_attr_once(done1, k_det_pass1, smem)) return e;
+    return smem_attr_once(done2, k_det_pass2, smem);
 }
 
 cudaError_t launch_det_pass1(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)

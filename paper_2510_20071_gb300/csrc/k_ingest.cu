@@ -708,29 +708,29 @@ k_sort_pass(Ctrl *ctrl, const unsigned long long *in, unsigned long long *out, u
     }
 }
 
-static int g_sms = 0;
+// SM count of each device (0: not looked up yet), for grid sizes in whole waves
+static std::atomic<int> g_sms[64];
 
 int grid_for(int mult)
 {
-    if (!g_sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_sms <= 0) g_sms = 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int n = dev >= 0 && dev < 64 ? g_sms[dev].load(std::memory_order_relaxed) : 0;
+    if (n <= 0) {
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+        if (dev >= 0 && dev < 64) g_sms[dev].store(n, std::memory_order_relaxed);
     }
-    return g_sms * mult;
+    return n * mult;
 }
 
 cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, unsigned sort_passes,
                           cudaStream_t s, unsigned long long &nl)
 {
     nl += 1;
-    static bool attr_set = false;
+    static std::atomic<unsigned long long> attr_done{0};
     const int smem = DEC_TILE * (int)sizeof(int4);
-    if (!attr_set) {
-        if (cudaError_t e = cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) return e;
-        attr_set = true;
-    }
+    if (cudaError_t e = smem_attr_once(attr_done, k_decode, (size_t)smem)) return e;
     DecHist dh{nullptr, nullptr, nullptr, nullptr, kp.nbuckets, kp.lb};
     if (sort_passes == 1) {
         dh.ghist = b.sort_hist;
@@ -747,14 +747,9 @@ cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsig
                         cudaStream_t s, unsigned long long &nl)
 {
     nl += (passes == 1 ? 0 : 1) + passes;  // one pass: the decode counted the digits
-    static bool attr_set = false;
+    static std::atomic<unsigned long long> attr_done{0};
     const size_t smem = sizeof(SortSmem);
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    if (cudaError_t e = smem_attr_once(attr_done, k_sort_pass, smem)) return e;
     const unsigned bucket_bits = kp.key_bits - kp.lb;
     const unsigned dbits = passes ? (bucket_bits + passes - 1) / passes : 1u;
     if (passes != 1)

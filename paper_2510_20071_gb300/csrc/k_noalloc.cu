@@ -6,15 +6,17 @@
 // __device__ array of NOALLOC_MAX_PIXELS 32-bit counters, 4 MiB), so a caller that must
 // not allocate device memory once it is running can still read the counts.
 //
-// Set-up: the first call on a device looks up the buffer's device address with
-// cudaGetSymbolAddress while that device is current, and keeps it for later calls; make
-// that first call before any stream capture.
+// Set-up: every call looks up the buffer's device address with cudaGetSymbolAddress
+// while the handle's device is current (this allocates nothing).  The first lookup in a
+// process may load the library's device code on that device; make the first call before
+// any stream capture.  Looking the address up again on each call keeps it valid after a
+// context has been torn down and re-created (the module then reloads at a new address).
 // Zeroing: the counters must start at zero; every call clears the first W*H of them on
 // its stream before counting.
 // Sharing: the buffer is one per device for the whole process.  Calls that overlap in
 // time (other streams, other threads, other handles on the same device) race on it and
 // may return wrong counts; calls issued on one stream are ordered and safe.
-#include <mutex>
+#include <stdio.h>
 
 #include "fibar_internal.cuh"
 
@@ -22,24 +24,15 @@ namespace fibar {
 namespace {
 
 constexpr size_t NOALLOC_MAX_PIXELS = size_t(1) << 20;  // 4 MiB of counters
-constexpr int NOALLOC_MAX_DEVICES = 64;
-
 static __device__ __align__(256) unsigned g_count_scratch[NOALLOC_MAX_PIXELS];
 
-std::mutex g_setup_mutex;
-unsigned *g_scratch_ptr[NOALLOC_MAX_DEVICES] = {};
-
-// Device address of the scratch array on `device`, which must be current.
-cudaError_t scratch_for(int device, unsigned **ptr)
+// Device address of the scratch array on the current device.
+cudaError_t scratch_address(unsigned **ptr)
 {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[device]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_count_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[device] = static_cast<unsigned *>(p);
-    }
-    *ptr = g_scratch_ptr[device];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_count_scratch);
+    if (e != cudaSuccess) return e;
+    *ptr = static_cast<unsigned *>(p);
     return cudaSuccess;
 }
 
@@ -76,10 +69,10 @@ extern "C" int fibar_queue_counts_noalloc(fibar_t *h, uint32_t *cnt, int on_devi
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail_msg(h, FIBAR_ECUDA, std::string("fibar_queue_counts_noalloc: ") + cudaGetErrorString(e));
-    if (dev != h->device || dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+    if (dev != h->device)
         return fail_msg(h, FIBAR_EINVAL, "fibar_queue_counts_noalloc: the handle's device must be current");
     unsigned *scratch = nullptr;
-    e = scratch_for(dev, &scratch);
+    e = scratch_address(&scratch);
     if (e != cudaSuccess)
         return fail_msg(h, FIBAR_ECUDA, std::string("fibar_queue_counts_noalloc set-up: ") + cudaGetErrorString(e));
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -92,7 +85,18 @@ extern "C" int fibar_queue_counts_noalloc(fibar_t *h, uint32_t *cnt, int on_devi
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(cnt, scratch, npix * sizeof(unsigned),
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    // host output: after the synchronisation, the pipeline's error word says whether a
+    // bounded device wait gave up (the queue window may then be inconsistent); it is
+    // read into a stack variable, which allocates nothing
+    unsigned err = 0;
+    if (e == cudaSuccess && !on_device)
+        e = cudaMemcpyAsync(&err, &h->b.ctrl->error, sizeof(err), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail_msg(h, FIBAR_ECUDA, std::string("fibar_queue_counts_noalloc: ") + cudaGetErrorString(e));
+    if (err) {
+        char msg[96];
+        snprintf(msg, sizeof msg, "fibar_queue_counts_noalloc: a bounded device wait gave up (flags 0x%x)", err);
+        return fail_msg(h, FIBAR_ETIMEOUT, msg);
+    }
     return FIBAR_OK;
 }
