@@ -42,6 +42,16 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 DRAM_TRAFFIC = {"det_pass1": 16.99e6, "walk": None, "decode": None, "det_counts": None}  # None: changed since the capture
 
 
+MODE_PARAMS = {"s2": dict(spatial_filter=1, blur_mode=1), "s1": dict(spatial_filter=1, blur_mode=0),
+               "nsf": dict(spatial_filter=0)}
+MODE_NAMES = {"s2": "S2 masked-blur read-out", "s1": "S1 in-place blur (paper)", "nsf": "NSF (no spatial filter)"}
+WORKLOAD = ("1280x720 rotating+zooming Perlin, 2% noise events, C=0.2, seed 1, 65,536-event device packets, "
+            "read-out every 1,000,000 events")
+PARITY_READOUTS = 20    # timed read-outs whose images are kept and compared with the oracle
+PARITY_TOL = 1e-4       # absolute, per pixel, log brightness (C = 0.2)
+ORACLE_SECONDS = 60.0   # bound on the oracle's replay of the warm-up and timed steps
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -400,13 +410,7 @@ def main():
     torch.cuda.synchronize()
     log(f"[rank {rank}] simulated {ev.shape[0]} events in {time.time() - t0:.1f} s")
 
-    params = dict(c_on=0.2, c_off=0.2)
-    if args.mode == "s2":
-        params.update(spatial_filter=1, blur_mode=1)
-    elif args.mode == "s1":
-        params.update(spatial_filter=1, blur_mode=0)
-    else:
-        params.update(spatial_filter=0)
+    params = dict(c_on=0.2, c_off=0.2, **MODE_PARAMS[args.mode])
     stream = torch.cuda.current_stream()
     f = Fibar(W, H, stream=stream, **params)
     plan = step_plan(n_total, ev[:, 1].cpu())
@@ -427,8 +431,14 @@ def main():
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    # the first PARITY_READOUTS timed steps write their images to buffers of their own
+    # (checked against the oracle after the run); the others reuse one buffer
+    n_cmp = min(len(timed), PARITY_READOUTS)
+    cmp_out = [torch.empty((H, W), dtype=torch.float32, device=ev.device) for _ in range(n_cmp)]
+    torch.cuda.synchronize()
     e0.record(stream)
-    run_steps(f, ev, timed, out)
+    for i, step in enumerate(timed):
+        run_steps(f, ev, [step], cmp_out[i] if i < n_cmp else out)
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -439,6 +449,9 @@ def main():
     st = f.stats()
     applied = st["events_applied"] - applied0
     launches = st["kernel_launches"] - launches0
+    gpu_state = f.state()  # after the last timed step, for the oracle check
+    gpu_imgs = [o.cpu().numpy() for o in cmp_out]
+    del cmp_out
 
     # read-out latency: one step per event pair (all of a step's work runs in its read-out)
     lat = []
@@ -497,10 +510,8 @@ def main():
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded contrast-threshold simulator)",
-        "config": {"workload": "1280x720 rotating+zooming Perlin, 2% noise events, C=0.2, seed 1, "
-                               "65,536-event device packets, read-out every 1,000,000 events",
-                   "mode": {"s2": "S2 masked-blur read-out", "s1": "S1 in-place blur (paper)",
-                            "nsf": "NSF (no spatial filter)"}[args.mode],
+        "config": {"workload": WORKLOAD,
+                   "mode": MODE_NAMES[args.mode],
                    "stream_events": int(ev.shape[0]), "events_per_step": int(per_step_events),
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2: each step reads a fresh 16 MB slice of the 3.2 GB stream"},
@@ -525,7 +536,8 @@ def main():
     if not args.no_e2e:
         result["e2e"] = run_e2e(args, ev, plan[:w1], params, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = run_cpu_baseline(ev, params)
+        result["cpu_baseline"], result["parity"] = run_cpu_baseline(ev, params, plan, w0, timed, gpu_imgs,
+                                                                    gpu_state)
     f.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -550,6 +562,7 @@ def run_e2e(args, ev, plan, params, torch):
             f.push(warm[lo:hi])
         f.readout(t, out)
     torch.cuda.synchronize()
+    applied0 = f.stats()["events_applied"]
     t0 = time.perf_counter()
     for pk, t in plan[args.warmup:]:
         # the step's packets in one call (adjacent packets: one host-to-device copy)
@@ -557,79 +570,116 @@ def run_e2e(args, ev, plan, params, torch):
         f.readout(t, out)  # host image: waits for the result
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    st = f.stats()
+    applied = f.stats()["events_applied"] - applied0
     f.close()
     steps = len(plan) - args.warmup
     n = sum(hi - lo for pk, _ in plan[args.warmup:] for lo, hi in pk)
-    applied = n  # every pushed event of the timed steps is applied by its read-out or the next
     return {"value": round(applied / dt / 1e6, 3), "unit": UNIT,
             "h2d_bytes_per_step": int(16 * n / steps), "d2h_bytes_per_step": int(4 * W * H),
             "ms_per_step": round(dt * 1e3 / steps, 4)}
 
 
-def run_cpu_baseline(ev, params, seconds: float = 15.0):
-    """The FP64 oracle, single-threaded, on a bounded prefix of the same stream."""
+def run_cpu_baseline(ev, params, plan, w0, timed, gpu_imgs, gpu_state):
+    """The FP64 oracle, single-threaded, replaying the GPU run's own packets and read-outs:
+    the warm-up steps, then the timed steps (bounded by ORACLE_SECONDS).  Its throughput is
+    the CPU baseline; its images of the first timed read-outs and its state after the last
+    timed step are compared with the GPU's (images within PARITY_TOL, integer state
+    bit-exact)."""
+    import numpy as np
     import oracle
     oracle.build()
     o = oracle.Oracle(W, H, **params)
-    cpu = ev[: 40 * READ_EVERY].cpu()
-    t_col = cpu[:, 1]
-    t0 = time.perf_counter()
-    done = 0
-    while done < cpu.shape[0] and time.perf_counter() - t0 < seconds:
-        o.push(cpu[done:done + READ_EVERY])
-        o.readout(int(t_col[done + READ_EVERY - 1]))
-        done += READ_EVERY
-    dt = time.perf_counter() - t0
-    return {"value": round(done / dt / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {done // READ_EVERY} read-out intervals ({done} events) of the same stream, "
-                      f"FP64 event-by-event, one thread"}
+    n_steps = w0 + len(timed)
+    hi_all = plan[n_steps - 1][0][-1][1]
+    cpu = ev[:hi_all].cpu()
+    busy, worst, compared, reached = 0.0, 0.0, 0, 0
+    for s_i, (pk, t) in enumerate(plan[:n_steps]):
+        t0 = time.perf_counter()
+        for lo, hi in pk:
+            o.push(cpu[lo:hi])
+        img = o.readout(t)
+        busy += time.perf_counter() - t0
+        reached = s_i + 1
+        j = s_i - w0
+        if 0 <= j < len(gpu_imgs):
+            worst = max(worst, float(np.abs(img - gpu_imgs[j].astype(np.float64)).max()))
+            compared += 1
+        if busy > ORACLE_SECONDS and j >= len(gpu_imgs) - 1:
+            break
+    ost = o.state()
+    applied = ost["k"]
+    int_equal = None
+    state_err = None
+    if reached == n_steps:
+        keys = ["k", "h", "q", "q_targ", "n_ap", "n_at"] if params.get("spatial_filter", 1) else ["k"]
+        int_equal = all(int(gpu_state[k]) == int(ost[k]) for k in keys)
+        int_equal = int_equal and bool(np.array_equal(gpu_state["last_idx"], ost["last"].astype(np.uint64)))
+        if params.get("spatial_filter", 1):
+            int_equal = int_equal and bool(np.array_equal(gpu_state["cnt"], ost["cnt"]))
+        state_err = max(float(np.abs(gpu_state["L"] - ost["L"]).max()),
+                        float(np.abs(gpu_state["pbar"] - ost["pbar"]).max()))
+    o.close()
+    ok = compared == len(gpu_imgs) and worst <= PARITY_TOL and int_equal is not False and \
+        (state_err is None or state_err <= PARITY_TOL)
+    baseline = {"value": round(applied / busy / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"the run's first {reached} read-out intervals ({applied} events: {w0} warm-up and "
+                          f"{reached - w0} timed steps) with the same packets and read-out times, FP64 "
+                          f"event-by-event, one thread"}
+    parity = {"read_outs": compared, "timed_steps_compared": [0, compared], "max_abs_err": worst,
+              "tol": PARITY_TOL, "int_state_equal": int_equal,
+              "state_after_step": n_steps if reached == n_steps else None,
+              "state_max_abs_err": state_err, "pass": bool(ok),
+              "what": "GPU images of the first timed read-outs and the GPU state after the last timed step "
+                      "against the FP64 oracle replaying the same packets (k, h, q, q_targ, N_ap, N_at, "
+                      "per-pixel queued counts and last event index bit-exact; images, L, p_bar within tol)"}
+    return baseline, parity
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 oracle on the host cores, same config / metric / unit."""
+    """Reference arm: the FP64 oracle on the host cores, same workload / metric / unit and
+    mode.  Each step pushes a bounded sample of the stream (the whole read-out interval
+    of 1,000,000 events when K <= 20, else 20/K of it) as 65,536-event packets and reads
+    out at its last time stamp."""
     if rank != 0:
         return 0
     import torch
     import oracle
     import eventsim
     oracle.build()
-    mode_params = dict(spatial_filter=1, blur_mode=1) if args.mode == "s2" else dict(spatial_filter=0)
+    mode_params = MODE_PARAMS[args.mode]
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    n = (args.warmup + args.steps) * READ_EVERY
-    # bounded: at most 40 read-out intervals of the stream are simulated for this arm
-    n_sim = min(n, 40 * READ_EVERY)
+    per_step = max(1, min(READ_EVERY, int(READ_EVERY * 20 / max(args.steps, 1))))
+    n = (args.warmup + args.steps) * per_step
     cfg = dict(eventsim.CONFIGS[CONFIG_NAME])
-    cfg["n_events"] = STREAM_EVENTS
-    if dev == "cpu":
-        cfg["n_events"] = n_sim
-    ev = eventsim.simulate(cfg.pop("W"), cfg.pop("H"), cfg.pop("n_events"), device=dev, **cfg)[:n_sim].cpu()
+    cfg["n_events"] = STREAM_EVENTS if dev == "cuda" else n
+    ev = eventsim.simulate(cfg.pop("W"), cfg.pop("H"), cfg.pop("n_events"), device=dev, **cfg)[:n].cpu()
     t_col = ev[:, 1]
     o = oracle.Oracle(W, H, c_on=0.2, c_off=0.2, **mode_params)
-    per_step = max(1, min(READ_EVERY, int(READ_EVERY * 20 / max(args.steps, 1))))
-    pos = 0
-    for s in range(args.warmup):
-        o.push(ev[pos:pos + per_step]); o.readout(int(t_col[pos + per_step - 1])); pos += per_step
-    t0 = time.perf_counter()
-    done = 0
-    for s in range(args.steps):
-        if pos + per_step > ev.shape[0]:
-            pos = 0
-            o = oracle.Oracle(W, H, c_on=0.2, c_off=0.2, **mode_params)
-        o.push(ev[pos:pos + per_step])
+
+    def step(pos):
+        for lo in range(pos, pos + per_step, PACKET):
+            o.push(ev[lo:min(lo + PACKET, pos + per_step)])
         o.readout(int(t_col[pos + per_step - 1]))
+
+    pos = 0
+    for _ in range(args.warmup):
+        step(pos)
         pos += per_step
-        done += per_step
+    t0 = time.perf_counter()
+    applied0 = o.state()["k"]
+    for _ in range(args.steps):
+        step(pos)
+        pos += per_step
     dt = time.perf_counter() - t0
+    done = o.state()["k"] - applied0
     value = done / dt / 1e6
     res = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded simulator)",
-           "impl": "reference",
-           "config": {"workload": "1280x720 rotating+zooming Perlin, 2% noise events, C=0.2, seed 1, "
-                                  "read-out every step", "events_per_step": per_step},
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded contrast-threshold simulator)", "impl": "reference",
+           "config": {"workload": WORKLOAD, "mode": MODE_NAMES[args.mode], "events_per_step": per_step},
            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{per_step} events per step of the same stream"},
+                            "sample": f"{per_step} events per step of the same stream, FP64, one thread"},
            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res), flush=True)
     return 0
