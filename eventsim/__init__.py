@@ -357,6 +357,24 @@ def random_events(W: int, H: int, n: int, seed: int, *, t_step_us: int = 1,
                        torch.from_numpy(p), torch.from_numpy(t))
 
 
+def hot_pixel_events(W: int, H: int, n: int, seed: int, *, hot: list[tuple[int, int]],
+                     hot_frac: float = 0.9, t_step_us: int = 1) -> torch.Tensor:
+    """A stream dominated by a few flickering ("hot") pixels: each event is, with
+    probability ``hot_frac``, on one of the ``hot`` (x, y) pixels (uniformly), else on a
+    uniform random pixel; random polarity; time stamps increase by ``t_step_us``.  Hot
+    pixels are a common defect of event sensors; here they give one pixel or one tile
+    very long event chains."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    hp = np.asarray([y * W + x for x, y in hot], dtype=np.int64)
+    pix = rng.integers(0, W * H, size=n, dtype=np.int64)
+    on_hot = rng.random(n) < hot_frac
+    pix[on_hot] = hp[rng.integers(0, len(hp), size=int(on_hot.sum()))]
+    p = np.where(rng.random(n) < 0.5, 1, -1).astype(np.int64)
+    t = np.arange(n, dtype=np.int64) * t_step_us
+    return pack_events(torch.from_numpy(pix % W), torch.from_numpy(pix // W),
+                       torch.from_numpy(p), torch.from_numpy(t))
+
+
 # batched serving: many streams of mixed sensors ------------------------------------
 
 SERVING_SENSORS = [(240, 180), (346, 260), (640, 480), (1280, 720)]

@@ -67,7 +67,13 @@ typedef struct {
                                 1 = "S2": never modify L; at read-out, output the 3x3 blur
                                    of L at stale pixels (had an event, none queued) and L
                                    elsewhere                                              */
-    int32_t chain_policy;    /* reserved (0)                                              */
+    int32_t chain_policy;    /* schedule of the temporal filter (same results up to FP32
+                                rounding; the paper runs it event by event):
+                                0 = auto: per piece of <= 2048 events of 512 tiles, the scan
+                                    when one tile has more than 64 events in it, else the walk;
+                                1 = walk: one thread per 2x2 tile, events in arrival order;
+                                2 = scan: segmented scan of the per-event affine maps of
+                                    Eqs. 7, 6, 10 along each pixel's events               */
     uint32_t max_pending;    /* capacity, in events, of pushed-but-unapplied events and of
                                 one processing batch; 0 = 8 Mi events                     */
 } fibar_params_t;
@@ -93,6 +99,9 @@ typedef struct {
     uint64_t detector_big_pops;    /* detector steps whose many pops a whole warp counted  */
     uint64_t detector_ring_misses; /* popped-event links read past the staged ring         */
     uint64_t detector_recenters;   /* batches whose window bands were rebuilt from samples */
+    uint64_t iir_walk_pieces;      /* pieces (<= 2048 events of one bucket of 512 tiles) whose
+                                      temporal filter ran as a walk per tile (cumulative)   */
+    uint64_t iir_scan_pieces;      /* pieces whose temporal filter ran as a segmented scan  */
 } fibar_stats_t;
 
 /* Stages of one read-out, in launch order (fibar_stage_times). */

@@ -50,7 +50,8 @@ class FibarStats(C.Structure):
                                           "n_at", "detector_fixups", "kernel_launches",
                                           "detector_unmerged", "detector_pass2_steps",
                                           "detector_fix_steps", "s1_blurs", "detector_big_pops",
-                                          "detector_ring_misses", "detector_recenters"]]
+                                          "detector_ring_misses", "detector_recenters",
+                                          "iir_walk_pieces", "iir_scan_pieces"]]
 
 
 class FibarStageTimes(C.Structure):

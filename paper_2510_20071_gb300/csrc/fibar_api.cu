@@ -106,6 +106,7 @@ int derive_layout(uint32_t W, uint32_t H, const fibar_params_t *pp, Layout &lo)
     if (!(p.c_on > 0.f) || !(p.c_off > 0.f) || !isfinite(p.c_on) || !isfinite(p.c_off)) return FIBAR_EINVAL;
     if (p.spatial_filter != 0 && p.spatial_filter != 1) return FIBAR_EINVAL;
     if (p.blur_mode != 0 && p.blur_mode != 1) return FIBAR_EINVAL;
+    if (p.chain_policy < 0 || p.chain_policy > 2) return FIBAR_EINVAL;
     const unsigned long long qmin = p.q_min ? p.q_min : std::max(1ull, (npix + 1023) / 1024);
     const unsigned long long qinit = p.q_init ? p.q_init : qmin;
     if (qmin > npix || qinit < qmin || qinit > npix) return FIBAR_EINVAL;
@@ -151,6 +152,7 @@ int derive_layout(uint32_t W, uint32_t H, const fibar_params_t *pp, Layout &lo)
     lo.sort_passes = (bits - kp.lb + RADIX_BITS - 1) / RADIX_BITS;
     kp.spatial = p.spatial_filter;
     kp.blur_mode = p.blur_mode;
+    kp.chain_policy = p.chain_policy;
     // event ring: the batch plus everything a window (or a guessed window) can reach back
     lo.R = next_pow2(maxp + npix + 8ull * 256);
     kp.ring_mask = lo.R - 1;
@@ -698,6 +700,8 @@ extern "C" int fibar_stats(fibar_t *h, fibar_stats_t *st, void *cuda_stream)
     st->detector_big_pops = c.big_pops;
     st->detector_ring_misses = c.ring_misses;
     st->detector_recenters = c.recenters;
+    st->iir_walk_pieces = c.walk_pieces;
+    st->iir_scan_pieces = c.scan_pieces;
     return rc;
 }
 

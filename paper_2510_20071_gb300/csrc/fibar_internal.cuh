@@ -99,6 +99,7 @@ struct Ctrl {
     unsigned long long fix_steps;
     unsigned long long s1_blurs;
     unsigned long long big_pops, ring_misses;
+    unsigned long long walk_pieces, scan_pieces;  // temporal filter schedules (cumulative)
 };
 
 // Constant per-handle parameters passed to kernels by value.
@@ -117,6 +118,7 @@ struct KParams {
     uint32_t lb;                 // low tile-id bits handled inside a bucket (<= 9)
     uint32_t nbuckets;           // buckets of 2^lb consecutive tiles
     int spatial, blur_mode;
+    int chain_policy;            // temporal filter schedule: 0 auto (per piece), 1 walk, 2 scan
 };
 
 struct SegTable {

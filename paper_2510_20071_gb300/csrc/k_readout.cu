@@ -144,6 +144,7 @@ __global__ void k_init(KParams kp, Ctrl *ctrl)
     ctrl->fixups = 0;
     ctrl->unmerged_total = ctrl->pass2_steps = ctrl->fix_steps = ctrl->s1_blurs = 0;
     ctrl->big_pops = ctrl->ring_misses = 0;
+    ctrl->walk_pieces = ctrl->scan_pieces = 0;
     ctrl->p2_count = 0;
     ctrl->batch_no = 1;
     ctrl->h_prev = 0;
