@@ -210,6 +210,31 @@ class _Scene:
         return torch.log(0.05 + self.texture(t))
 
 
+def _make_scene(scene: SceneSpec, W: int, H: int, rng: np.random.Generator, device, C: float) -> _Scene:
+    sc = _Scene(scene, W, H, rng, device)
+    if scene.texture == "perlin_pan":
+        # calibrate events per px of pan motion with a short probe pan along x
+        sc.px_per_event = 1.0
+        I0 = torch.log(0.05 + sc.noise((sc.xs) / scene.perlin_scale_px + float(sc.offset[0]),
+                                       sc.ys / scene.perlin_scale_px + float(sc.offset[1])))
+        I1 = torch.log(0.05 + sc.noise((sc.xs + 1.0) / scene.perlin_scale_px + float(sc.offset[0]),
+                                       sc.ys / scene.perlin_scale_px + float(sc.offset[1])))
+        ev_per_px = float(torch.abs(I1 - I0).sum().item()) / C
+        sc.px_per_event = 1.0 / max(ev_per_px, 1.0)
+    return sc
+
+
+def ground_truth(W: int, H: int, *, scene: SceneSpec | str = "sine_checker", seed: int = 0, C: float = 0.2,
+                 device: str | torch.device = "cpu"):
+    """The scene that ``simulate`` with the same arguments samples, as a function of time:
+    returns ``f(t_us) -> (H, W) float32`` log intensity log(0.05 + texture) at t_us."""
+    if isinstance(scene, str):
+        scene = SceneSpec(texture=scene)
+    rng = np.random.Generator(np.random.Philox(seed))
+    sc = _make_scene(scene, W, H, rng, torch.device(device), C)
+    return lambda t_us: sc.log_intensity(float(t_us) / 1e6).reshape(H, W)
+
+
 def simulate(W: int, H: int, n_events: int, *, scene: SceneSpec | str = "sine_checker",
              seed: int = 0, C: float = 0.2, noise_frac: float = 0.0,
              device: str | torch.device = "cpu", t0_s: float = 0.0,
@@ -228,19 +253,9 @@ def simulate(W: int, H: int, n_events: int, *, scene: SceneSpec | str = "sine_ch
         scene = SceneSpec(texture=scene)
     device = torch.device(device)
     rng = np.random.Generator(np.random.Philox(seed))
-    sc = _Scene(scene, W, H, rng, device)
+    sc = _make_scene(scene, W, H, rng, device, C)
     n_noise = int(round(n_events * noise_frac))
     n_signal = n_events - n_noise
-
-    if scene.texture == "perlin_pan":
-        # calibrate events per px of pan motion with a short probe pan along x
-        sc.px_per_event = 1.0
-        I0 = torch.log(0.05 + sc.noise((sc.xs) / scene.perlin_scale_px + float(sc.offset[0]),
-                                       sc.ys / scene.perlin_scale_px + float(sc.offset[1])))
-        I1 = torch.log(0.05 + sc.noise((sc.xs + 1.0) / scene.perlin_scale_px + float(sc.offset[0]),
-                                       sc.ys / scene.perlin_scale_px + float(sc.offset[1])))
-        ev_per_px = float(torch.abs(I1 - I0).sum().item()) / C
-        sc.px_per_event = 1.0 / max(ev_per_px, 1.0)
 
     t = t0_s
     I_prev = sc.log_intensity(t)
