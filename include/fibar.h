@@ -66,7 +66,10 @@ typedef struct {
                                    (Sec. 4.2, the paper's method; read-out copies L);
                                 1 = "S2": never modify L; at read-out, output the 3x3 blur
                                    of L at stale pixels (had an event, none queued) and L
-                                   elsewhere                                              */
+                                   elsewhere;
+                                2 = learned fill: as S2, with the stale pixels filled by
+                                   the network set by fibar_fill_set_weights (the Gaussian
+                                   of S2 until weights are set)                           */
     int32_t chain_policy;    /* schedule of the temporal filter (same results up to FP32
                                 rounding; the paper runs it event by event):
                                 0 = auto: per piece of <= 2048 events of 512 tiles, the scan
@@ -265,6 +268,54 @@ int fibar_debug_state(fibar_t *h, fibar_state_view_t *v, void *cuda_stream);
  * time on other streams or threads, with this or another handle on the same device,
  * share the buffer and race; calls on one stream are ordered. */
 int fibar_queue_counts_noalloc(fibar_t *h, uint32_t *cnt, int on_device, void *cuda_stream);
+
+/* ---- Learned stale-pixel fill ---------------------------------------------------------
+ * The paper fills a pixel that goes stale with an isotropic 3x3 Gaussian (Sec. 4.2); its
+ * limitations section names what that blur ignores (the gradient's magnitude and
+ * direction) and leaves more elaborate fills to GPUs.  The learned fill is a 3-layer 3x3
+ * convolutional network (2 -> 16 -> 16 -> 1 channels, ReLU, zero padding; BF16 weights,
+ * FP32 accumulation; the 16 -> 16 layer on the tensor cores) whose inputs per pixel are
+ * L (Eq. 10) and the activity age min(4, (k - last) / q) (k the events applied, last the
+ * pixel's last event, q the queue length); its output replaces L at the stale pixels.
+ * Parameters theta: FIBAR_FILL_NPARAMS floats, in order W1 [16][2][3][3], b1 [16],
+ * W2 [16][16][3][3], b2 [16], W3 [1][16][3][3], b3 [1] (weights are rounded to BF16).  */
+#define FIBAR_FILL_NPARAMS 2769
+
+/* Set (theta != NULL, n = FIBAR_FILL_NPARAMS host floats, copied) or remove (theta = NULL)
+ * the network a blur_mode = 2 handle fills with from its next read-out on.
+ * Errors: EINVAL (h NULL, wrong n, a non-finite parameter), ENOMEM. */
+int fibar_fill_set_weights(fibar_t *h, const float *theta, size_t n);
+
+/* The network's inputs for the handle's current state (after its last read-out or flush),
+ * for training and evaluation: x = device float [2][H][W] (L, then the age), stale = device
+ * uint8 [H][W] (1 = had an event, none queued) or NULL.  Asynchronous on cuda_stream.
+ * Errors: EINVAL (NULL h or x, misaligned x, a handle with spatial_filter = 0), ECUDA. */
+int fibar_fill_features(fibar_t *h, float *x, uint8_t *stale, void *cuda_stream);
+
+/* The fill image of explicit inputs with the read-out's kernel: out[i] = the network's
+ * output where stale[i] != 0, x[0][i] elsewhere.  theta: host floats (as above); x, stale,
+ * out: device memory (x, out 4-byte aligned).  Synchronises cuda_stream.  Needs no handle
+ * (a 4-byte status word is allocated on the stream).  Errors: EINVAL (NULL pointer, W or
+ * H = 0, W*H > 2^24, a non-finite parameter), ENOMEM, ECUDA, ETIMEOUT (the tensor-core
+ * completion wait gave up). */
+int fibar_fill_forward(const float *theta, const float *x, const uint8_t *stale, uint32_t W, uint32_t H,
+                       float *out, void *cuda_stream);
+
+/* One training step of the fill network (all pointers device memory):
+ *   X [F][2][H][W] inputs, T [F][H][W] targets, M [F][H][W] loss mask (uint8), F = n_frames;
+ *   crops [n_crops][3] = (frame, y0, x0) of 24 x 24 crops inside a frame (a crop that is not
+ *   is skipped and counted in loss_acc[2]); the loss is the
+ *   mean squared error of the network (evaluated on each crop with zero padding at its
+ *   border, BF16 weights) against T over the masked pixels at least 3 pixels inside a crop;
+ *   theta, m, v: FIBAR_FILL_NPARAMS FP32 master weights and Adam moments, updated in place
+ *   with step number `step` (>= 1) and learning rate lr (beta1 0.9, beta2 0.999, eps 1e-8;
+ *   lr <= 0: gradient only); grad receives the mean gradient; loss_acc[3] receives (sum of
+ *   squared errors, number of loss pixels, skipped crops) in double.  Asynchronous on cuda_stream.
+ * Errors: EINVAL (NULL pointer, W or H < 24, n_frames = 0, n_crops = 0 or > 65535,
+ * step = 0), ECUDA. */
+int fibar_fill_train_step(const float *X, const float *T, const uint8_t *M, uint32_t W, uint32_t H,
+                          uint32_t n_frames, const int32_t *crops, uint32_t n_crops, float *theta, float *m,
+                          float *v, float *grad, uint32_t step, float lr, double *loss_acc, void *cuda_stream);
 
 /* Failure-detection check (no counterpart in the paper): runs, on the device, the bounded
  * wait that the pipeline's look-back and dataflow kernels use, on a flag that nothing

@@ -25,7 +25,10 @@ EXPORTED = ["fibar_default_params", "fibar_create", "fibar_push_events", "fibar_
             "fibar_flush", "fibar_debug_state", "fibar_stats", "fibar_set_timing",
             "fibar_stage_times", "fibar_last_error", "fibar_destroy", "fibar_queue_counts_noalloc",
             "fibar_readout_batch", "fibar_memory_bytes", "fibar_relative_thresholds",
-            "fibar_set_pixel_gain", "fibar_debug_wait_timeout", "fibar_push_events_many"]
+            "fibar_set_pixel_gain", "fibar_debug_wait_timeout", "fibar_push_events_many",
+            "fibar_fill_set_weights", "fibar_fill_features", "fibar_fill_forward", "fibar_fill_train_step"]
+
+FIBAR_FILL_NPARAMS = 2769
 
 STAGES = ["decode", "sort", "walk", "det_counts", "det_pass1", "det_pass2", "det_fix", "s1_blur",
           "readout", "commit"]
@@ -120,6 +123,15 @@ def load_library(build_if_missing: bool = True):
             lib.fibar_debug_wait_timeout.restype = C.c_int
             lib.fibar_push_events_many.argtypes = [vp, C.POINTER(vp), C.POINTER(C.c_size_t), C.c_size_t, C.c_int, vp]
             lib.fibar_push_events_many.restype = C.c_int
+            lib.fibar_fill_set_weights.argtypes = [vp, vp, C.c_size_t]
+            lib.fibar_fill_set_weights.restype = C.c_int
+            lib.fibar_fill_features.argtypes = [vp, vp, vp, vp]
+            lib.fibar_fill_features.restype = C.c_int
+            lib.fibar_fill_forward.argtypes = [vp, vp, vp, C.c_uint32, C.c_uint32, vp, vp]
+            lib.fibar_fill_forward.restype = C.c_int
+            lib.fibar_fill_train_step.argtypes = [vp, vp, vp, C.c_uint32, C.c_uint32, C.c_uint32, vp, C.c_uint32,
+                                                  vp, vp, vp, vp, C.c_uint32, C.c_float, vp, vp]
+            lib.fibar_fill_train_step.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -212,6 +224,23 @@ def fibar_push_events_many(h, ev_ptrs, ns, on_device: int, stream: int) -> int:
 
 def fibar_debug_wait_timeout(h, max_spins: int, stream: int) -> int:
     return load_library().fibar_debug_wait_timeout(h, max_spins, stream)
+
+
+def fibar_fill_set_weights(h, theta_ptr, n: int) -> int:
+    return load_library().fibar_fill_set_weights(h, theta_ptr, n)
+
+
+def fibar_fill_features(h, x_ptr: int, stale_ptr, stream: int) -> int:
+    return load_library().fibar_fill_features(h, x_ptr, stale_ptr, stream)
+
+
+def fibar_fill_forward(theta_ptr: int, x_ptr: int, stale_ptr: int, W: int, H: int, out_ptr: int, stream: int) -> int:
+    return load_library().fibar_fill_forward(theta_ptr, x_ptr, stale_ptr, W, H, out_ptr, stream)
+
+
+def fibar_fill_train_step(X, T, M, W, H, F, crops, n_crops, theta, m, v, grad, step, lr, loss_acc, stream) -> int:
+    return load_library().fibar_fill_train_step(X, T, M, W, H, F, crops, n_crops, theta, m, v, grad, step, lr,
+                                                loss_acc, stream)
 
 
 # --- convenience wrapper ---------------------------------------------------------------
@@ -348,6 +377,23 @@ class Fibar:
         if gain.is_cuda:
             self._keep.append(gain)
 
+    def set_fill_weights(self, theta) -> None:
+        """Learned-fill network of a blur_mode = 2 handle (FIBAR_FILL_NPARAMS floats, host
+        array or CPU tensor); None returns to the Gaussian."""
+        if theta is None:
+            self._check(fibar_fill_set_weights(self.h, None, 0))
+            return
+        a = np.ascontiguousarray(np.asarray(theta, dtype=np.float32).reshape(-1))
+        self._check(fibar_fill_set_weights(self.h, a.ctypes.data, a.size))
+
+    def fill_features(self):
+        """(x [2, H, W] float32, stale [H, W] uint8) CUDA tensors of the current state."""
+        t = self.torch
+        x = t.empty((2, self.H, self.W), dtype=t.float32, device="cuda")
+        st = t.empty((self.H, self.W), dtype=t.uint8, device="cuda")
+        self._check(fibar_fill_features(self.h, x.data_ptr(), st.data_ptr(), self._s))
+        return x, st
+
     def memory_bytes(self) -> int:
         """Device bytes this handle allocated (fibar_memory_bytes of its parameters)."""
         rc, b = fibar_memory_bytes(self.W, self.H, self.params)
@@ -438,3 +484,23 @@ def relative_thresholds(ev, W: int, H: int, stream=None):
     if rc != 0:
         raise FibarError(rc, "fibar_relative_thresholds failed")
     return tuple(outs)
+
+
+def fill_forward(theta, x, stale, stream=None):
+    """The learned fill of explicit inputs (x [2, H, W] float32 and stale [H, W] uint8 CUDA
+    tensors) with the read-out's kernel: a new [H, W] CUDA float32 image."""
+    import torch
+    if not (x.is_cuda and stale.is_cuda and x.dtype == torch.float32 and stale.dtype == torch.uint8
+            and x.dim() == 3 and x.shape[0] == 2 and tuple(stale.shape) == tuple(x.shape[1:])
+            and x.is_contiguous() and stale.is_contiguous()):
+        raise TypeError("x must be a contiguous CUDA float32 [2, H, W] tensor and stale a uint8 [H, W] one")
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32).reshape(-1))
+    if th.size != FIBAR_FILL_NPARAMS:
+        raise ValueError(f"theta must have {FIBAR_FILL_NPARAMS} parameters")
+    H, W = int(x.shape[1]), int(x.shape[2])
+    out = torch.empty((H, W), dtype=torch.float32, device=x.device)
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    rc = fibar_fill_forward(th.ctypes.data, x.data_ptr(), stale.data_ptr(), W, H, out.data_ptr(), s)
+    if rc != 0:
+        raise FibarError(rc, "fibar_fill_forward failed")
+    return out

@@ -105,7 +105,7 @@ int derive_layout(uint32_t W, uint32_t H, const fibar_params_t *pp, Layout &lo)
     if (p.fill_num == 0 || p.fill_den == 0 || p.fill_num > 255 || p.fill_den > 255) return FIBAR_EINVAL;
     if (!(p.c_on > 0.f) || !(p.c_off > 0.f) || !isfinite(p.c_on) || !isfinite(p.c_off)) return FIBAR_EINVAL;
     if (p.spatial_filter != 0 && p.spatial_filter != 1) return FIBAR_EINVAL;
-    if (p.blur_mode != 0 && p.blur_mode != 1) return FIBAR_EINVAL;
+    if (p.blur_mode < 0 || p.blur_mode > 2) return FIBAR_EINVAL;
     if (p.chain_policy < 0 || p.chain_policy > 2) return FIBAR_EINVAL;
     const unsigned long long qmin = p.q_min ? p.q_min : std::max(1ull, (npix + 1023) / 1024);
     const unsigned long long qinit = p.q_init ? p.q_init : qmin;
@@ -417,6 +417,7 @@ extern "C" void fibar_destroy(fibar_t *h)
     cudaDeviceSynchronize();
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     free_all(h);
+    delete h->fill;
     delete h;
 }
 
@@ -580,7 +581,10 @@ int process(fibar_t *h, unsigned long long t_read, float *out, cudaStream_t s)
     }
     mk.mark(FIBAR_STAGE_READOUT);
     if (out) {
-        e = launch_readout(kp, b, out, s, nl);
+        if (kp.spatial && kp.blur_mode == 2 && h->fill)
+            e = launch_fill_readout(*h->fill, kp, b, out, s, nl);
+        else
+            e = launch_readout(kp, b, out, s, nl);
         if (e != cudaSuccess) return cuda_fail(h, e, "readout");
     }
     mk.mark(FIBAR_STAGE_COMMIT);

@@ -182,6 +182,16 @@ struct Bufs {
     size_t max_chunks, max_dec_tiles, max_sort_tiles;
 };
 
+// Learned stale-pixel fill (k_fill.cu): network parameters as a kernel parameter.
+constexpr int FILL_NPARAMS = 2769;  // W1 16x2x3x3, b1 16, W2 16x16x3x3, b2 16, W3 1x16x3x3, b3 1
+struct FillParams {
+    uint4 w2[9 * 32];      // conv2 B operand per tap: 16 (co) x 16 (ci) BF16, K-major, no swizzle
+    float w1[16 * 18];     // conv1 [co][ci * 9 + tap], BF16 values
+    float b1[16], b2[16];
+    float w3[16 * 9];      // conv3 [ci][tap], BF16 values
+    float b3;
+};
+
 }  // namespace fibar
 
 struct fibar_s {
@@ -199,6 +209,7 @@ struct fibar_s {
     unsigned long long pending_upper;   // upper bound of records not yet applied
     unsigned int *snap_host;            // host view of Bufs::snap (written by k_commit)
     float *gain_buf;                    // per-pixel gains, allocated by the first fibar_set_pixel_gain
+    fibar::FillParams *fill;            // learned-fill network (blur_mode 2), nullptr = Gaussian
     unsigned long long commits;         // read-outs and flushes launched
     unsigned long long pushed_since;    // records pushed since the last read-out or flush
     int carry_slot;
@@ -307,4 +318,7 @@ cudaError_t launch_s1(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned
 cudaError_t launch_debug_counts(const KParams &kp, const Bufs &b, unsigned int *cnt,
                                 cudaStream_t s, unsigned long long &nl);
 int grid_for(int sms_mult);
+// learned fill read-out of a handle (k_fill.cu)
+cudaError_t launch_fill_readout(const FillParams &fp, const KParams &kp, const Bufs &b, float *out, cudaStream_t s,
+                                unsigned long long &nl);
 }  // namespace fibar

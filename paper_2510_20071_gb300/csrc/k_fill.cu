@@ -1,0 +1,709 @@
+// Learned stale-pixel fill: a 3-layer 3x3 convolutional network replaces the 3x3
+// Gaussian at stale pixels (the read-out's masked fill).  The paper fills a pixel that
+// went stale with an isotropic 3x3 Gaussian (Sec. 4.2) and, in its limitations section,
+// names what that blur ignores (the gradient's magnitude and direction) and leaves more
+// elaborate fills to GPUs; this is one such fill.
+//
+// Network (inputs per pixel: x0 = L, the filter output of Eq. 10, and x1 = the activity
+// age min(4, (k - last) / q), k the events applied, last the pixel's last event, q the
+// queue length; the queue of Sec. 4.2 is the window [k - q, k)):
+//   a1 = relu(b1 + W1 * x)        2 -> 16 channels   CUDA cores, FP32, BF16 weights
+//   a2 = relu(b2 + W2 * bf16(a1)) 16 -> 16           tcgen05.mma kind::f16, BF16 in, FP32 acc
+//   y  = b3 + W3 * a2             16 -> 1            CUDA cores, FP32, BF16 weights
+//   out = y at stale pixels (had an event, none queued), L elsewhere
+// ("*" a 3x3 cross-correlation with zero padding at the image border).
+//
+// Inference kernel (k_fill): persistent, one CTA of 256 threads per SM, units of 8 output
+// rows x 126 output columns.  Per unit: the inputs of 14 x 132 pixels go to shared memory;
+// conv1 writes a1 for 12 x 130 pixels as BF16 in the tensor cores' canonical K-major
+// layout (no swizzle: two planes of 8 channels, one 16-byte row per pixel); conv2 is 90
+// MMAs of 128 x 16 x 16 (10 rows of 128 pixels, 9 taps each: the tap (dy, dx) is the a1
+// row r + dy read from pixel dx on, i.e. the descriptor's start moved by dx rows) into
+// 160 TMEM columns; the epilogue reads them back with tcgen05.ld (lane = pixel), adds
+// the bias, applies ReLU and stores a2 (FP32) to shared memory; conv3 and the mask
+// write the image.  Weights travel as a kernel parameter (constant bank).
+//
+// Training (k_fill_train, k_fill_adam): one CTA per 24 x 24 crop runs the forward pass,
+// the loss gradient over the crop's interior stale pixels (the 7 x 7 receptive field
+// inside the crop) and the backward pass in shared memory on CUDA cores (FP32), and
+// adds its weight gradients to a global sum; the Adam step divides by the number of
+// loss pixels and updates the FP32 master weights.
+#include <math.h>
+#include <string.h>
+
+#include "fibar_internal.cuh"
+
+namespace fibar {
+
+constexpr int FL_R = 8;            // output rows per unit
+constexpr int FL_OC = 126;         // output columns per unit
+constexpr int FL_M = 128;          // a2 columns per unit (the MMA's M)
+constexpr int FL_A1C = FL_M + 2;   // a1 columns
+constexpr int FL_XC = FL_M + 4;    // input columns
+constexpr int FL_A2R = FL_R + 2;   // a2 rows
+constexpr int FL_A1R = FL_R + 4;   // a1 rows
+constexpr int FL_XR = FL_R + 6;    // input rows
+constexpr int FL_THREADS = 256;
+constexpr unsigned FL_TMEM_COLS = 256;                      // >= 16 columns x 10 rows
+constexpr unsigned FL_PLANE = FL_A1C * 16;                  // one K plane of an a1 row
+constexpr unsigned FL_A1ROW = 2 * FL_PLANE;                 // bytes per a1 row
+constexpr float FL_AGE_MAX = 4.f;
+constexpr unsigned FL_SPIN_LIMIT = 1u << 20;
+constexpr unsigned ERR_FILL_WAIT = 32u;                     // Ctrl::error bit
+
+struct FillSmem {
+    unsigned char a1[FL_A1R * FL_A1ROW];   // canonical layout, 16-byte aligned
+    uint4 w2[9 * 32];                      // B operands (per tap 16 x 16 BF16)
+    float x[2][FL_XR][FL_XC];
+    float a2[FL_A2R][FL_M][17];            // padded: conflict-free by pixel
+    unsigned char stale[FL_R][FL_OC + 2];
+    unsigned long long bar;
+    unsigned tmem;
+};
+
+// Where the inputs come from: a handle's state (read-out) or explicit images.
+struct FillIO {
+    int from_handle;
+    const Ctrl *ctrl;                      // handle: k = base + m, h = det.h
+    const float *L;                        // handle: filter output
+    const unsigned long long *last_pix;    // handle: global index of each pixel's last event
+    const float *x;                        // explicit: [2][H][W]
+    const unsigned char *stale;            // explicit: [H][W] (1 = fill)
+    float *out;                            // [H][W]
+    unsigned *err;                         // error word (bit ERR_FILL_WAIT)
+    unsigned W, H;
+};
+
+__device__ __forceinline__ unsigned fl_smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned short fl_bf16_bits(float v)
+{
+    // round to nearest even (v is finite and >= 0 here: a ReLU output)
+    const unsigned u = __float_as_uint(v);
+    return (unsigned short)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+
+// tcgen05 shared-memory matrix descriptor: K-major, no swizzle; lbo = byte distance of
+// the two 8-element K halves, sbo = byte distance of 8-row groups.
+__device__ __forceinline__ unsigned long long fl_desc(unsigned saddr, unsigned lbo, unsigned sbo)
+{
+    return (unsigned long long)((saddr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M = 128, N = 16
+constexpr unsigned FL_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void fl_mma(unsigned d_tmem, unsigned long long a, unsigned long long b, unsigned acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(d_tmem), "l"(a), "l"(b), "r"(FL_IDESC), "r"(acc)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool fl_wait(unsigned long long *bar, unsigned phase)
+{
+    for (unsigned spins = 0; spins < FL_SPIN_LIMIT; ++spins) {
+        unsigned ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(fl_smem_u32(bar)), "r"(phase)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fl_tmem_ld16(unsigned taddr, float (&v)[16])
+{
+    unsigned r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                 "%12, %13, %14, %15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(FL_THREADS, 1) k_fill(FillParams fp, FillIO io)
+{
+    PDL_ENTRY();
+    extern __shared__ __align__(1024) unsigned char fl_smem_raw[];
+    FillSmem &S = *reinterpret_cast<FillSmem *>(fl_smem_raw);
+    const int W = (int)io.W, H = (int)io.H;
+    const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nseg = (W + FL_OC - 1) / FL_OC, nstrip = (H + FL_R - 1) / FL_R;
+    const int units = nseg * nstrip;
+
+    unsigned long long k_now = 0, h = 0, q = 1;
+    if (io.from_handle) {
+        k_now = io.ctrl->base + io.ctrl->m;
+        h = (unsigned long long)io.ctrl->det.h;
+        q = k_now > h ? k_now - h : 1ull;
+    }
+    for (int i = threadIdx.x; i < 9 * 32; i += FL_THREADS) S.w2[i] = fp.w2[i];
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(fl_smem_u32(&S.bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(fl_smem_u32(&S.tmem)), "r"(FL_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = S.tmem;
+    const unsigned a1_base = fl_smem_u32(S.a1), w2_base = fl_smem_u32(S.w2);
+    unsigned phase = 0;
+    bool failed = false;
+
+    for (int u = blockIdx.x; u < units && !failed; u += gridDim.x) {
+        const int y0 = (u / nseg) * FL_R, x0 = (u % nseg) * FL_OC;
+        // inputs: rows y0-3 .. y0+10, columns x0-3 .. x0+128 (zero outside the image)
+        for (int i = threadIdx.x; i < FL_XR * FL_XC; i += FL_THREADS) {
+            const int r = i / FL_XC, c = i % FL_XC;
+            const int gy = y0 - 3 + r, gx = x0 - 3 + c;
+            float v0 = 0.f, v1 = 0.f;
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                const size_t p = (size_t)gy * W + gx;
+                if (io.from_handle) {
+                    v0 = io.L[p];
+                    const unsigned long long lp = io.last_pix[p];
+                    if (lp == NONE64) {
+                        v1 = FL_AGE_MAX;
+                    } else {
+                        const unsigned long long gap = k_now - lp;
+                        v1 = gap >= 4ull * q ? FL_AGE_MAX : (float)gap / (float)q;
+                    }
+                    const int orow = gy - y0, ocol = gx - x0;
+                    if (orow >= 0 && orow < FL_R && ocol >= 0 && ocol < FL_OC)
+                        S.stale[orow][ocol] = (lp != NONE64 && lp < h) ? 1 : 0;
+                } else {
+                    v0 = io.x[p];
+                    v1 = io.x[(size_t)W * H + p];
+                    const int orow = gy - y0, ocol = gx - x0;
+                    if (orow >= 0 && orow < FL_R && ocol >= 0 && ocol < FL_OC) S.stale[orow][ocol] = io.stale[p];
+                }
+            }
+            S.x[0][r][c] = v0;
+            S.x[1][r][c] = v1;
+        }
+        __syncthreads();
+        // conv1 -> a1 (BF16, canonical layout); zero outside the image
+        for (int i = threadIdx.x; i < FL_A1R * FL_A1C; i += FL_THREADS) {
+            const int j = i / FL_A1C, c = i % FL_A1C;
+            const int gy = y0 - 2 + j, gx = x0 - 2 + c;
+            float acc[16];
+#pragma unroll
+            for (int o = 0; o < 16; ++o) acc[o] = fp.b1[o];
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+#pragma unroll
+                for (int ci = 0; ci < 2; ++ci)
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const float xv = S.x[ci][j + dy][c + dx];
+#pragma unroll
+                            for (int o = 0; o < 16; ++o) acc[o] = fmaf(fp.w1[o * 18 + ci * 9 + dy * 3 + dx], xv, acc[o]);
+                        }
+            }
+            unsigned pk[8];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+                const unsigned lo = in ? fl_bf16_bits(fmaxf(acc[2 * o], 0.f)) : 0u;
+                const unsigned hi = in ? fl_bf16_bits(fmaxf(acc[2 * o + 1], 0.f)) : 0u;
+                pk[o] = lo | (hi << 16);
+            }
+            uint4 *row = reinterpret_cast<uint4 *>(S.a1 + j * FL_A1ROW);
+            row[c] = make_uint4(pk[0], pk[1], pk[2], pk[3]);            // channels 0-7
+            row[FL_A1C + c] = make_uint4(pk[4], pk[5], pk[6], pk[7]);   // channels 8-15
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (threadIdx.x == 0) {
+            // conv2: a2 row r (global row y0-1+r), pixels x0-1 .. x0+126; tap (dy, dx)
+            // reads a1 row r+dy from pixel dx on
+            for (int r = 0; r < FL_A2R; ++r) {
+#pragma unroll
+                for (int t = 0; t < 9; ++t) {
+                    const int dy = t / 3, dx = t % 3;
+                    const unsigned long long ad = fl_desc(a1_base + (r + dy) * FL_A1ROW + dx * 16, FL_PLANE, 128);
+                    const unsigned long long bd = fl_desc(w2_base + t * 512, 256, 128);
+                    fl_mma(tmem + 16 * r, ad, bd, t > 0 ? 1u : 0u);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(fl_smem_u32(&S.bar)) : "memory");
+        }
+        if (!fl_wait(&S.bar, phase)) {
+            if (threadIdx.x == 0) atomicOr(io.err, ERR_FILL_WAIT);
+            failed = true;
+        }
+        phase ^= 1u;
+        failed = __syncthreads_or(failed) != 0;
+        if (failed) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (its pixels), rows of its half
+        {
+            const int px = 32 * (warp & 3) + lane;
+            const int gx = x0 - 1 + px;
+            for (int r = (int)(warp >> 2); r < FL_A2R; r += 2) {
+                float v[16];
+                fl_tmem_ld16(tmem + ((32u * (warp & 3)) << 16) + 16u * r, v);
+                const int gy = y0 - 1 + r;
+                const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+#pragma unroll
+                for (int o = 0; o < 16; ++o) S.a2[r][px][o] = in ? fmaxf(v[o] + fp.b2[o], 0.f) : 0.f;
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        // conv3 and the mask
+        for (int i = threadIdx.x; i < FL_R * FL_OC; i += FL_THREADS) {
+            const int o = i / FL_OC, oc = i % FL_OC;
+            const int gy = y0 + o, gx = x0 + oc;
+            if (gy >= H || gx >= W) continue;
+            float v = S.x[0][o + 3][oc + 3];
+            if (S.stale[o][oc]) {
+                float acc = fp.b3;
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) acc = fmaf(fp.w3[c * 9 + dy * 3 + dx], S.a2[o + dy][oc + dx][c], acc);
+                v = acc;
+            }
+            io.out[(size_t)gy * W + gx] = v;
+        }
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(FL_TMEM_COLS) : "memory");
+}
+
+// The network's inputs from a handle's state: x [2][H][W] (L, age) and the stale mask.
+__global__ void k_fill_features(const Ctrl *ctrl, const float *L, const unsigned long long *last_pix,
+                                unsigned W, unsigned H, float *x, unsigned char *stale)
+{
+    const unsigned long long k_now = ctrl->base + ctrl->m, h = (unsigned long long)ctrl->det.h;
+    const unsigned long long q = k_now > h ? k_now - h : 1ull;
+    const size_t n = (size_t)W * H;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+        const unsigned long long lp = last_pix[p];
+        float a = FL_AGE_MAX;
+        if (lp != NONE64) {
+            const unsigned long long gap = k_now - lp;
+            a = gap >= 4ull * q ? FL_AGE_MAX : (float)gap / (float)q;
+        }
+        x[p] = L[p];
+        x[n + p] = a;
+        if (stale) stale[p] = (lp != NONE64 && lp < h) ? 1 : 0;
+    }
+}
+
+// ---- training --------------------------------------------------------------------
+
+constexpr int FT_S = 24;                 // crop side
+constexpr int FT_P = FT_S * FT_S;
+constexpr int FT_THREADS = 256;
+constexpr int FT_MARGIN = 3;             // loss only where the 7 x 7 receptive field is inside
+
+struct TrainSmem {
+    float x[2][FT_P];
+    float z1[16][FT_P];     // z1, then dz1
+    float z2[16][FT_P];     // z2, then dz2
+    float g[FT_P];          // y, then the loss gradient gy
+    float th[FILL_NPARAMS];
+    float red[FT_THREADS / 32];
+};
+
+// parameter offsets in theta (W1, b1, W2, b2, W3, b3)
+constexpr int OW1 = 0, OB1 = 288, OW2 = 304, OB2 = 2608, OW3 = 2624, OB3 = 2768;
+
+__device__ __forceinline__ float fl_bf16_round(float v)
+{
+    const unsigned u = __float_as_uint(v);
+    return __uint_as_float(((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16) << 16);
+}
+
+__device__ __forceinline__ float crop_at(const float *a, int y, int x)
+{
+    return (y >= 0 && y < FT_S && x >= 0 && x < FT_S) ? a[y * FT_S + x] : 0.f;
+}
+
+__device__ __forceinline__ float block_sum_ft(float v, float *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.f;
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < FT_THREADS / 32 ? red[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+    }
+    return t;  // valid in thread 0
+}
+
+// One CTA per crop: forward, loss gradient, backward; unnormalised gradient sums into
+// grad[0 .. FILL_NPARAMS), the loss sum into acc[0] and the loss pixel count into acc[1].
+__global__ void __launch_bounds__(FT_THREADS, 2)
+k_fill_train(const float *X, const float *T, const unsigned char *M, unsigned W, unsigned H, unsigned F,
+             const int *crops, const float *theta, float *grad, double *acc)
+{
+    extern __shared__ __align__(16) unsigned char ft_smem_raw[];
+    TrainSmem &S = *reinterpret_cast<TrainSmem *>(ft_smem_raw);
+    const int f = crops[3 * blockIdx.x], cy = crops[3 * blockIdx.x + 1], cx = crops[3 * blockIdx.x + 2];
+    // a crop outside the frames contributes nothing (counted in acc[2])
+    if (f < 0 || f >= (int)F || cy < 0 || cx < 0 || cy + FT_S > (int)H || cx + FT_S > (int)W) {
+        if (threadIdx.x == 0) atomicAdd(&acc[2], 1.0);
+        return;
+    }
+    const size_t plane = (size_t)W * H;
+    const float *Xf = X + (size_t)f * 2 * plane;
+    for (int i = threadIdx.x; i < FILL_NPARAMS; i += FT_THREADS) {
+        const float v = theta[i];
+        // the forward pass uses BF16 weights (biases stay FP32)
+        const bool is_w = i < OB1 || (i >= OW2 && i < OB2) || (i >= OW3 && i < OB3);
+        S.th[i] = is_w ? fl_bf16_round(v) : v;
+    }
+    for (int p = threadIdx.x; p < FT_P; p += FT_THREADS) {
+        const size_t g = (size_t)(cy + p / FT_S) * W + cx + p % FT_S;
+        S.x[0][p] = Xf[g];
+        S.x[1][p] = Xf[plane + g];
+    }
+    __syncthreads();
+    // forward: z1, z2 (pre-activations), y
+    for (int i = threadIdx.x; i < 16 * FT_P; i += FT_THREADS) {
+        const int o = i / FT_P, p = i % FT_P, py = p / FT_S, px = p % FT_S;
+        float a = S.th[OB1 + o];
+        for (int ci = 0; ci < 2; ++ci)
+            for (int t = 0; t < 9; ++t)
+                a = fmaf(S.th[OW1 + o * 18 + ci * 9 + t], crop_at(S.x[ci], py + t / 3 - 1, px + t % 3 - 1), a);
+        S.z1[o][p] = a;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 16 * FT_P; i += FT_THREADS) {
+        const int o = i / FT_P, p = i % FT_P, py = p / FT_S, px = p % FT_S;
+        float a = S.th[OB2 + o];
+        for (int ci = 0; ci < 16; ++ci)
+            for (int t = 0; t < 9; ++t) {
+                const int yy = py + t / 3 - 1, xx = px + t % 3 - 1;
+                const float v = (yy >= 0 && yy < FT_S && xx >= 0 && xx < FT_S) ? fl_bf16_round(fmaxf(S.z1[ci][yy * FT_S + xx], 0.f)) : 0.f;
+                a = fmaf(S.th[OW2 + (o * 16 + ci) * 9 + t], v, a);
+            }
+        S.z2[o][p] = a;
+    }
+    __syncthreads();
+    float lsum = 0.f, lcnt = 0.f;
+    for (int p = threadIdx.x; p < FT_P; p += FT_THREADS) {
+        const int py = p / FT_S, px = p % FT_S;
+        float a = S.th[OB3];
+        for (int ci = 0; ci < 16; ++ci)
+            for (int t = 0; t < 9; ++t)
+                a = fmaf(S.th[OW3 + ci * 9 + t], fmaxf(crop_at(S.z2[ci], py + t / 3 - 1, px + t % 3 - 1), 0.f), a);
+        const bool inner = py >= FT_MARGIN && py < FT_S - FT_MARGIN && px >= FT_MARGIN && px < FT_S - FT_MARGIN;
+        const size_t g = (size_t)f * plane + (size_t)(cy + py) * W + cx + px;
+        float gy = 0.f;
+        if (inner && M[g]) {
+            const float r = a - T[g];
+            gy = 2.f * r;
+            lsum += r * r;
+            lcnt += 1.f;
+        }
+        S.g[p] = gy;
+    }
+    __syncthreads();
+    {
+        const float ls = block_sum_ft(lsum, S.red);
+        const float lc = block_sum_ft(lcnt, S.red);
+        if (threadIdx.x == 0) {
+            atomicAdd(&acc[0], (double)ls);
+            atomicAdd(&acc[1], (double)lc);
+        }
+    }
+    // conv3 weights and bias
+    for (int i = threadIdx.x; i < 16 * 9 + 1; i += FT_THREADS) {
+        float s = 0.f;
+        if (i < 144) {
+            const int ci = i / 9, t = i % 9;
+            for (int p = 0; p < FT_P; ++p)
+                s = fmaf(S.g[p], fmaxf(crop_at(S.z2[ci], p / FT_S + t / 3 - 1, p % FT_S + t % 3 - 1), 0.f), s);
+            atomicAdd(&grad[OW3 + i], s);
+        } else {
+            for (int p = 0; p < FT_P; ++p) s += S.g[p];
+            atomicAdd(&grad[OB3], s);
+        }
+    }
+    __syncthreads();
+    // dz2 = (conv3 transposed applied to gy) where z2 > 0, in place of z2
+    for (int i = threadIdx.x; i < 16 * FT_P; i += FT_THREADS) {
+        const int c = i / FT_P, p = i % FT_P, py = p / FT_S, px = p % FT_S;
+        float d = 0.f;
+        if (S.z2[c][p] > 0.f)
+            for (int t = 0; t < 9; ++t) d = fmaf(S.th[OW3 + c * 9 + t], crop_at(S.g, py - (t / 3 - 1), px - (t % 3 - 1)), d);
+        S.z2[c][p] = d;
+    }
+    __syncthreads();
+    // conv2 weights and biases: sum over pixels of dz2 x bf16(a1) shifted
+    for (int i = threadIdx.x; i < 16 * 16 * 9 + 16; i += FT_THREADS) {
+        float s = 0.f;
+        if (i < 2304) {
+            const int o = i / 144, ci = (i / 9) % 16, t = i % 9;
+            for (int p = 0; p < FT_P; ++p) {
+                const int yy = p / FT_S + t / 3 - 1, xx = p % FT_S + t % 3 - 1;
+                const float a1 = (yy >= 0 && yy < FT_S && xx >= 0 && xx < FT_S) ? fl_bf16_round(fmaxf(S.z1[ci][yy * FT_S + xx], 0.f)) : 0.f;
+                s = fmaf(S.z2[o][p], a1, s);
+            }
+            atomicAdd(&grad[OW2 + i], s);
+        } else {
+            const int o = i - 2304;
+            for (int p = 0; p < FT_P; ++p) s += S.z2[o][p];
+            atomicAdd(&grad[OB2 + o], s);
+        }
+    }
+    __syncthreads();
+    // dz1 = (conv2 transposed applied to dz2) where z1 > 0, in place of z1
+    for (int i = threadIdx.x; i < 16 * FT_P; i += FT_THREADS) {
+        const int ci = i / FT_P, p = i % FT_P, py = p / FT_S, px = p % FT_S;
+        float d = 0.f;
+        if (S.z1[ci][p] > 0.f)
+            for (int o = 0; o < 16; ++o)
+                for (int t = 0; t < 9; ++t)
+                    d = fmaf(S.th[OW2 + (o * 16 + ci) * 9 + t], crop_at(S.z2[o], py - (t / 3 - 1), px - (t % 3 - 1)), d);
+        S.z1[ci][p] = d;
+    }
+    __syncthreads();
+    // conv1 weights and biases
+    for (int i = threadIdx.x; i < 16 * 2 * 9 + 16; i += FT_THREADS) {
+        float s = 0.f;
+        if (i < 288) {
+            const int o = i / 18, ci = (i / 9) % 2, t = i % 9;
+            for (int p = 0; p < FT_P; ++p)
+                s = fmaf(S.z1[o][p], crop_at(S.x[ci], p / FT_S + t / 3 - 1, p % FT_S + t % 3 - 1), s);
+            atomicAdd(&grad[OW1 + i], s);
+        } else {
+            const int o = i - 288;
+            for (int p = 0; p < FT_P; ++p) s += S.z1[o][p];
+            atomicAdd(&grad[OB1 + o], s);
+        }
+    }
+}
+
+// Adam on the FP32 master weights with the gradient sums divided by the loss pixels;
+// grad is left holding the mean gradient.
+__global__ void k_fill_adam(float *theta, float *m, float *v, float *grad, const double *acc, unsigned step,
+                            float lr, float b1, float b2, float eps)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= FILL_NPARAMS) return;
+    const double n = acc[1];
+    const float g = n > 0.0 ? (float)((double)grad[i] / n) : 0.f;
+    grad[i] = g;
+    if (lr <= 0.f) return;
+    const float mi = b1 * m[i] + (1.f - b1) * g;
+    const float vi = b2 * v[i] + (1.f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / (1.f - powf(b1, (float)step));
+    const float vh = vi / (1.f - powf(b2, (float)step));
+    theta[i] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+cudaError_t launch_fill(const FillParams &fp, const FillIO &io, cudaStream_t s, unsigned long long &nl);
+
+cudaError_t launch_fill_readout(const FillParams &fp, const KParams &kp, const Bufs &b, float *out, cudaStream_t s,
+                                unsigned long long &nl)
+{
+    FillIO io{};
+    io.from_handle = 1;
+    io.ctrl = b.ctrl;
+    io.L = b.L;
+    io.last_pix = b.last_pix;
+    io.out = out;
+    io.err = &b.ctrl->error;
+    io.W = kp.W;
+    io.H = kp.H;
+    return launch_fill(fp, io, s, nl);
+}
+
+size_t fill_smem_bytes() { return sizeof(FillSmem); }
+size_t fill_train_smem_bytes() { return sizeof(TrainSmem); }
+
+cudaError_t launch_fill(const FillParams &fp, const FillIO &io, cudaStream_t s, unsigned long long &nl)
+{
+    nl += 1;
+    static std::atomic<unsigned long long> attr_done{0};
+    if (cudaError_t e = smem_attr_once(attr_done, k_fill, sizeof(FillSmem))) return e;
+    const int units = ((int)((io.W + FL_OC - 1) / FL_OC)) * ((int)((io.H + FL_R - 1) / FL_R));
+    const int grid = std::min(grid_for(1), units);
+    if (cudaError_t e = launch_pdl(k_fill, grid, FL_THREADS, sizeof(FillSmem), s, fp, io)) return e;
+    return cudaGetLastError();
+}
+
+}  // namespace fibar
+
+using namespace fibar;
+
+namespace {
+
+unsigned short host_bf16_bits(float v)
+{
+    unsigned u;
+    memcpy(&u, &v, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return (unsigned short)(u >> 16);  // inf / nan: truncate
+    return (unsigned short)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+
+float host_bf16(float v)
+{
+    const unsigned u = (unsigned)host_bf16_bits(v) << 16;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+}  // namespace
+
+namespace fibar {
+
+// Kernel parameters of the network from theta (W1, b1, W2, b2, W3, b3; FP32): weights
+// rounded to BF16, W2 packed as the per-tap B operands.
+int pack_fill_params(const float *theta, FillParams *fp)
+{
+    for (int i = 0; i < FILL_NPARAMS; ++i)
+        if (!isfinite(theta[i])) return FIBAR_EINVAL;
+    memset(fp, 0, sizeof(*fp));
+    for (int i = 0; i < 288; ++i) fp->w1[i] = host_bf16(theta[OW1 + i]);
+    for (int i = 0; i < 16; ++i) fp->b1[i] = theta[OB1 + i];
+    for (int i = 0; i < 16; ++i) fp->b2[i] = theta[OB2 + i];
+    for (int i = 0; i < 144; ++i) fp->w3[i] = host_bf16(theta[OW3 + i]);
+    fp->b3 = theta[OB3];
+    unsigned short *w2 = reinterpret_cast<unsigned short *>(fp->w2);
+    for (int co = 0; co < 16; ++co)
+        for (int ci = 0; ci < 16; ++ci)
+            for (int t = 0; t < 9; ++t) {
+                // tap t: row co (16 bytes per row within a K half), K half ci / 8 at +256 B
+                const size_t byte = (size_t)t * 512 + (ci / 8) * 256 + co * 16 + (ci % 8) * 2;
+                w2[byte / 2] = host_bf16_bits(theta[OW2 + (co * 16 + ci) * 9 + t]);
+            }
+    return FIBAR_OK;
+}
+
+}  // namespace fibar
+
+extern "C" int fibar_fill_set_weights(fibar_t *h, const float *theta, size_t n)
+{
+    if (!h) return FIBAR_EINVAL;
+    if (!theta) {
+        delete h->fill;
+        h->fill = nullptr;
+        return FIBAR_OK;
+    }
+    if (n != (size_t)FILL_NPARAMS) {
+        h->err = "fill_set_weights: expected " + std::to_string(FILL_NPARAMS) + " parameters";
+        return FIBAR_EINVAL;
+    }
+    FillParams fp;
+    if (pack_fill_params(theta, &fp) != FIBAR_OK) {
+        h->err = "fill_set_weights: every parameter must be finite";
+        return FIBAR_EINVAL;
+    }
+    if (!h->fill) h->fill = new (std::nothrow) FillParams;
+    if (!h->fill) return FIBAR_ENOMEM;
+    *h->fill = fp;
+    return FIBAR_OK;
+}
+
+extern "C" int fibar_fill_features(fibar_t *h, float *x, uint8_t *stale, void *cuda_stream)
+{
+    if (!h || !x) return FIBAR_EINVAL;
+    if (((uintptr_t)x & 3) != 0) {
+        h->err = "fill_features: misaligned output";
+        return FIBAR_EINVAL;
+    }
+    if (!h->kp.spatial) {
+        h->err = "fill_features: the handle has no stale-pixel detector (spatial_filter = 0)";
+        return FIBAR_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    k_fill_features<<<grid_for(4), 256, 0, s>>>(h->b.ctrl, h->b.L, h->b.last_pix, h->W, h->H, x, stale);
+    h->launches += 1;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        h->err = std::string("fill_features: ") + cudaGetErrorString(e);
+        return FIBAR_ECUDA;
+    }
+    return FIBAR_OK;
+}
+
+extern "C" int fibar_fill_forward(const float *theta, const float *x, const uint8_t *stale, uint32_t W, uint32_t H,
+                                  float *out, void *cuda_stream)
+{
+    if (!theta || !x || !stale || !out || W == 0 || H == 0 || (unsigned long long)W * H > (1ull << 24))
+        return FIBAR_EINVAL;
+    if (((uintptr_t)x & 3) != 0 || ((uintptr_t)out & 3) != 0) return FIBAR_EINVAL;
+    FillParams fp;
+    if (pack_fill_params(theta, &fp) != FIBAR_OK) return FIBAR_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    unsigned *err = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&err, sizeof(unsigned), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return FIBAR_ENOMEM;
+    }
+    e = cudaMemsetAsync(err, 0, sizeof(unsigned), s);
+    FillIO io{};
+    io.from_handle = 0;
+    io.x = x;
+    io.stale = stale;
+    io.out = out;
+    io.err = err;
+    io.W = W;
+    io.H = H;
+    unsigned long long nl = 0;
+    if (e == cudaSuccess) e = launch_fill(fp, io, s, nl);
+    unsigned herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(err, s);
+    if (e != cudaSuccess) return FIBAR_ECUDA;
+    return herr ? FIBAR_ETIMEOUT : FIBAR_OK;
+}
+
+extern "C" int fibar_fill_train_step(const float *X, const float *T, const uint8_t *M, uint32_t W, uint32_t H,
+                                     uint32_t n_frames, const int32_t *crops, uint32_t n_crops, float *theta,
+                                     float *m, float *v, float *grad, uint32_t step, float lr, double *loss_acc,
+                                     void *cuda_stream)
+{
+    if (!X || !T || !M || !crops || !theta || !m || !v || !grad || !loss_acc || W < FT_S || H < FT_S ||
+        n_frames == 0 || n_crops == 0 || n_crops > 65535 || step == 0)
+        return FIBAR_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    static std::atomic<unsigned long long> attr_done{0};
+    if (cudaError_t e = smem_attr_once(attr_done, k_fill_train, sizeof(TrainSmem))) return FIBAR_ECUDA;
+    cudaError_t e = cudaMemsetAsync(grad, 0, FILL_NPARAMS * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(loss_acc, 0, 3 * sizeof(double), s);
+    if (e != cudaSuccess) return FIBAR_ECUDA;
+    k_fill_train<<<n_crops, FT_THREADS, sizeof(TrainSmem), s>>>(X, T, M, W, H, n_frames, crops, theta, grad, loss_acc);
+    k_fill_adam<<<(FILL_NPARAMS + 255) / 256, 256, 0, s>>>(theta, m, v, grad, loss_acc, step, lr, 0.9f, 0.999f, 1e-8f);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? FIBAR_OK : FIBAR_ECUDA;
+}

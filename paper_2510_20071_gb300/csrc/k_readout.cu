@@ -184,7 +184,7 @@ cudaError_t launch_readout(const KParams &kp, const Bufs &b, float *out, cudaStr
                            unsigned long long &nl)
 {
     nl += 1;
-    if (kp.spatial && kp.blur_mode == 1) {
+    if (kp.spatial && kp.blur_mode >= 1) {  // S2, and the learned fill's Gaussian fallback
         dim3 grid((kp.W + RB_X - 1) / RB_X, (kp.H + RB_TY - 1) / RB_TY);
         if (cudaError_t e_ = launch_pdl(k_readout_s2, grid, RB_X * RB_Y, 0, s, kp, b.ctrl, b.L, b.last_pix, out)) return e_;
     } else {
