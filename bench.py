@@ -39,7 +39,12 @@ UNIT = "Mevents/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) per launch of the stage's kernel, from one ncu capture of the
 # current kernel on this workload; a stage missing here has no capture of its current code.
-DRAM_TRAFFIC = {"det_pass1": 16.99e6, "walk": None, "decode": None, "det_counts": None}  # None: changed since the capture
+# Cold-cache ncu capture (caches flushed before each launch), summed over the stage's kernels.
+DRAM_TRAFFIC = {
+    "s2": {"decode": 16.80e6, "sort": 8.03e6, "walk": 65.51e6, "det_counts": 41.01e6, "det_pass1": 16.97e6,
+           "det_pass2": 11.67e6, "det_fix": 0.02e6, "readout": 11.07e6, "commit": 0.01e6},
+    "s1": {"walk": 100.08e6, "s1_blur": 164.03e6},
+}
 
 
 MODE_PARAMS = {"s2": dict(spatial_filter=1, blur_mode=1), "s1": dict(spatial_filter=1, blur_mode=0),
@@ -386,6 +391,163 @@ def run_pan(args, rank, world, local):
         print(json.dumps(result), flush=True)
 
 
+FILL_TRAIN_SEEDS = [101, 102, 103]   # training streams (the benchmark stream, seed 1, is held out)
+FILL_TRAIN_STEPS = 800
+FILL_BATCH = 512
+
+
+def run_fill(args, rank, world, local):
+    """Learned stale-pixel fill (blur_mode 2) on the benchmark stream.
+
+    Training: 1280x720 Perlin streams of seeds 101-103 (3 read-outs each after 2 of queue
+    start-up), FILL_TRAIN_STEPS Adam steps of FILL_BATCH 24x24 crops through
+    fibar_fill_train_step.  Evaluation: RMSE over the stale pixels of 6 read-outs of the
+    held-out benchmark stream (seed 1) against the simulator's log intensity in L units,
+    for the learned fill, the Gaussian (S2) and no fill.  Timed region: K steps of the
+    benchmark stream (as the headline) with the learned-fill read-out; `value` = events/s.
+    The fill kernel's time per read-out comes from the stage pass, beside the S2 read-out's."""
+    import numpy as np
+    import torch
+    import eventsim
+    from paper_2510_20071_gb300 import Fibar
+    from paper_2510_20071_gb300 import fill as FL
+
+    t0 = time.time()
+    train = FL.Frames.concat([FL.collect_frames(W, H, 5 * READ_EVERY, seed=s) for s in FILL_TRAIN_SEEDS])
+    held = FL.collect_frames(W, H, 8 * READ_EVERY, seed=1 + rank)
+    log(f"[rank {rank}] frames: {train.n} training, {held.n} held out ({time.time() - t0:.1f} s)")
+    theta, train_s, hist = FL.train(train, FILL_TRAIN_STEPS, batch=FILL_BATCH, lr=3e-3, seed=rank, log_every=100)
+    quality = FL.evaluate(theta, held)
+    del train, held
+
+    n_stage = min(args.steps, 20)
+    n_total = args.warmup + args.steps + n_stage
+    cfg = dict(eventsim.CONFIGS[CONFIG_NAME])
+    cfg["seed"] += rank
+    ev = eventsim.simulate(cfg.pop("W"), cfg.pop("H"), n_total * READ_EVERY + PACKET, device=f"cuda:{local}",
+                           **{k: v for k, v in cfg.items() if k != "n_events"})
+    plan = step_plan(n_total, ev[:, 1].cpu())
+    stream = torch.cuda.current_stream()
+    out = torch.empty((H, W), dtype=torch.float32, device=ev.device)
+    w0, w1 = args.warmup, args.warmup + args.steps
+
+    def handle(mode):
+        f = Fibar(W, H, stream=stream, c_on=0.2, c_off=0.2, spatial_filter=1, blur_mode=mode)
+        if mode == 2:
+            f.set_fill_weights(theta)
+        return f
+
+    f = handle(2)
+    run_steps(f, ev, plan[:w0], out)
+    st0 = f.stats()
+    first = torch.empty_like(out)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.4)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i, step in enumerate(plan[w0:w1]):
+        run_steps(f, ev, [step], first if i == 0 else out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    time.sleep(0.3)
+    clocks = sampler.stop()
+    st = f.stats()
+    applied = st["events_applied"] - st0["events_applied"]
+    launches = st["kernel_launches"] - st0["kernel_launches"]
+    f.set_timing(True)
+    f.stage_times(reset=True)
+    run_steps(f, ev, plan[w1:], out)
+    fill_stages = f.stage_times(reset=True)
+    f.close()
+    g = handle(1)
+    run_steps(g, ev, plan[:w1], out)
+    g.set_timing(True)
+    g.stage_times(reset=True)
+    run_steps(g, ev, plan[w1:], out)
+    s2_stages = g.stage_times(reset=True)
+    g.close()
+    fill_ms = fill_stages["readout"] / max(fill_stages["calls"], 1)
+    s2_ms = s2_stages["readout"] / max(s2_stages["calls"], 1)
+
+    ms_max, total, value = whole_job(ms, float(applied), world)
+    # conv2 on the tensor cores: 2 x 16 x 144 FLOP per pixel, 10/8 rows and 128/126 columns
+    # per output pixel computed (tile halos); the conv1 / conv3 FMAs run on CUDA cores
+    tc_flop = 2.0 * 16 * 144 * W * H
+    tc_tflops = tc_flop / (fill_ms / 1e3) / 1e12
+    peak_tf, peak_kind = load_tensor_peak()
+    hbm, hbm_kind = load_peaks()
+    fill_bytes = (4 + 8 + 4) * W * H   # L and last event read, image written
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 state, bf16 weights / fp32 accumulation (fill)",
+        "data": "synthetic (seeded contrast-threshold simulator); fill trained on seeds 101-103, scored on seed 1",
+        "config": {"workload": WORKLOAD, "mode": "learned stale-pixel fill (3x3 conv 2-16-16-1, blur_mode 2)",
+                   "train_frames": 3 * len(FILL_TRAIN_SEEDS), "train_steps": FILL_TRAIN_STEPS,
+                   "train_batch": FILL_BATCH, "crop": FL.CROP, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2: each step reads a fresh 16 MB slice of the stream"},
+        "fill": {"rmse_learned": round(quality["learned"], 5), "rmse_gaussian": round(quality["gaussian"], 5),
+                 "rmse_no_fill": round(quality["none"], 5), "scored_pixels": quality["pixels"],
+                 "what": "RMSE over stale pixels of 6 held-out read-outs against the simulator's log intensity "
+                         "mapped into L units (per-frame least squares over the active pixels)",
+                 "train_seconds": round(train_s, 3), "train_loss": hist,
+                 "fill_readout_ms": round(fill_ms, 5), "gaussian_readout_ms": round(s2_ms, 5)},
+        "roofline": {"bound": "tensor", "kernel": "k_fill (conv2 on tcgen05)", "achieved": round(tc_tflops, 2),
+                     "peak": peak_tf, "unit": "TFLOP/s", "frac": round(tc_tflops / peak_tf, 5), "traffic": None,
+                     "peak_kind": peak_kind,
+                     "hbm_gbs": round(fill_bytes / (fill_ms / 1e3) / 1e9, 1), "hbm_peak": hbm,
+                     "alg": "2 x 16 x 144 FLOP per pixel on the tensor cores; 16 B per pixel of HBM"},
+        "stages_ms_per_step": {k: round(v / max(fill_stages["calls"], 1), 5) for k, v in fill_stages.items()
+                               if k != "calls"},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["parity"] = fill_parity(ev, plan[:w0 + 1], theta, first.cpu().numpy())
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def fill_parity(ev, plan, theta, gpu_img):
+    """The first timed learned-fill image against the event oracle's state (same packets)
+    passed through the fill oracle; bound as in the fill's parity tests (FP32 state of L
+    propagated through the network, FP32 accumulation, rare BF16 rounding flips)."""
+    import numpy as np
+    import oracle
+    from oracle import learned_fill as lf
+    oracle.build()
+    o = oracle.Oracle(W, H, c_on=0.2, c_off=0.2, spatial_filter=1, blur_mode=1)
+    cpu = ev[:plan[-1][0][-1][1]].cpu()
+    for pk, t in plan:
+        for lo, hi in pk:
+            o.push(cpu[lo:hi])
+        o.readout(t)
+    st = o.state()
+    o.close()
+    L = st["L"].reshape(H, W)
+    age = lf.age_feature(st["k"], st["q"], st["last"]).reshape(H, W)
+    stale = lf.stale_mask(st["h"], st["last"]).reshape(H, W)
+    th = np.asarray(theta, dtype=np.float64)
+    ref = np.where(stale, lf.forward(th, np.stack([L, age]))["y"], L)
+    err = np.abs(gpu_img.astype(np.float64) - ref)
+    return {"read_outs": 1, "max_abs_err": float(err.max()), "p999_abs_err": float(np.quantile(err, 0.999)),
+            "frac_within_1e-3": float(np.mean(err <= 1e-3)), "pass": bool(np.mean(err <= 1e-3) >= 0.99),
+            "what": "first timed learned-fill image against the FP64 event oracle's state through the FP64 "
+                    "fill oracle"}
+
+
+def load_tensor_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
 CALIB_EVENTS = 100_000_000
 
 
@@ -467,9 +629,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stream-events", type=int, default=None,
                     help="simulate a shorter stream (profiling runs); default: the 200 M workload")
-    ap.add_argument("--workload", default="stream", choices=["stream", "pan", "batch32", "calib"],
+    ap.add_argument("--workload", default="stream", choices=["stream", "pan", "fill", "batch32", "calib"],
                     help="stream: one 1280x720 stream (the headline); pan: the bursty 1280x720 pan "
-                         "stream at three packet sizes; batch32: 32 mixed streams served in concurrent "
+                         "stream at three packet sizes; fill: the learned stale-pixel fill; batch32: 32 mixed streams served in concurrent "
                          "batches; calib: relative thresholds of a 640x480 recording")
     ap.add_argument("--batch-seconds", type=float, default=0.2,
                     help="batch32: stream time simulated per stream")
@@ -497,6 +659,8 @@ def main():
         return run_calib(args, rank, world, local)
     if args.workload == "pan":
         return run_pan(args, rank, world, local)
+    if args.workload == "fill":
+        return run_fill(args, rank, world, local)
     from paper_2510_20071_gb300 import Fibar
 
     n_lat = min(args.steps, 50)     # read-out latency pass
@@ -619,7 +783,8 @@ def main():
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2: each step reads a fresh 16 MB slice of the 3.2 GB stream"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": DRAM_TRAFFIC.get(dom),
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": DRAM_TRAFFIC.get(args.mode, {}).get(dom),
                      "peak_kind": peak_kind,
                      "whole_step_gbs": round(whole_gbs, 1),
                      "whole_step_frac": round(whole_gbs / peak, 4),

@@ -43,7 +43,9 @@ constexpr int FL_XC = FL_M + 4;    // input columns
 constexpr int FL_A2R = FL_R + 2;   // a2 rows
 constexpr int FL_A1R = FL_R + 4;   // a1 rows
 constexpr int FL_XR = FL_R + 6;    // input rows
-constexpr int FL_THREADS = 256;
+constexpr int FL_THREADS = 512;
+constexpr int FL_XN = FL_XR * FL_XC;                        // input positions per unit
+constexpr int FL_XITER = (FL_XN + FL_THREADS - 1) / FL_THREADS;
 constexpr unsigned FL_TMEM_COLS = 256;                      // >= 16 columns x 10 rows
 constexpr unsigned FL_PLANE = FL_A1C * 16;                  // one K plane of an a1 row
 constexpr unsigned FL_A1ROW = 2 * FL_PLANE;                 // bytes per a1 row
@@ -166,34 +168,58 @@ __global__ void __launch_bounds__(FL_THREADS, 1) k_fill(FillParams fp, FillIO io
 
     for (int u = blockIdx.x; u < units && !failed; u += gridDim.x) {
         const int y0 = (u / nseg) * FL_R, x0 = (u % nseg) * FL_OC;
-        // inputs: rows y0-3 .. y0+10, columns x0-3 .. x0+128 (zero outside the image)
-        for (int i = threadIdx.x; i < FL_XR * FL_XC; i += FL_THREADS) {
-            const int r = i / FL_XC, c = i % FL_XC;
-            const int gy = y0 - 3 + r, gx = x0 - 3 + c;
-            float v0 = 0.f, v1 = 0.f;
-            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-                const size_t p = (size_t)gy * W + gx;
-                if (io.from_handle) {
-                    v0 = io.L[p];
-                    const unsigned long long lp = io.last_pix[p];
-                    if (lp == NONE64) {
-                        v1 = FL_AGE_MAX;
+        // inputs: rows y0-3 .. y0+10, columns x0-3 .. x0+128 (zero outside the image); all
+        // of a thread's global loads are issued before any is used
+        {
+            float v0[FL_XITER];
+            unsigned long long lp[FL_XITER];
+            float v1x[FL_XITER];
+            unsigned char sx[FL_XITER];
+#pragma unroll
+            for (int it = 0; it < FL_XITER; ++it) {
+                const int i = threadIdx.x + it * FL_THREADS;
+                const int r = i / FL_XC, c = i % FL_XC;
+                const int gy = y0 - 3 + r, gx = x0 - 3 + c;
+                const bool in = i < FL_XN && gy >= 0 && gy < H && gx >= 0 && gx < W;
+                const size_t p = in ? (size_t)gy * W + gx : 0;
+                v0[it] = 0.f;
+                v1x[it] = 0.f;
+                lp[it] = NONE64;
+                sx[it] = 0;
+                if (in) {
+                    if (io.from_handle) {
+                        v0[it] = io.L[p];
+                        lp[it] = io.last_pix[p];
                     } else {
-                        const unsigned long long gap = k_now - lp;
-                        v1 = gap >= 4ull * q ? FL_AGE_MAX : (float)gap / (float)q;
+                        v0[it] = io.x[p];
+                        v1x[it] = io.x[(size_t)W * H + p];
+                        sx[it] = io.stale[p];
                     }
-                    const int orow = gy - y0, ocol = gx - x0;
-                    if (orow >= 0 && orow < FL_R && ocol >= 0 && ocol < FL_OC)
-                        S.stale[orow][ocol] = (lp != NONE64 && lp < h) ? 1 : 0;
-                } else {
-                    v0 = io.x[p];
-                    v1 = io.x[(size_t)W * H + p];
-                    const int orow = gy - y0, ocol = gx - x0;
-                    if (orow >= 0 && orow < FL_R && ocol >= 0 && ocol < FL_OC) S.stale[orow][ocol] = io.stale[p];
                 }
             }
-            S.x[0][r][c] = v0;
-            S.x[1][r][c] = v1;
+#pragma unroll
+            for (int it = 0; it < FL_XITER; ++it) {
+                const int i = threadIdx.x + it * FL_THREADS;
+                if (i >= FL_XN) break;
+                const int r = i / FL_XC, c = i % FL_XC;
+                const int gy = y0 - 3 + r, gx = x0 - 3 + c;
+                const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+                float v1 = v1x[it];
+                unsigned char st = sx[it];
+                if (in && io.from_handle) {
+                    if (lp[it] == NONE64) {
+                        v1 = FL_AGE_MAX;
+                    } else {
+                        const unsigned long long gap = k_now - lp[it];
+                        v1 = gap >= 4ull * q ? FL_AGE_MAX : (float)gap / (float)q;
+                    }
+                    st = (lp[it] != NONE64 && lp[it] < h) ? 1 : 0;
+                }
+                const int orow = gy - y0, ocol = gx - x0;
+                if (in && orow >= 0 && orow < FL_R && ocol >= 0 && ocol < FL_OC) S.stale[orow][ocol] = st;
+                S.x[0][r][c] = v0[it];
+                S.x[1][r][c] = in ? v1 : 0.f;
+            }
         }
         __syncthreads();
         // conv1 -> a1 (BF16, canonical layout); zero outside the image
@@ -258,7 +284,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1) k_fill(FillParams fp, FillIO io
         {
             const int px = 32 * (warp & 3) + lane;
             const int gx = x0 - 1 + px;
-            for (int r = (int)(warp >> 2); r < FL_A2R; r += 2) {
+            for (int r = (int)(warp >> 2); r < FL_A2R; r += FL_THREADS / 128) {
                 float v[16];
                 fl_tmem_ld16(tmem + ((32u * (warp & 3)) << 16) + 16u * r, v);
                 const int gy = y0 - 1 + r;
@@ -276,14 +302,15 @@ __global__ void __launch_bounds__(FL_THREADS, 1) k_fill(FillParams fp, FillIO io
             if (gy >= H || gx >= W) continue;
             float v = S.x[0][o + 3][oc + 3];
             if (S.stale[o][oc]) {
-                float acc = fp.b3;
+                float acc[3] = {fp.b3, 0.f, 0.f};  // one chain per kernel row
 #pragma unroll
                 for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) acc = fmaf(fp.w3[c * 9 + dy * 3 + dx], S.a2[o + dy][oc + dx][c], acc);
-                v = acc;
+                        for (int c = 0; c < 16; ++c)
+                            acc[dy] = fmaf(fp.w3[c * 9 + dy * 3 + dx], S.a2[o + dy][oc + dx][c], acc[dy]);
+                v = (acc[0] + acc[1]) + acc[2];
             }
             io.out[(size_t)gy * W + gx] = v;
         }
