@@ -157,9 +157,13 @@ void fibar_default_params(fibar_params_t *p);
 int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *p, fibar_t **out);
 
 /* Queue n events for the next read-out (Sec. 1: events arrive in packets).
- *   on_device = 0: `ev` is host memory; it is copied to the device on `cuda_stream`
- *                  (pageable buffers may be reused on return; page-locked buffers once
- *                  the stream has passed the copy).
+ *   on_device = 0: `ev` is host memory; it is copied to the device on an internal copy
+ *                  stream of the handle, into one of two staging buffers (the next
+ *                  read-out's packets go to the other one, so their copy overlaps the
+ *                  current read-out); the next read-out or flush on `cuda_stream` waits
+ *                  for the copy.  Pageable buffers may be reused on return; page-locked
+ *                  buffers once that read-out has completed.  The first host push
+ *                  allocates the second staging buffer (16 bytes x max_pending).
  *   on_device = 1: `ev` is device memory (16-byte aligned) read in place by the next
  *                  fibar_readout() or fibar_flush(); it must stay valid and unchanged
  *                  until that call's work has completed on the stream.
@@ -187,6 +191,19 @@ int fibar_push_events_many(fibar_t *h, const fibar_event_t *const *evs, const si
  *   on_device = 0: out is host memory; the call waits for the result.
  * Errors: EINVAL, EORDER (t_us < previous read-out time), ECUDA, ETIMEOUT. */
 int fibar_readout(fibar_t *h, uint64_t t_us, float *out, int on_device, void *cuda_stream);
+
+/* fibar_readout into a HOST buffer without waiting: queues the read-out and the
+ * device-to-host copy of the image into `out` (W*H floats; page-locked memory makes the
+ * copy asynchronous) on cuda_stream and returns.  The image is in `out` once the stream
+ * has passed the copy (fibar_wait, or an event recorded on the stream after this call).
+ * The paper has no counterpart; this lets a caller overlap the next packets' upload and
+ * read-out with the current one.  Errors: EINVAL, EORDER, ECUDA (bounded device waits
+ * that gave up are reported by fibar_wait). */
+int fibar_readout_host_async(fibar_t *h, uint64_t t_us, float *out, void *cuda_stream);
+
+/* Wait for the work queued on cuda_stream (synchronises it); ETIMEOUT if a bounded device
+ * wait of the last committed read-out or flush gave up.  Errors: EINVAL, ECUDA, ETIMEOUT. */
+int fibar_wait(fibar_t *h, void *cuda_stream);
 
 /* Read out n handles together: for every i, what fibar_readout(hs[i], t_us[i], outs[i],
  * 1, ...) does, with the work of different handles running concurrently on the device.

@@ -26,7 +26,8 @@ EXPORTED = ["fibar_default_params", "fibar_create", "fibar_push_events", "fibar_
             "fibar_stage_times", "fibar_last_error", "fibar_destroy", "fibar_queue_counts_noalloc",
             "fibar_readout_batch", "fibar_memory_bytes", "fibar_relative_thresholds",
             "fibar_set_pixel_gain", "fibar_debug_wait_timeout", "fibar_push_events_many",
-            "fibar_fill_set_weights", "fibar_fill_features", "fibar_fill_forward", "fibar_fill_train_step"]
+            "fibar_fill_set_weights", "fibar_fill_features", "fibar_fill_forward", "fibar_fill_train_step",
+            "fibar_readout_host_async", "fibar_wait"]
 
 FIBAR_FILL_NPARAMS = 2769
 
@@ -123,6 +124,10 @@ def load_library(build_if_missing: bool = True):
             lib.fibar_debug_wait_timeout.restype = C.c_int
             lib.fibar_push_events_many.argtypes = [vp, C.POINTER(vp), C.POINTER(C.c_size_t), C.c_size_t, C.c_int, vp]
             lib.fibar_push_events_many.restype = C.c_int
+            lib.fibar_readout_host_async.argtypes = [vp, C.c_uint64, vp, vp]
+            lib.fibar_readout_host_async.restype = C.c_int
+            lib.fibar_wait.argtypes = [vp, vp]
+            lib.fibar_wait.restype = C.c_int
             lib.fibar_fill_set_weights.argtypes = [vp, vp, C.c_size_t]
             lib.fibar_fill_set_weights.restype = C.c_int
             lib.fibar_fill_features.argtypes = [vp, vp, vp, vp]
@@ -226,6 +231,14 @@ def fibar_debug_wait_timeout(h, max_spins: int, stream: int) -> int:
     return load_library().fibar_debug_wait_timeout(h, max_spins, stream)
 
 
+def fibar_readout_host_async(h, t_us: int, out_ptr: int, stream: int) -> int:
+    return load_library().fibar_readout_host_async(h, t_us, out_ptr, stream)
+
+
+def fibar_wait(h, stream: int) -> int:
+    return load_library().fibar_wait(h, stream)
+
+
 def fibar_fill_set_weights(h, theta_ptr, n: int) -> int:
     return load_library().fibar_fill_set_weights(h, theta_ptr, n)
 
@@ -298,6 +311,8 @@ class Fibar:
             self._keep.append(ev)
         else:
             self._check(fibar_push_events(self.h, ev.data_ptr(), n, 0, self._s))
+            if ev.is_pinned():  # copied asynchronously: keep it until its read-out has run
+                self._keep.append(ev)
 
     def push_many(self, packets) -> None:
         """Push several packets in one call (``fibar_push_events_many``): all CUDA or all CPU
@@ -312,7 +327,7 @@ class Fibar:
                 raise TypeError("packets must be contiguous (n, 2) int64 tensors on one device type")
         self._check(fibar_push_events_many(self.h, [ev.data_ptr() for ev in packets],
                                            [ev.shape[0] for ev in packets], 1 if cuda else 0, self._s))
-        if cuda:
+        if cuda or packets[0].is_pinned():
             self._keep.extend(packets)
 
     def _rotate(self):
@@ -331,6 +346,20 @@ class Fibar:
         self._rotate()
         self._check(rc)
         return out
+
+    def readout_host_async(self, t_us: int, out) -> None:
+        """Queue the read-out at t_us and the copy of its image into ``out`` (a contiguous
+        float32 CPU tensor of W*H elements, pinned for an asynchronous copy); the image is
+        there once the stream has passed it (``wait``)."""
+        t = self.torch
+        if out.dtype != t.float32 or out.numel() != self.W * self.H or not out.is_contiguous() or out.is_cuda:
+            raise TypeError("out must be a contiguous float32 CPU tensor with W*H elements")
+        rc = fibar_readout_host_async(self.h, int(t_us), out.data_ptr(), self._s)
+        self._rotate()
+        self._check(rc)
+
+    def wait(self) -> None:
+        self._check(fibar_wait(self.h, self._s))
 
     def flush(self) -> None:
         rc = fibar_flush(self.h, self._s)

@@ -416,6 +416,13 @@ extern "C" void fibar_destroy(fibar_t *h)
     if (!h) return;
     cudaDeviceSynchronize();
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->copy_stream) {
+        cudaStreamDestroy(h->copy_stream);
+        cudaEventDestroy(h->ev_free[0]);
+        cudaEventDestroy(h->ev_free[1]);
+        cudaEventDestroy(h->ev_copied);
+        cudaFree(h->staging2);
+    }
     free_all(h);
     delete h->fill;
     delete h;
@@ -460,8 +467,28 @@ extern "C" int fibar_push_events(fibar_t *h, const fibar_event_t *ev, size_t n, 
     } else {
         if (h->staging_used + n > h->params.max_pending)
             return fail(h, FIBAR_ENOMEM, "push: host staging full; read out or flush first");
-        int4 *dst = h->b.staging + h->staging_used;
-        cudaError_t e = cudaMemcpyAsync(dst, ev, n * sizeof(fibar_event_t), cudaMemcpyHostToDevice, s);
+        if (!h->copy_stream) {
+            cudaError_t e = cudaMalloc((void **)&h->staging2, (size_t)h->params.max_pending * sizeof(int4));
+            if (e != cudaSuccess) {
+                h->staging2 = nullptr;
+                cudaGetLastError();
+                return fail(h, FIBAR_ENOMEM, "push: second host staging buffer");
+            }
+            e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_free[0], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_free[1], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_copied, cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(h, e, "push: copy stream");
+        }
+        int4 *buf = h->staging_cur ? h->staging2 : h->b.staging;
+        if (!h->copy_pending) {
+            // the decode that last read this buffer must have run
+            cudaError_t e = cudaStreamWaitEvent(h->copy_stream, h->ev_free[h->staging_cur], 0);
+            if (e != cudaSuccess) return cuda_fail(h, e, "push: wait for the staging buffer");
+            h->copy_pending = true;
+        }
+        int4 *dst = buf + h->staging_used;
+        cudaError_t e = cudaMemcpyAsync(dst, ev, n * sizeof(fibar_event_t), cudaMemcpyHostToDevice, h->copy_stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "push: host-to-device copy");
         if (!h->seg_ptr.empty() && h->seg_ptr.back() + h->seg_n.back() == dst) {
             h->seg_n.back() += (unsigned)n;
@@ -554,9 +581,24 @@ int process(fibar_t *h, unsigned long long t_read, float *out, cudaStream_t s)
     unsigned long long &nl = h->launches;
     StageMarks mk(h, s);
 
+    cudaError_t e = cudaSuccess;
+    if (h->copy_pending) {
+        // the read-out's host packets, copied on the internal stream
+        e = cudaEventRecord(h->ev_copied, h->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_copied, 0);
+        if (e != cudaSuccess) return cuda_fail(h, e, "wait for the host packets");
+    }
     mk.mark(FIBAR_STAGE_DECODE);
-    cudaError_t e = launch_decode(kp, b, T, h->sort_passes, s, nl);
+    e = launch_decode(kp, b, T, h->sort_passes, s, nl);
     if (e != cudaSuccess) return cuda_fail(h, e, "decode");
+    if (h->copy_pending) {
+        // the staging buffer is free again once the decode has run; the next host packets
+        // go to the other one
+        e = cudaEventRecord(h->ev_free[h->staging_cur], s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "staging event");
+        h->staging_cur ^= 1;
+        h->copy_pending = false;
+    }
     mk.mark(FIBAR_STAGE_SORT);
     e = launch_sort(kp, b, h->sort_passes, h->epoch, s, nl);
     h->epoch += SORT_MAX_PASSES;
@@ -638,6 +680,32 @@ extern "C" int fibar_readout(fibar_t *h, uint64_t t_us, float *out, int on_devic
         return check_device_error(h);
     }
     return FIBAR_OK;
+}
+
+extern "C" int fibar_readout_host_async(fibar_t *h, uint64_t t_us, float *out, void *cuda_stream)
+{
+    if (!h) return FIBAR_EINVAL;
+    if (!out) return fail(h, FIBAR_EINVAL, "readout_host_async: null output");
+    if (h->have_readout && t_us < h->last_readout)
+        return fail(h, FIBAR_EORDER, "readout: time earlier than the previous read-out");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int rc = process(h, t_us, h->b.out_staging, s);
+    if (rc) return rc;
+    h->have_readout = true;
+    h->last_readout = t_us;
+    h->readouts += 1;
+    cudaError_t e = cudaMemcpyAsync(out, h->b.out_staging, (size_t)h->kp.npix * sizeof(float),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "readout_host_async: device-to-host copy");
+    return FIBAR_OK;
+}
+
+extern "C" int fibar_wait(fibar_t *h, void *cuda_stream)
+{
+    if (!h) return FIBAR_EINVAL;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "wait: sync");
+    return h->commits ? check_device_error(h) : FIBAR_OK;
 }
 
 extern "C" int fibar_flush(fibar_t *h, void *cuda_stream)

@@ -210,6 +210,14 @@ struct fibar_s {
     unsigned int *snap_host;            // host view of Bufs::snap (written by k_commit)
     float *gain_buf;                    // per-pixel gains, allocated by the first fibar_set_pixel_gain
     fibar::FillParams *fill;            // learned-fill network (blur_mode 2), nullptr = Gaussian
+    // host packets: copied on an internal stream into one of two staging buffers, so that
+    // the copy for the next read-out overlaps the current one (created by the first host push)
+    int4 *staging2;                     // second staging buffer (b.staging is the first)
+    int staging_cur;                    // buffer the pending host packets go to
+    cudaStream_t copy_stream;
+    cudaEvent_t ev_free[2];             // recorded after the decode that read buffer i
+    cudaEvent_t ev_copied;              // the pending read-out's host packets have arrived
+    bool copy_pending;                  // host packets queued since the last read-out
     unsigned long long commits;         // read-outs and flushes launched
     unsigned long long pushed_since;    // records pushed since the last read-out or flush
     int carry_slot;

@@ -298,18 +298,25 @@ __global__ void __launch_bounds__(128) k_s1_blur(KParams kp, Bufs b)
         bool done = !active;
         unsigned spins = 0;
         float dv[9];  // published D of each tap's blur (the value and its flag in one word)
+        unsigned pending = 0;  // taps whose blur has not been seen published yet
 #pragma unroll
-        for (int t = 0; t < 9; ++t) dv[t] = 0.f;
+        for (int t = 0; t < 9; ++t) {
+            dv[t] = 0.f;
+            if (tp[t].bl != NOBLUR) pending |= 1u << t;
+        }
         while (__any_sync(0xFFFFFFFFu, !done)) {
             if (!done) {
-                bool ready = true;
+                // poll only the taps still pending: a published value never changes
 #pragma unroll
                 for (int t = 0; t < 9; ++t)
-                    if (tp[t].bl != NOBLUR) {
+                    if (pending >> t & 1u) {
                         const unsigned long long v = ld_acquire_u64b(&b.bval[tp[t].bl]);
-                        if ((unsigned)(v >> 32) != g.batch_no) ready = false;
-                        dv[t] = __uint_as_float((unsigned)v);
+                        if ((unsigned)(v >> 32) == g.batch_no) {
+                            dv[t] = __uint_as_float((unsigned)v);
+                            pending &= ~(1u << t);
+                        }
                     }
+                const bool ready = pending == 0;
                 if (ready) {
                     float acc = 0.f;
 #pragma unroll
@@ -326,6 +333,8 @@ __global__ void __launch_bounds__(128) k_s1_blur(KParams kp, Bufs b)
                 } else if (++spins > SPIN_LIMIT) {
                     atomicOr(&ctrl->error, ERR_S1_WAIT);
                     done = true;
+                } else {
+                    __nanosleep(32);  // back off: polls compete with the stores they wait for
                 }
             }
         }

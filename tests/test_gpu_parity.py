@@ -295,3 +295,35 @@ def test_config_perlin_pan_1280x720_prefix(oracle_mod, packet):
     assert stats["events_applied"] == n
     print(f"packet {packet}: max |diff| {worst:.2e}, walk pieces {stats['iir_walk_pieces']}, "
           f"scan pieces {stats['iir_scan_pieces']}, fixup steps {stats['detector_fix_steps']}")
+
+
+@pytest.mark.parametrize("mode", ["nsf", "s1", "s2"])
+def test_pinned_host_push_and_async_host_readout(oracle_mod, mode):
+    """Host packets from page-locked memory (copied on the handle's copy stream into two
+    alternating staging buffers) and fibar_readout_host_async images, waited for once at
+    the end: every image equals the oracle's."""
+    from paper_2510_20071_gb300 import Fibar
+    W, H, n = 64, 48, 40_000
+    ev = sim(W, H, n, seed=19, noise=0.01)
+    steps = plan_packets(n, 3_000, 7_000, ev)
+    p = dict(MODES[mode], c_on=0.2, c_off=0.2)
+    o_imgs, o_states = run_oracle(oracle_mod, W, H, ev, steps, **p)
+    host = ev.pin_memory()
+    bufs = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in o_imgs]
+    f = Fibar(W, H, **p)
+    r = 0
+    for st in steps:
+        if st[0] == "push":
+            f.push(host[st[1]:st[2]])
+        else:
+            f.readout_host_async(st[1], bufs[r])
+            r += 1
+    f.wait()
+    g_state = f.state()
+    f.close()
+    for i, (a, b) in enumerate(zip(o_imgs, bufs)):
+        assert np.abs(a - b.numpy()).max() <= 1e-4, i
+    assert g_state["k"] == o_states[-1]["k"]
+    if p.get("spatial_filter", 1):
+        for key in ["h", "q_targ", "n_ap", "n_at"]:
+            assert g_state[key] == o_states[-1][key]
