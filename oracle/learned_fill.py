@@ -12,14 +12,16 @@ Fill network (the read-out's masked fill, S2 mask):
                  k the events applied, last the global index of the pixel's last event,
                  q the queue length (the window of Sec. 4.2 is [k - q, k)); a pixel is
                  stale exactly when age > 1; a pixel without events has age = A_MAX
-  conv1   z1 = b1 + W1 * x  (2 -> 16 channels, 3x3, zero padding), a1 = relu(z1)
+  conv1   z1 = b1 + W1 * bf16(x)  (2 -> 16 channels, 3x3, zero padding), a1 = relu(z1)
   conv2   z2 = b2 + W2 * bf16(a1)  (16 -> 16), a2 = relu(z2)
-  conv3   y  = b3 + W3 * a2  (16 -> 1)
+  conv3   y  = b3 + W3 * bf16(a2)  (16 -> 1)
   output  out = y where the pixel is stale (had an event, none queued), L elsewhere
 "*" is a cross-correlation: (W * x)[c, i, j] = sum over ci, dy, dx in {0,1,2} of
-W[c, ci, dy, dx] x[ci, i + dy - 1, j + dx - 1], zero outside the image.  Weights are
-BF16 (W1, W2, W3 rounded to bfloat16, biases FP32); a1 enters conv2 rounded to bfloat16
-(a tensor-core operand); everything else is exact here (FP64).
+W[c, ci, dy, dx] x[ci, i + dy - 1, j + dx - 1], zero outside the image.  All three layers
+are tensor-core contractions with BF16 operands and FP32 accumulation: the weights (W1,
+W2, W3) and each layer's input (x, a1, a2) are rounded to bfloat16, biases stay FP32;
+everything else is exact here (FP64).  Outside the stale pixels the output is L itself
+(not its BF16 rounding).
 
 Training target (a reading: L is a high-passed log brightness, Eqs. 9-10 remove its DC,
 so it cannot be compared with the simulator's log intensity I directly): per frame, the
@@ -121,13 +123,15 @@ def forward(theta, x: np.ndarray, quantize: bool = True) -> dict:
     p = unflatten(theta)
     q = bf16 if quantize else (lambda v: np.asarray(v, dtype=np.float64))
     W1, W2, W3 = q(p["W1"]), q(p["W2"]), q(p["W3"])
-    z1 = conv3x3(x, W1, p["b1"])
+    xq = q(x)
+    z1 = conv3x3(xq, W1, p["b1"])
     a1 = np.maximum(z1, 0.0)
     a1q = q(a1)
     z2 = conv3x3(a1q, W2, p["b2"])
     a2 = np.maximum(z2, 0.0)
-    y = conv3x3(a2, W3, p["b3"])[0]
-    return dict(W1=W1, W2=W2, W3=W3, z1=z1, a1=a1, a1q=a1q, z2=z2, a2=a2, y=y)
+    a2q = q(a2)
+    y = conv3x3(a2q, W3, p["b3"])[0]
+    return dict(W1=W1, W2=W2, W3=W3, xq=xq, z1=z1, a1=a1, a1q=a1q, z2=z2, a2=a2, a2q=a2q, y=y)
 
 
 def fill_image(theta, L: np.ndarray, age: np.ndarray, stale: np.ndarray) -> np.ndarray:
@@ -163,7 +167,7 @@ def loss_and_grad(theta, xs, targets, masks, quantize: bool = True):
         r = np.where(m, f["y"] - t, 0.0)
         loss += float((r * r).sum()) / n
         gy = (2.0 / n) * r
-        da2, grads_W3, gb3 = conv3x3_backward(f["a2"], f["W3"], gy[None])
+        da2, grads_W3, gb3 = conv3x3_backward(f["a2q"], f["W3"], gy[None])
         grads["W3"] += grads_W3
         grads["b3"] += gb3
         dz2 = da2 * (f["z2"] > 0)
@@ -171,7 +175,7 @@ def loss_and_grad(theta, xs, targets, masks, quantize: bool = True):
         grads["W2"] += gW2
         grads["b2"] += gb2
         dz1 = da1 * (f["z1"] > 0)
-        _, gW1, gb1 = conv3x3_backward(x, f["W1"], dz1)
+        _, gW1, gb1 = conv3x3_backward(f["xq"], f["W1"], dz1)
         grads["W1"] += gW1
         grads["b1"] += gb1
     return loss, flatten(grads)

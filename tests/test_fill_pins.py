@@ -86,15 +86,21 @@ def test_backward_matches_finite_differences():
     assert abs(loss - ref) <= 1e-12 * max(1.0, ref)
 
 
-def test_quantized_forward_rounds_weights_and_a1_only():
+def test_quantized_forward_rounds_weights_and_layer_inputs_only():
     theta, xs, _, _ = _tiny_problem(4)
     f = lf.forward(theta, xs[0])
     p = lf.unflatten(theta)
     np.testing.assert_array_equal(f["W2"], lf.bf16(p["W2"]))
+    np.testing.assert_array_equal(f["xq"], lf.bf16(xs[0]))
     np.testing.assert_array_equal(f["a1q"], lf.bf16(np.maximum(f["z1"], 0)))
-    # with weights and b1 already bfloat16 and x = 0, a1 = relu(b1) is exact in bfloat16:
-    # rounding then changes nothing, so the rounded and unrounded passes agree exactly
-    q = {k: (lf.bf16(v) if k in ("W1", "W2", "W3", "b1") else v) for k, v in p.items()}
+    np.testing.assert_array_equal(f["a2q"], lf.bf16(np.maximum(f["z2"], 0)))
+    # with weights, b1, b2 already bfloat16 and x = 0: a1 = relu(b1) and a2 = relu(b2 + W2 * a1)
+    # - take b2 = 0 and a single nonzero W2 tap of 1 so that a2 is a1 moved - are exact in
+    # bfloat16; rounding then changes nothing, so the rounded and unrounded passes agree
+    q = {k: (lf.bf16(v) if k in ("W1", "W3", "b1") else v) for k, v in p.items()}
+    q["W2"] = np.zeros_like(p["W2"])
+    q["W2"][:, :, 1, 1] = np.eye(16)
+    q["b2"] = np.zeros(16)
     qt = lf.flatten(q)
     x = np.zeros_like(xs[0])
     np.testing.assert_array_equal(lf.forward(qt, x)["y"], lf.forward(qt, x, quantize=False)["y"])
