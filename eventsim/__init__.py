@@ -267,7 +267,9 @@ def simulate(W: int, H: int, n_events: int, *, scene: SceneSpec | str = "sine_ch
     steps = 0
     while count < n_signal:
         if scene.texture == "perlin_pan":
-            dt = min(dt, 0.05 / max(sc.pan_speed(t), 1e-3))
+            # at most 0.2 px of pan motion per sample: the step size adapts to the
+            # intensity change, but a segment's speed can jump at its start
+            dt = min(dt, 0.2 / max(sc.pan_speed(t), 1e-3))
         t1 = t + dt
         I = sc.log_intensity(t1)
         d = I - ref

@@ -185,10 +185,12 @@ struct Bufs {
 // Learned stale-pixel fill (k_fill.cu): network parameters as a kernel parameter.
 constexpr int FILL_NPARAMS = 2769;  // W1 16x2x3x3, b1 16, W2 16x16x3x3, b2 16, W3 1x16x3x3, b3 1
 struct FillParams {
-    uint4 w2[9 * 32];      // conv2 B operand per tap: 16 (co) x 16 (ci) BF16, K-major, no swizzle
-    float w1[16 * 18];     // conv1 [co][ci * 9 + tap], BF16 values
+    // B operands per dx: 48 (n) x 16 (k) BF16, K-major, no swizzle, n = 16 (2 - dy) + output
+    // channel: row n at 16 B, the second K half at +768 B, 1536 B per dx
+    uint4 w1[9 * 32];      // conv1: k = input channel (only 0, 1 used)
+    uint4 w2[9 * 32];      // conv2
+    uint4 w3[9 * 32];      // conv3: output channel 0 only (the other rows zero)
     float b1[16], b2[16];
-    float w3[16 * 9];      // conv3 [ci][tap], BF16 values
     float b3;
 };
 

@@ -7,21 +7,25 @@
 // Network (inputs per pixel: x0 = L, the filter output of Eq. 10, and x1 = the activity
 // age min(4, (k - last) / q), k the events applied, last the pixel's last event, q the
 // queue length; the queue of Sec. 4.2 is the window [k - q, k)):
-//   a1 = relu(b1 + W1 * x)        2 -> 16 channels   CUDA cores, FP32, BF16 weights
-//   a2 = relu(b2 + W2 * bf16(a1)) 16 -> 16           tcgen05.mma kind::f16, BF16 in, FP32 acc
-//   y  = b3 + W3 * a2             16 -> 1            CUDA cores, FP32, BF16 weights
+//   a1 = relu(b1 + W1 * bf16(x))   2 -> 16 channels
+//   a2 = relu(b2 + W2 * bf16(a1))  16 -> 16
+//   y  = b3 + W3 * bf16(a2)        16 -> 1
 //   out = y at stale pixels (had an event, none queued), L elsewhere
-// ("*" a 3x3 cross-correlation with zero padding at the image border).
+// ("*" a 3x3 cross-correlation with zero padding at the image border).  Every layer is a
+// tcgen05.mma kind::f16 contraction: BF16 weights and inputs, FP32 accumulation in TMEM.
 //
-// Inference kernel (k_fill): persistent, one CTA of 256 threads per SM, units of 8 output
-// rows x 126 output columns.  Per unit: the inputs of 14 x 132 pixels go to shared memory;
-// conv1 writes a1 for 12 x 130 pixels as BF16 in the tensor cores' canonical K-major
-// layout (no swizzle: two planes of 8 channels, one 16-byte row per pixel); conv2 is 90
-// MMAs of 128 x 16 x 16 (10 rows of 128 pixels, 9 taps each: the tap (dy, dx) is the a1
-// row r + dy read from pixel dx on, i.e. the descriptor's start moved by dx rows) into
-// 160 TMEM columns; the epilogue reads them back with tcgen05.ld (lane = pixel), adds
-// the bias, applies ReLU and stores a2 (FP32) to shared memory; conv3 and the mask
-// write the image.  Weights travel as a kernel parameter (constant bank).
+// Inference kernel (k_fill): persistent, one CTA of 512 threads per SM, units of 8 output
+// rows x 124 output columns, so that every layer's rows are 128 pixels (the MMA's M).  Per
+// unit: the inputs of 14 x 130 pixels go to shared memory as BF16 in the tensor cores'
+// canonical K-major layout without swizzle (one 16-byte row per pixel: L, age and six
+// zeros; the second K half of every input row is a shared block of zeros); each layer is
+// 9 MMAs of 128 x 16 x 16 per output row (tap (dy, dx): the input row r + dy read from
+// pixel dx on, i.e. the descriptor's start moved by dx rows), 108 + 90 + 72 per unit, issued
+// tap by tap across the rows (consecutive MMAs never share an accumulator) by one thread
+// into its own TMEM columns and completed through tcgen05.commit on an
+// mbarrier (bounded wait); the epilogues read TMEM with tcgen05.ld (lane = pixel), add the
+// bias, apply ReLU and store the next layer's BF16 tile (zero outside the image); the last
+// one writes the image.  conv3 has one real output: its B operand is padded to N = 16.
 //
 // Training (k_fill_train, k_fill_adam): one CTA per 24 x 24 crop runs the forward pass,
 // the loss gradient over the crop's interior stale pixels (the 7 x 7 receptive field
@@ -36,32 +40,40 @@
 namespace fibar {
 
 constexpr int FL_R = 8;            // output rows per unit
-constexpr int FL_OC = 126;         // output columns per unit
-constexpr int FL_M = 128;          // a2 columns per unit (the MMA's M)
-constexpr int FL_A1C = FL_M + 2;   // a1 columns
-constexpr int FL_XC = FL_M + 4;    // input columns
+constexpr int FL_OC = 124;         // output columns per unit
+constexpr int FL_M = 128;          // pixels per MMA (M): a1 columns, and a2 / output columns with halo
+constexpr int FL_C = FL_M + 2;     // allocated columns of every tile (an MMA reads pixels dx .. dx + 127)
 constexpr int FL_A2R = FL_R + 2;   // a2 rows
 constexpr int FL_A1R = FL_R + 4;   // a1 rows
 constexpr int FL_XR = FL_R + 6;    // input rows
 constexpr int FL_THREADS = 512;
-constexpr int FL_XN = FL_XR * FL_XC;                        // input positions per unit
+constexpr int FL_XN = FL_XR * FL_C;                         // input positions per unit
 constexpr int FL_XITER = (FL_XN + FL_THREADS - 1) / FL_THREADS;
-constexpr unsigned FL_TMEM_COLS = 256;                      // >= 16 columns x 10 rows
-constexpr unsigned FL_PLANE = FL_A1C * 16;                  // one K plane of an a1 row
-constexpr unsigned FL_A1ROW = 2 * FL_PLANE;                 // bytes per a1 row
+constexpr unsigned FL_TMEM_COLS = 512;                      // one CTA per SM (shared memory)
+// Each MMA multiplies one input row (shifted by dx) by the three dy taps at once (N = 48):
+// its three 16-column blocks are the accumulators of output rows j - 2, j - 1 and j, so
+// output row r's accumulator sits at column t0 + 16 (r + 2) (rows -2 and -1 and the last
+// two are scratch).  TMEM columns: conv1 16 x 16 = 256, conv2 14 x 16 = 224; conv3 (12 x 16)
+// reuses conv1's, which its epilogue has read by then.
+constexpr unsigned FL_T1 = 0, FL_T2 = 256, FL_T3 = 0;
+constexpr unsigned FL_PLANE = FL_C * 16;                    // one K half (8 channels) of a tile row
+constexpr unsigned FL_ROW2 = 2 * FL_PLANE;                  // a1 / a2 row: both K halves
 constexpr float FL_AGE_MAX = 4.f;
 constexpr unsigned FL_SPIN_LIMIT = 1u << 20;
 constexpr unsigned ERR_FILL_WAIT = 32u;                     // Ctrl::error bit
 
 struct FillSmem {
-    unsigned char a1[FL_A1R * FL_A1ROW];   // canonical layout, 16-byte aligned
-    uint4 w2[9 * 32];                      // B operands (per tap 16 x 16 BF16)
-    float x[2][FL_XR][FL_XC];
-    float a2[FL_A2R][FL_M][17];            // padded: conflict-free by pixel
-    unsigned char stale[FL_R][FL_OC + 2];
+    unsigned char x[FL_XR * FL_PLANE];    // inputs: channels (L, age, 0 x 6) as BF16, one K half
+    unsigned char zero[FL_M * 16];        // the inputs' second K half: zeros
+    unsigned char a1[FL_A1R * FL_ROW2];   // canonical K-major layout, no swizzle
+    unsigned char a2[FL_A2R * FL_ROW2];
+    uint4 w[3][9 * 32];                   // B operands of the three layers
+    float lout[FL_R][FL_OC];              // L of the output pixels (FP32: written where not stale)
+    unsigned char stale[FL_R][FL_OC];
     unsigned long long bar;
     unsigned tmem;
 };
+static_assert(sizeof(FillSmem) < 227 * 1024, "fill tile");
 
 // Where the inputs come from: a handle's state (read-out) or explicit images.
 struct FillIO {
@@ -85,6 +97,13 @@ __device__ __forceinline__ unsigned short fl_bf16_bits(float v)
     return (unsigned short)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
 }
 
+// round to nearest even for any finite value (inputs may be negative)
+__device__ __forceinline__ unsigned short fl_bf16_bits_any(float v)
+{
+    const unsigned u = __float_as_uint(v);
+    return (unsigned short)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+
 // tcgen05 shared-memory matrix descriptor: K-major, no swizzle; lbo = byte distance of
 // the two 8-element K halves, sbo = byte distance of 8-row groups.
 __device__ __forceinline__ unsigned long long fl_desc(unsigned saddr, unsigned lbo, unsigned sbo)
@@ -93,8 +112,9 @@ __device__ __forceinline__ unsigned long long fl_desc(unsigned saddr, unsigned l
            ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M = 128, N = 16
-constexpr unsigned FL_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M = 128, N = 48
+constexpr unsigned FL_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((48u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr unsigned FL_BDX = 1536;   // bytes of one dx block of a layer's B operand (48 rows x 32 B)
 
 __device__ __forceinline__ void fl_mma(unsigned d_tmem, unsigned long long a, unsigned long long b, unsigned acc)
 {
@@ -132,6 +152,40 @@ __device__ __forceinline__ void fl_tmem_ld16(unsigned taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// tcgen05.ld of 16 columns without the wait: several loads in flight, then fl_tmem_wait
+__device__ __forceinline__ void fl_tmem_ld16_async(unsigned taddr, unsigned (&r)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                 "%12, %13, %14, %15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void fl_tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 16 columns of zeros into the warp's TMEM lanes
+__device__ __forceinline__ void fl_tmem_zero16(unsigned taddr)
+{
+    const unsigned z = 0u;
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+                 "%1, %1, %1, %1};" ::"r"(taddr), "r"(z) : "memory");
+}
+
+__device__ __forceinline__ float fl_tmem_ld1(unsigned taddr)
+{
+    unsigned r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    return __uint_as_float(r);
+}
+
+// A layer (run_layer in k_fill): for each of its output rows r, 9 MMAs (taps dy, dx) of
+// 128 pixels x 16 channels x 16 inputs into TMEM columns t0 + 16 r.  The A operand of tap
+// (dy, dx) is the input tile's row r + dy from pixel dx on (the descriptor's start moves by
+// dx rows of 16 bytes); its second K half lies `lbo` bytes after the start: the next plane
+// of the tile, or for the 2-channel inputs a block of zeros.  One thread issues them.
 __global__ void __launch_bounds__(FL_THREADS, 1) k_fill(FillParams fp, FillIO io)
 {
     PDL_ENTRY();
@@ -148,7 +202,12 @@ __global__ void __launch_bounds__(FL_THREADS, 1) k_fill(FillParams fp, FillIO io
         h = (unsigned long long)io.ctrl->det.h;
         q = k_now > h ? k_now - h : 1ull;
     }
-    for (int i = threadIdx.x; i < 9 * 32; i += FL_THREADS) S.w2[i] = fp.w2[i];
+    for (int i = threadIdx.x; i < 9 * 32; i += FL_THREADS) {
+        S.w[0][i] = fp.w1[i];
+        S.w[1][i] = fp.w2[i];
+        S.w[2][i] = fp.w3[i];
+    }
+    for (int i = threadIdx.x; i < FL_M; i += FL_THREADS) reinterpret_cast<uint4 *>(S.zero)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(fl_smem_u32(&S.bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -162,46 +221,124 @@ __global__ void __launch_bounds__(FL_THREADS, 1) k_fill(FillParams fp, FillIO io
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = S.tmem;
-    const unsigned a1_base = fl_smem_u32(S.a1), w2_base = fl_smem_u32(S.w2);
+    const unsigned bar = fl_smem_u32(&S.bar);
+    const unsigned x_base = fl_smem_u32(S.x), z_base = fl_smem_u32(S.zero);
+    const unsigned a1_base = fl_smem_u32(S.a1), a2_base = fl_smem_u32(S.a2);
+    const unsigned w_base = fl_smem_u32(S.w[0]);
     unsigned phase = 0;
     bool failed = false;
+    // make the threads' shared-memory writes visible to the tensor cores, wait for every
+    // thread, and (thread 0) issue a layer; then everyone waits for its completion
+    auto run_layer = [&](unsigned in_base, unsigned row_bytes, bool lbo_to_zero, unsigned wsel, unsigned t0,
+                         int in_rows) {
+        // zero the layer's accumulators (every MMA adds to three of them)
+        for (int c = (int)(warp >> 2); c < in_rows + 2; c += FL_THREADS / 128)
+            fl_tmem_zero16(tmem + ((32u * (warp & 3)) << 16) + t0 + 16u * c);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (threadIdx.x == 0) {
+            // descriptors of input row 0, dx 0; a row or dx moves the start address (low
+            // field, in 16-byte units) and, for the inputs, the distance to the zero block
+            // the other way (the LBO field)
+            const unsigned long long a0 = fl_desc(in_base, lbo_to_zero ? z_base - in_base : FL_PLANE, 128);
+            const unsigned long long b0 = fl_desc(w_base + wsel * 3 * FL_BDX, FL_BDX / 2, 128);
+            const unsigned long long step_unit = lbo_to_zero ? (1ull - (1ull << 16)) : 1ull;
+            // rows in steps of three: consecutive MMAs write disjoint accumulators
+            for (int dx = 0; dx < 3; ++dx)
+                for (int j0 = 0; j0 < 3; ++j0)
+                    for (int j = j0; j < in_rows; j += 3) {
+                        const unsigned off = (j * row_bytes + dx * 16) >> 4;
+                        fl_mma(tmem + t0 + 16 * j, a0 + step_unit * off, b0 + (unsigned long long)(dx * (FL_BDX >> 4)), 1u);
+                    }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                         : "memory");
+        }
+        // one warp polls the barrier, the others wait at the block barrier
+        bool ok = warp == 0 ? fl_wait(&S.bar, phase) : true;
+        phase ^= 1u;
+        if (!ok && threadIdx.x == 0) atomicOr(io.err, ERR_FILL_WAIT);
+        failed = __syncthreads_or(!ok) != 0;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    };
+    // epilogue of conv1 / conv2: TMEM -> bias, ReLU -> BF16 tile rows (zero outside the image)
+    auto epilogue = [&](unsigned t0, int rows, const float *bias, unsigned char *dst, int gy0, int gx0) {
+        constexpr int RSTEP = FL_THREADS / 128;                      // rows a warp handles apart
+        constexpr int RMAX = (FL_A1R + RSTEP - 1) / RSTEP;           // rows per warp at most
+        const int px = 32 * (warp & 3) + lane;
+        const int gx = gx0 + px;
+        const int r0 = (int)(warp >> 2);
+        // all of the warp's TMEM loads first, one wait
+        unsigned raw[RMAX][16];
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j)
+            if (r0 + j * RSTEP < rows)
+                fl_tmem_ld16_async(tmem + ((32u * (warp & 3)) << 16) + t0 + 16u * (r0 + j * RSTEP + 2), raw[j]);
+        fl_tmem_wait();
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j) {
+            const int r = r0 + j * RSTEP;
+            if (r >= rows) break;
+            const int gy = gy0 + r;
+            const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+            unsigned pk[8];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const unsigned lo = in ? fl_bf16_bits(fmaxf(__uint_as_float(raw[j][2 * o]) + bias[2 * o], 0.f)) : 0u;
+                const unsigned hi = in ? fl_bf16_bits(fmaxf(__uint_as_float(raw[j][2 * o + 1]) + bias[2 * o + 1], 0.f)) : 0u;
+                pk[o] = lo | (hi << 16);
+            }
+            uint4 *row = reinterpret_cast<uint4 *>(dst + r * FL_ROW2);
+            row[px] = make_uint4(pk[0], pk[1], pk[2], pk[3]);            // channels 0-7
+            row[FL_C + px] = make_uint4(pk[4], pk[5], pk[6], pk[7]);     // channels 8-15
+        }
+    };
+
+    // a unit's global inputs, one thread's share, loaded into registers: the next unit's are
+    // requested right after the current unit's have been stored, so that they arrive
+    // while the tensor cores run the current unit
+    float v0[FL_XITER], v1x[FL_XITER];
+    unsigned long long lp[FL_XITER];
+    unsigned char sx[FL_XITER];
+    auto load_inputs = [&](int u) {
+        const int y0 = (u / nseg) * FL_R, x0 = (u % nseg) * FL_OC;
+#pragma unroll
+        for (int it = 0; it < FL_XITER; ++it) {
+            const int i = threadIdx.x + it * FL_THREADS;
+            const int r = i / FL_C, c = i % FL_C;
+            const int gy = y0 - 3 + r, gx = x0 - 3 + c;
+            const bool in = u < units && i < FL_XN && gy >= 0 && gy < H && gx >= 0 && gx < W;
+            const size_t p = in ? (size_t)gy * W + gx : 0;
+            v0[it] = 0.f;
+            v1x[it] = 0.f;
+            lp[it] = NONE64;
+            sx[it] = 0;
+            if (in) {
+                if (io.from_handle) {
+                    v0[it] = io.L[p];
+                    lp[it] = io.last_pix[p];
+                } else {
+                    v0[it] = io.x[p];
+                    v1x[it] = io.x[(size_t)W * H + p];
+                    sx[it] = io.stale[p];
+                }
+            }
+        }
+    };
+    load_inputs(blockIdx.x);
 
     for (int u = blockIdx.x; u < units && !failed; u += gridDim.x) {
         const int y0 = (u / nseg) * FL_R, x0 = (u % nseg) * FL_OC;
-        // inputs: rows y0-3 .. y0+10, columns x0-3 .. x0+128 (zero outside the image); all
-        // of a thread's global loads are issued before any is used
+        // inputs: rows y0-3 .. y0+10, columns x0-3 .. x0+126 (zero outside the image), as
+        // BF16 channels (L, age); the output pixels' L in FP32 and their stale flags
         {
-            float v0[FL_XITER];
-            unsigned long long lp[FL_XITER];
-            float v1x[FL_XITER];
-            unsigned char sx[FL_XITER];
-#pragma unroll
-            for (int it = 0; it < FL_XITER; ++it) {
-                const int i = threadIdx.x + it * FL_THREADS;
-                const int r = i / FL_XC, c = i % FL_XC;
-                const int gy = y0 - 3 + r, gx = x0 - 3 + c;
-                const bool in = i < FL_XN && gy >= 0 && gy < H && gx >= 0 && gx < W;
-                const size_t p = in ? (size_t)gy * W + gx : 0;
-                v0[it] = 0.f;
-                v1x[it] = 0.f;
-                lp[it] = NONE64;
-                sx[it] = 0;
-                if (in) {
-                    if (io.from_handle) {
-                        v0[it] = io.L[p];
-                        lp[it] = io.last_pix[p];
-                    } else {
-                        v0[it] = io.x[p];
-                        v1x[it] = io.x[(size_t)W * H + p];
-                        sx[it] = io.stale[p];
-                    }
-                }
-            }
 #pragma unroll
             for (int it = 0; it < FL_XITER; ++it) {
                 const int i = threadIdx.x + it * FL_THREADS;
                 if (i >= FL_XN) break;
-                const int r = i / FL_XC, c = i % FL_XC;
+                const int r = i / FL_C, c = i % FL_C;
                 const int gy = y0 - 3 + r, gx = x0 - 3 + c;
                 const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
                 float v1 = v1x[it];
@@ -216,104 +353,37 @@ __global__ void __launch_bounds__(FL_THREADS, 1) k_fill(FillParams fp, FillIO io
                     st = (lp[it] != NONE64 && lp[it] < h) ? 1 : 0;
                 }
                 const int orow = gy - y0, ocol = gx - x0;
-                if (in && orow >= 0 && orow < FL_R && ocol >= 0 && ocol < FL_OC) S.stale[orow][ocol] = st;
-                S.x[0][r][c] = v0[it];
-                S.x[1][r][c] = in ? v1 : 0.f;
-            }
-        }
-        __syncthreads();
-        // conv1 -> a1 (BF16, canonical layout); zero outside the image
-        for (int i = threadIdx.x; i < FL_A1R * FL_A1C; i += FL_THREADS) {
-            const int j = i / FL_A1C, c = i % FL_A1C;
-            const int gy = y0 - 2 + j, gx = x0 - 2 + c;
-            float acc[16];
-#pragma unroll
-            for (int o = 0; o < 16; ++o) acc[o] = fp.b1[o];
-            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-#pragma unroll
-                for (int ci = 0; ci < 2; ++ci)
-#pragma unroll
-                    for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                        for (int dx = 0; dx < 3; ++dx) {
-                            const float xv = S.x[ci][j + dy][c + dx];
-#pragma unroll
-                            for (int o = 0; o < 16; ++o) acc[o] = fmaf(fp.w1[o * 18 + ci * 9 + dy * 3 + dx], xv, acc[o]);
-                        }
-            }
-            unsigned pk[8];
-#pragma unroll
-            for (int o = 0; o < 8; ++o) {
-                const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-                const unsigned lo = in ? fl_bf16_bits(fmaxf(acc[2 * o], 0.f)) : 0u;
-                const unsigned hi = in ? fl_bf16_bits(fmaxf(acc[2 * o + 1], 0.f)) : 0u;
-                pk[o] = lo | (hi << 16);
-            }
-            uint4 *row = reinterpret_cast<uint4 *>(S.a1 + j * FL_A1ROW);
-            row[c] = make_uint4(pk[0], pk[1], pk[2], pk[3]);            // channels 0-7
-            row[FL_A1C + c] = make_uint4(pk[4], pk[5], pk[6], pk[7]);   // channels 8-15
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (threadIdx.x == 0) {
-            // conv2: a2 row r (global row y0-1+r), pixels x0-1 .. x0+126; tap (dy, dx)
-            // reads a1 row r+dy from pixel dx on
-            for (int r = 0; r < FL_A2R; ++r) {
-#pragma unroll
-                for (int t = 0; t < 9; ++t) {
-                    const int dy = t / 3, dx = t % 3;
-                    const unsigned long long ad = fl_desc(a1_base + (r + dy) * FL_A1ROW + dx * 16, FL_PLANE, 128);
-                    const unsigned long long bd = fl_desc(w2_base + t * 512, 256, 128);
-                    fl_mma(tmem + 16 * r, ad, bd, t > 0 ? 1u : 0u);
+                if (in && orow >= 0 && orow < FL_R && ocol >= 0 && ocol < FL_OC) {
+                    S.stale[orow][ocol] = st;
+                    S.lout[orow][ocol] = v0[it];
                 }
+                const unsigned b0 = in ? fl_bf16_bits_any(v0[it]) : 0u;
+                const unsigned b1 = in ? fl_bf16_bits_any(v1) : 0u;
+                reinterpret_cast<uint4 *>(S.x + r * FL_PLANE)[c] = make_uint4(b0 | (b1 << 16), 0u, 0u, 0u);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(fl_smem_u32(&S.bar)) : "memory");
         }
-        if (!fl_wait(&S.bar, phase)) {
-            if (threadIdx.x == 0) atomicOr(io.err, ERR_FILL_WAIT);
-            failed = true;
-        }
-        phase ^= 1u;
-        failed = __syncthreads_or(failed) != 0;
+        load_inputs(u + (int)gridDim.x);
+        // conv1: a1 rows (global y0-2 ..), pixels x0-2 .. x0+125
+        run_layer(x_base, FL_PLANE, true, 0, FL_T1, FL_XR);
         if (failed) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (its pixels), rows of its half
+        epilogue(FL_T1, FL_A1R, fp.b1, S.a1, y0 - 2, x0 - 2);
+        // conv2: a2 rows (global y0-1 ..), pixels x0-1 .. x0+126
+        run_layer(a1_base, FL_ROW2, false, 1, FL_T2, FL_A1R);
+        if (failed) break;
+        epilogue(FL_T2, FL_A2R, fp.b2, S.a2, y0 - 1, x0 - 1);
+        // conv3: output rows y0 .., pixels x0 .. x0+127 (the first 124 kept)
+        run_layer(a2_base, FL_ROW2, false, 2, FL_T3, FL_A2R);
+        if (failed) break;
         {
             const int px = 32 * (warp & 3) + lane;
-            const int gx = x0 - 1 + px;
-            for (int r = (int)(warp >> 2); r < FL_A2R; r += FL_THREADS / 128) {
-                float v[16];
-                fl_tmem_ld16(tmem + ((32u * (warp & 3)) << 16) + 16u * r, v);
-                const int gy = y0 - 1 + r;
-                const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-#pragma unroll
-                for (int o = 0; o < 16; ++o) S.a2[r][px][o] = in ? fmaxf(v[o] + fp.b2[o], 0.f) : 0.f;
+            const int gx = x0 + px;
+            for (int o = (int)(warp >> 2); o < FL_R; o += FL_THREADS / 128) {
+                const float y = fl_tmem_ld1(tmem + ((32u * (warp & 3)) << 16) + FL_T3 + 16u * (o + 2)) + fp.b3;
+                const int gy = y0 + o;
+                if (px < FL_OC && gx < W && gy < H) io.out[(size_t)gy * W + gx] = S.stale[o][px] ? y : S.lout[o][px];
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        // conv3 and the mask
-        for (int i = threadIdx.x; i < FL_R * FL_OC; i += FL_THREADS) {
-            const int o = i / FL_OC, oc = i % FL_OC;
-            const int gy = y0 + o, gx = x0 + oc;
-            if (gy >= H || gx >= W) continue;
-            float v = S.x[0][o + 3][oc + 3];
-            if (S.stale[o][oc]) {
-                float acc[3] = {fp.b3, 0.f, 0.f};  // one chain per kernel row
-#pragma unroll
-                for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                    for (int dx = 0; dx < 3; ++dx)
-#pragma unroll
-                        for (int c = 0; c < 16; ++c)
-                            acc[dy] = fmaf(fp.w3[c * 9 + dy * 3 + dx], S.a2[o + dy][oc + dx][c], acc[dy]);
-                v = (acc[0] + acc[1]) + acc[2];
-            }
-            io.out[(size_t)gy * W + gx] = v;
-        }
         __syncthreads();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -412,9 +482,10 @@ k_fill_train(const float *X, const float *T, const unsigned char *M, unsigned W,
         S.th[i] = is_w ? fl_bf16_round(v) : v;
     }
     for (int p = threadIdx.x; p < FT_P; p += FT_THREADS) {
+        // every layer's input enters as BF16 (the read-out's tensor-core operands)
         const size_t g = (size_t)(cy + p / FT_S) * W + cx + p % FT_S;
-        S.x[0][p] = Xf[g];
-        S.x[1][p] = Xf[plane + g];
+        S.x[0][p] = fl_bf16_round(Xf[g]);
+        S.x[1][p] = fl_bf16_round(Xf[plane + g]);
     }
     __syncthreads();
     // forward: z1, z2 (pre-activations), y
@@ -445,7 +516,8 @@ k_fill_train(const float *X, const float *T, const unsigned char *M, unsigned W,
         float a = S.th[OB3];
         for (int ci = 0; ci < 16; ++ci)
             for (int t = 0; t < 9; ++t)
-                a = fmaf(S.th[OW3 + ci * 9 + t], fmaxf(crop_at(S.z2[ci], py + t / 3 - 1, px + t % 3 - 1), 0.f), a);
+                a = fmaf(S.th[OW3 + ci * 9 + t],
+                         fl_bf16_round(fmaxf(crop_at(S.z2[ci], py + t / 3 - 1, px + t % 3 - 1), 0.f)), a);
         const bool inner = py >= FT_MARGIN && py < FT_S - FT_MARGIN && px >= FT_MARGIN && px < FT_S - FT_MARGIN;
         const size_t g = (size_t)f * plane + (size_t)(cy + py) * W + cx + px;
         float gy = 0.f;
@@ -472,7 +544,7 @@ k_fill_train(const float *X, const float *T, const unsigned char *M, unsigned W,
         if (i < 144) {
             const int ci = i / 9, t = i % 9;
             for (int p = 0; p < FT_P; ++p)
-                s = fmaf(S.g[p], fmaxf(crop_at(S.z2[ci], p / FT_S + t / 3 - 1, p % FT_S + t % 3 - 1), 0.f), s);
+                s = fmaf(S.g[p], fl_bf16_round(fmaxf(crop_at(S.z2[ci], p / FT_S + t / 3 - 1, p % FT_S + t % 3 - 1), 0.f)), s);
             atomicAdd(&grad[OW3 + i], s);
         } else {
             for (int p = 0; p < FT_P; ++p) s += S.g[p];
@@ -599,13 +671,6 @@ unsigned short host_bf16_bits(float v)
     return (unsigned short)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
 }
 
-float host_bf16(float v)
-{
-    const unsigned u = (unsigned)host_bf16_bits(v) << 16;
-    float r;
-    memcpy(&r, &u, 4);
-    return r;
-}
 
 }  // namespace
 
@@ -618,19 +683,23 @@ int pack_fill_params(const float *theta, FillParams *fp)
     for (int i = 0; i < FILL_NPARAMS; ++i)
         if (!isfinite(theta[i])) return FIBAR_EINVAL;
     memset(fp, 0, sizeof(*fp));
-    for (int i = 0; i < 288; ++i) fp->w1[i] = host_bf16(theta[OW1 + i]);
     for (int i = 0; i < 16; ++i) fp->b1[i] = theta[OB1 + i];
     for (int i = 0; i < 16; ++i) fp->b2[i] = theta[OB2 + i];
-    for (int i = 0; i < 144; ++i) fp->w3[i] = host_bf16(theta[OW3 + i]);
     fp->b3 = theta[OB3];
-    unsigned short *w2 = reinterpret_cast<unsigned short *>(fp->w2);
-    for (int co = 0; co < 16; ++co)
-        for (int ci = 0; ci < 16; ++ci)
-            for (int t = 0; t < 9; ++t) {
-                // tap t: row co (16 bytes per row within a K half), K half ci / 8 at +256 B
-                const size_t byte = (size_t)t * 512 + (ci / 8) * 256 + co * 16 + (ci % 8) * 2;
-                w2[byte / 2] = host_bf16_bits(theta[OW2 + (co * 16 + ci) * 9 + t]);
-            }
+    // tap (dy, dx), output channel co, input channel k: dx block of 48 rows n = 16 (2 - dy) + co,
+    // byte dx * 1536 + (k / 8) * 768 + n * 16 + (k % 8) * 2
+    auto put = [](uint4 *ops, int t, int co, int k, float v) {
+        const int dy = t / 3, dx = t % 3, n = 16 * (2 - dy) + co;
+        unsigned short *w = reinterpret_cast<unsigned short *>(ops);
+        w[((size_t)dx * 1536 + (k / 8) * 768 + n * 16 + (k % 8) * 2) / 2] = host_bf16_bits(v);
+    };
+    for (int t = 0; t < 9; ++t)
+        for (int co = 0; co < 16; ++co) {
+            for (int ci = 0; ci < 2; ++ci) put(fp->w1, t, co, ci, theta[OW1 + (co * 2 + ci) * 9 + t]);
+            for (int ci = 0; ci < 16; ++ci) put(fp->w2, t, co, ci, theta[OW2 + (co * 16 + ci) * 9 + t]);
+        }
+    for (int t = 0; t < 9; ++t)
+        for (int ci = 0; ci < 16; ++ci) put(fp->w3, t, 0, ci, theta[OW3 + ci * 9 + t]);
     return FIBAR_OK;
 }
 

@@ -1,13 +1,15 @@
 """The learned stale-pixel fill's CUDA kernels against the FP64 oracle
 (oracle/learned_fill.py).
 
-Tolerances come from the arithmetic.  The kernel accumulates in FP32 (conv2 on the
-tensor cores); with inputs and weights on a coarse binary grid, conv1 is exact in FP32,
-so both sides round a1 to BF16 identically and the remaining difference is bounded by
-the FP32 accumulation: per output, |dy| <= eps32 (2 n) (sum |W3| |a2| + conv(|W3|, dz2))
-with dz2 <= eps32 (2 n) (sum |W2| |a1| + |b2|), n = 145 terms.  On arbitrary inputs a1
-values that sit within rounding noise of a BF16 tie may round differently on the two
-sides; such pixels are bounded by conv(|W3|, conv(|W2|, ulp(a1))) and must be rare.
+Tolerances come from the arithmetic.  Every layer takes BF16 inputs and accumulates in
+FP32 on the tensor cores.  With inputs and weights on a coarse binary grid, conv1 is exact
+in FP32, so both sides round a1 to BF16 identically; conv2 then differs by at most the FP32
+accumulation bound dz2 = eps32 (2 n) (sum |W2| |a1| + |b2|), n = 145 terms, and a2 can round
+to the neighbouring BF16 value only where it lies within dz2 of a rounding boundary; the
+output differs by at most eps32 (2 n) (sum |W3| |a2| + |b3|) + conv(|W3|, dz2 + those
+flips).  On arbitrary inputs a1 can also round differently on the two sides where it lies
+within rounding noise of a tie; such pixels are bounded by the worst case of every a1 and
+a2 flipping and must be rare.
 """
 import numpy as np
 import pytest
@@ -19,6 +21,7 @@ from oracle import learned_fill as lf
 pytestmark = pytest.mark.gpu
 
 EPS32 = 2.0 ** -24
+N_TERMS = 145
 
 
 def _grid_theta(seed):
@@ -36,6 +39,7 @@ def _grid_theta(seed):
 
 
 def _grid_inputs(W, H, seed):
+    """Inputs on a 2^-6 grid within [-4, 4]: at most 8 significant bits, exactly BF16."""
     rng = np.random.default_rng(seed)
     L = np.round(rng.normal(size=(H, W)) * 40) / 64.0
     L = np.clip(L, -4, 4)
@@ -48,16 +52,30 @@ def _abs_conv(x, W):
     return lf.conv3x3(np.abs(x), np.abs(W), np.zeros(W.shape[0]))
 
 
+def _bf16_ulp(v):
+    """Spacing of the BF16 values at |v| (8 significant bits); 0 at 0."""
+    a = np.abs(v)
+    with np.errstate(divide="ignore"):
+        e = np.floor(np.log2(np.where(a > 0, a, 1.0)))
+    return np.where(a > 0, 2.0 ** (e - 7), 0.0)
+
+
 def _exact_path_bound(f, theta):
+    """Bound for identical a1 roundings: FP32 accumulation of conv2 and conv3, and the
+    a2 values it can move across a BF16 rounding boundary."""
     p = lf.unflatten(theta)
-    n = 145
-    dz2 = EPS32 * 2 * n * (_abs_conv(f["a1q"], f["W2"]) + np.abs(p["b2"])[:, None, None])
-    return EPS32 * 2 * n * (_abs_conv(f["a2"], f["W3"])[0] + abs(p["b3"][0])) + _abs_conv(dz2, f["W3"])[0]
+    dz2 = EPS32 * 2 * N_TERMS * (_abs_conv(f["a1q"], f["W2"]) + np.abs(p["b2"])[:, None, None])
+    ulp2 = _bf16_ulp(f["a2q"])
+    to_boundary = ulp2 / 2 - np.abs(f["a2"] - f["a2q"])
+    flip2 = np.where(to_boundary <= dz2, np.maximum(ulp2, _bf16_ulp(f["a2"] + dz2)), 0.0)
+    return (EPS32 * 2 * N_TERMS * (_abs_conv(f["a2q"], f["W3"])[0] + abs(p["b3"][0]))
+            + _abs_conv(dz2 + flip2, f["W3"])[0])
 
 
 def _flip_bound(f):
-    ulp = 2.0 ** -7 * np.abs(f["a1q"])
-    return _abs_conv(_abs_conv(ulp, f["W2"]), f["W3"])[0]
+    """Worst case of every a1 and a2 value rounding to its BF16 neighbour."""
+    da2 = _abs_conv(2.0 ** -7 * np.abs(f["a1q"]), f["W2"])
+    return _abs_conv(da2 + 2.0 ** -7 * (np.abs(f["a2q"]) + da2), f["W3"])[0]
 
 
 def _gpu_forward(theta, x, stale):
@@ -141,9 +159,10 @@ def test_readout_with_learned_fill_matches_the_oracle_chain(oracle_mod):
         f = lf.forward(theta, x)
         ref = np.where(stale, f["y"], L)
         err = np.abs(img - ref)
-        # L itself differs from the oracle by up to 1e-4 (the filter's FP32 state);
-        # through the network that moves y by at most conv(|W3|, conv(|W2|, conv(|W1|, 1e-4)))
-        dl = 1e-4 * np.stack([np.ones_like(L), np.zeros_like(L)])
+        # L itself differs from the oracle by up to 1e-4 (the filter's FP32 state), and its
+        # BF16 rounding can differ by one BF16 step; through the network that moves y by at
+        # most conv(|W3|, conv(|W2|, conv(|W1|, dL))) plus the later roundings' flips
+        dl = np.stack([1e-4 + 2.0 ** -7 * np.abs(L), np.zeros_like(L)])
         p = lf.unflatten(theta)
         prop = _abs_conv(_abs_conv(_abs_conv(dl, f["W1"]), f["W2"]), f["W3"])[0]
         bound = np.where(stale, _exact_path_bound(f, theta) + _flip_bound(f) + prop, 1e-4)

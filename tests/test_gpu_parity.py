@@ -283,13 +283,21 @@ def test_push_many_equals_single_pushes(device):
     np.testing.assert_array_equal(a_st["cnt"], b_st["cnt"])
 
 
+PAN_PREFIX = 20_000_000
+
+
+@pytest.fixture(scope="module")
+def pan_prefix():
+    return eventsim.make_config("perlin_pan_1280x720_1B", n_events=PAN_PREFIX, device="cuda").cpu()
+
+
 @pytest.mark.parametrize("packet", [8_192, 65_536, 1_048_576])
-def test_config_perlin_pan_1280x720_prefix(oracle_mod, packet):
+def test_config_perlin_pan_1280x720_prefix(oracle_mod, pan_prefix, packet):
     """1280x720 Perlin noise panned in bursts (segments of 1-50 Mev/s), seed 2: the first
     20 M events, read out every 1,000,000 events, pushed as packets of 8,192, 65,536 and
     1,048,576 events (S2).  The temporal filter's schedule is chosen per piece (auto)."""
-    n = 20_000_000
-    ev = eventsim.make_config("perlin_pan_1280x720_1B", n_events=n, device="cuda").cpu()
+    n = PAN_PREFIX
+    ev = pan_prefix
     steps = plan_packets(n, packet, 1_000_000, ev)
     worst, stats = _check(oracle_mod, 1280, 720, ev, steps, "s2", c_on=0.2, c_off=0.2)
     assert stats["events_applied"] == n
