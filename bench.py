@@ -208,6 +208,29 @@ def run_batch(args, rank, world, local):
     sids = [srv.admit(s["W"], s["H"], **params) for s in streams]
     if None in sids:
         raise RuntimeError("not enough device memory for the 32 streams")
+    tuning = None
+    if args.grid_share is not None:
+        srv.set_grid_share({(s["W"], s["H"]): args.grid_share for s in streams})
+        tuning = {"fixed_sms": args.grid_share}
+    elif not args.no_autotune:
+        # per sensor shape: the SM share with the most events/s when as many streams of
+        # that shape as a batch holds on average are read out together, each at its
+        # shape's mean events per read-out (100 Hz requests)
+        from paper_2510_20071_gb300.serving import GridTuner
+        tuner = GridTuner()
+        shapes = {}
+        for s in streams:
+            shapes.setdefault((s["W"], s["H"]), []).append(s["events"].shape[0] / seconds)
+        sizes = [len(reads) for _, _, reads in sched if reads]
+        per_batch = max(1, round(sum(sizes) / max(len(sizes), 1)))
+        t_tune = time.time()
+        for (w_, h_), rates in shapes.items():
+            tuner.tune(w_, h_, per_batch, int(sum(rates) / len(rates) / 100.0), **params)
+        srv.set_grid_share(tuner.table)
+        tuning = {"sms": {f"{w_}x{h_}": v for (w_, h_), v in tuner.table.items()},
+                  "trials": {f"{w_}x{h_}": v for (w_, h_), v in tuner.trials.items()},
+                  "streams_per_trial": per_batch, "seconds": round(time.time() - t_tune, 2)}
+        log(f"[rank {rank}] grid shares {tuning['sms']} ({tuning['seconds']} s)")
 
     def tick(T, pushes, reads):
         for i, lo, hi in pushes:
@@ -282,6 +305,7 @@ def run_batch(args, rank, world, local):
         "readout_latency_ms": {"p50": pct(50), "p99": pct(99), "max": pct(100), "samples": len(lat),
                                "what": "device time from a batch's start to the request's image"},
         "host_ms": round(host_ms, 3),
+        "grid_share_autotune": tuning,
         "batches": st1["batches"] - st0["batches"],
         "clocks": clocks,
         "gpu_launches": launches,
@@ -635,6 +659,9 @@ def main():
                          "batches; calib: relative thresholds of a 640x480 recording")
     ap.add_argument("--batch-seconds", type=float, default=0.2,
                     help="batch32: stream time simulated per stream")
+    ap.add_argument("--grid-share", type=int, default=None,
+                    help="batch32: SMs every stream's grids are sized for (default: autotuned per shape)")
+    ap.add_argument("--no-autotune", action="store_true", help="batch32: whole-device grids for every stream")
     ap.add_argument("--calib-events", type=int, default=100_000_000,
                     help="calib: records in the recording (profiling runs use fewer)")
     args = ap.parse_args()

@@ -356,6 +356,14 @@ int fibar_stage_times(fibar_t *h, fibar_stage_times_t *t, int reset, void *cuda_
 /* Message of the last failed call on this handle ("" if none).  Owned by the handle. */
 const char *fibar_last_error(fibar_t *h);
 
+/* Size the handle's kernel grids for `sms` streaming multiprocessors from its next
+ * read-out on (0, or more than the device has: all of them; the default).  Results do not
+ * change (every kernel distributes its work by tickets or strided loops).  The paper has
+ * no counterpart; when many small streams are read out concurrently
+ * (fibar_readout_batch), a share below the whole device lets their pipelines run side by
+ * side instead of each one's grids filling the GPU in turn.  Errors: EINVAL. */
+int fibar_set_grid_share(fibar_t *h, uint32_t sms);
+
 /* Release the handle and its device memory (waits for its outstanding work). */
 void fibar_destroy(fibar_t *h);
 

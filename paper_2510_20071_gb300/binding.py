@@ -27,7 +27,7 @@ EXPORTED = ["fibar_default_params", "fibar_create", "fibar_push_events", "fibar_
             "fibar_readout_batch", "fibar_memory_bytes", "fibar_relative_thresholds",
             "fibar_set_pixel_gain", "fibar_debug_wait_timeout", "fibar_push_events_many",
             "fibar_fill_set_weights", "fibar_fill_features", "fibar_fill_forward", "fibar_fill_train_step",
-            "fibar_readout_host_async", "fibar_wait"]
+            "fibar_readout_host_async", "fibar_wait", "fibar_set_grid_share"]
 
 FIBAR_FILL_NPARAMS = 2769
 
@@ -124,6 +124,8 @@ def load_library(build_if_missing: bool = True):
             lib.fibar_debug_wait_timeout.restype = C.c_int
             lib.fibar_push_events_many.argtypes = [vp, C.POINTER(vp), C.POINTER(C.c_size_t), C.c_size_t, C.c_int, vp]
             lib.fibar_push_events_many.restype = C.c_int
+            lib.fibar_set_grid_share.argtypes = [vp, C.c_uint32]
+            lib.fibar_set_grid_share.restype = C.c_int
             lib.fibar_readout_host_async.argtypes = [vp, C.c_uint64, vp, vp]
             lib.fibar_readout_host_async.restype = C.c_int
             lib.fibar_wait.argtypes = [vp, vp]
@@ -229,6 +231,10 @@ def fibar_push_events_many(h, ev_ptrs, ns, on_device: int, stream: int) -> int:
 
 def fibar_debug_wait_timeout(h, max_spins: int, stream: int) -> int:
     return load_library().fibar_debug_wait_timeout(h, max_spins, stream)
+
+
+def fibar_set_grid_share(h, sms: int) -> int:
+    return load_library().fibar_set_grid_share(h, sms)
 
 
 def fibar_readout_host_async(h, t_us: int, out_ptr: int, stream: int) -> int:
@@ -357,6 +363,10 @@ class Fibar:
         rc = fibar_readout_host_async(self.h, int(t_us), out.data_ptr(), self._s)
         self._rotate()
         self._check(rc)
+
+    def set_grid_share(self, sms: int) -> None:
+        """Size the handle's kernel grids for `sms` SMs (0: the whole device)."""
+        self._check(fibar_set_grid_share(self.h, int(sms)))
 
     def wait(self) -> None:
         self._check(fibar_wait(self.h, self._s))

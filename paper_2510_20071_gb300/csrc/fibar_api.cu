@@ -379,6 +379,13 @@ extern "C" int fibar_debug_wait_timeout(fibar_t *h, uint32_t max_spins, void *cu
     return FIBAR_OK;
 }
 
+extern "C" int fibar_set_grid_share(fibar_t *h, uint32_t sms)
+{
+    if (!h) return FIBAR_EINVAL;
+    h->kp.grid_sms = sms;
+    return FIBAR_OK;
+}
+
 extern "C" int fibar_set_pixel_gain(fibar_t *h, const float *gain, int on_device, void *cuda_stream)
 {
     if (!h) return FIBAR_EINVAL;

@@ -119,6 +119,7 @@ struct KParams {
     uint32_t nbuckets;           // buckets of 2^lb consecutive tiles
     int spatial, blur_mode;
     int chain_policy;            // temporal filter schedule: 0 auto (per piece), 1 walk, 2 scan
+    uint32_t grid_sms;           // SMs the handle's grids are sized for (0: all of the device)
 };
 
 struct SegTable {
@@ -328,6 +329,7 @@ cudaError_t launch_s1(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned
 cudaError_t launch_debug_counts(const KParams &kp, const Bufs &b, unsigned int *cnt,
                                 cudaStream_t s, unsigned long long &nl);
 int grid_for(int sms_mult);
+int grid_for(const KParams &kp, int sms_mult);  // the handle's share of the SMs
 // learned fill read-out of a handle (k_fill.cu)
 cudaError_t launch_fill_readout(const FillParams &fp, const KParams &kp, const Bufs &b, float *out, cudaStream_t s,
                                 unsigned long long &nl);

@@ -601,7 +601,7 @@ static cudaError_t walk_variant(const KParams &kp, const Bufs &b, const unsigned
     static std::atomic<unsigned long long> attr_done{0};
     const size_t smem = sizeof(BwSmem);
     if (cudaError_t e = smem_attr_once(attr_done, k_bwalk<kLinks, kS1, kGain>, smem)) return e;
-    return launch_pdl(k_bwalk<kLinks, kS1, kGain>, grid_for(2), BW_THREADS, smem, s, kp, b, sorted);
+    return launch_pdl(k_bwalk<kLinks, kS1, kGain>, grid_for(kp, 2), BW_THREADS, smem, s, kp, b, sorted);
 }
 
 cudaError_t launch_walk(const KParams &kp, const Bufs &b_in, const unsigned long long *sorted, unsigned sort_passes,

@@ -1179,16 +1179,16 @@ cudaError_t launch_det_counts(const KParams &kp, const Bufs &b, cudaStream_t s, 
     const size_t smem = sizeof(HistSmem);
     if (cudaError_t e = smem_attr_once(attr_done0, k_det_hist<0>, smem)) return e;
     if (cudaError_t e = smem_attr_once(attr_done1, k_det_hist<1>, smem)) return e;
-    if (cudaError_t e_ = launch_pdl(k_det_hist<0>, grid_for(HB_BLOCKS_PER_SM), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
+    if (cudaError_t e_ = launch_pdl(k_det_hist<0>, grid_for(kp, HB_BLOCKS_PER_SM), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
                                     b.det_base, b.det_prof, b.n_samples, (const unsigned short *)b.band_ctr))
         return e_;
-    if (cudaError_t e_ = launch_pdl(k_det_center, grid_for(2), 256, 0, s, kp, b.ctrl, (const unsigned short *)b.det_prof,
+    if (cudaError_t e_ = launch_pdl(k_det_center, grid_for(kp, 2), 256, 0, s, kp, b.ctrl, (const unsigned short *)b.det_prof,
                                     b.n_samples, b.band_ctr))
         return e_;
-    if (cudaError_t e_ = launch_pdl(k_det_hist<1>, grid_for(HB_BLOCKS_PER_SM), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
+    if (cudaError_t e_ = launch_pdl(k_det_hist<1>, grid_for(kp, HB_BLOCKS_PER_SM), 256, smem, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
                                     b.det_base, b.det_prof, b.n_samples, (const unsigned short *)b.band_ctr))
         return e_;
-    if (cudaError_t e_ = launch_pdl(k_det_init, grid_for(8), 256, 0, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
+    if (cudaError_t e_ = launch_pdl(k_det_init, grid_for(kp, 8), 256, 0, s, kp, b.ctrl, b.ring4, b.dMt, b.mt_rows,
                                     b.det_base, (const unsigned short *)b.band_ctr, b.E0, b.qout))
         return e_;
     return cudaGetLastError();
@@ -1206,7 +1206,7 @@ cudaError_t launch_det_pass1(const KParams &kp, const Bufs &b, cudaStream_t s, u
 {
     nl += 1;
     if (cudaError_t e = lane_smem_attr()) return e;
-    if (cudaError_t e_ = launch_pdl(k_det_pass1, grid_for(2), 32 * LR_WARPS, sizeof(LaneSmem) * LR_WARPS, s, kp,
+    if (cudaError_t e_ = launch_pdl(k_det_pass1, grid_for(kp, 2), 32 * LR_WARPS, sizeof(LaneSmem) * LR_WARPS, s, kp,
                                     b.ctrl, b.ring4, b.qout, b.E0, b.E1))
         return e_;
     return cudaGetLastError();
@@ -1216,10 +1216,10 @@ cudaError_t launch_det_pass2(const KParams &kp, const Bufs &b, cudaStream_t s, u
 {
     nl += 2;
     if (cudaError_t e = lane_smem_attr()) return e;
-    if (cudaError_t e_ = launch_pdl(k_det_pass2, grid_for(2), 32 * LR_WARPS, sizeof(LaneSmem) * LR_WARPS, s, kp,
+    if (cudaError_t e_ = launch_pdl(k_det_pass2, grid_for(kp, 2), 32 * LR_WARPS, sizeof(LaneSmem) * LR_WARPS, s, kp,
                                     b.ctrl, b.ring4, b.qout, b.E1, b.E2, b.merged, b.unm_bits, b.p2_ids))
         return e_;
-    if (cudaError_t e_ = launch_pdl(k_det_pass2w, grid_for(8), 256, 0, s, kp, b.ctrl, b.ring4, b.qout, b.E2,
+    if (cudaError_t e_ = launch_pdl(k_det_pass2w, grid_for(kp, 8), 256, 0, s, kp, b.ctrl, b.ring4, b.qout, b.E2,
                                     b.merged, b.unm_bits, b.p2_ids))
         return e_;
     return cudaGetLastError();

@@ -626,7 +626,7 @@ __global__ void k_fill_adam(float *theta, float *m, float *v, float *grad, const
     theta[i] -= lr * mh / (sqrtf(vh) + eps);
 }
 
-cudaError_t launch_fill(const FillParams &fp, const FillIO &io, cudaStream_t s, unsigned long long &nl);
+cudaError_t launch_fill(const FillParams &fp, const FillIO &io, cudaStream_t s, unsigned long long &nl, int max_ctas = 0);
 
 cudaError_t launch_fill_readout(const FillParams &fp, const KParams &kp, const Bufs &b, float *out, cudaStream_t s,
                                 unsigned long long &nl)
@@ -640,19 +640,19 @@ cudaError_t launch_fill_readout(const FillParams &fp, const KParams &kp, const B
     io.err = &b.ctrl->error;
     io.W = kp.W;
     io.H = kp.H;
-    return launch_fill(fp, io, s, nl);
+    return launch_fill(fp, io, s, nl, grid_for(kp, 1));
 }
 
 size_t fill_smem_bytes() { return sizeof(FillSmem); }
 size_t fill_train_smem_bytes() { return sizeof(TrainSmem); }
 
-cudaError_t launch_fill(const FillParams &fp, const FillIO &io, cudaStream_t s, unsigned long long &nl)
+cudaError_t launch_fill(const FillParams &fp, const FillIO &io, cudaStream_t s, unsigned long long &nl, int max_ctas)
 {
     nl += 1;
     static std::atomic<unsigned long long> attr_done{0};
     if (cudaError_t e = smem_attr_once(attr_done, k_fill, sizeof(FillSmem))) return e;
     const int units = ((int)((io.W + FL_OC - 1) / FL_OC)) * ((int)((io.H + FL_R - 1) / FL_R));
-    const int grid = std::min(grid_for(1), units);
+    const int grid = std::min(max_ctas > 0 ? max_ctas : grid_for(1), units);
     if (cudaError_t e = launch_pdl(k_fill, grid, FL_THREADS, sizeof(FillSmem), s, fp, io)) return e;
     return cudaGetLastError();
 }
@@ -740,7 +740,7 @@ extern "C" int fibar_fill_features(fibar_t *h, float *x, uint8_t *stale, void *c
         return FIBAR_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    k_fill_features<<<grid_for(4), 256, 0, s>>>(h->b.ctrl, h->b.L, h->b.last_pix, h->W, h->H, x, stale);
+    k_fill_features<<<grid_for(h->kp, 4), 256, 0, s>>>(h->b.ctrl, h->b.L, h->b.last_pix, h->W, h->H, x, stale);
     h->launches += 1;
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

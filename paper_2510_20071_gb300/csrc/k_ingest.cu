@@ -724,6 +724,13 @@ int grid_for(int mult)
     return n * mult;
 }
 
+int grid_for(const KParams &kp, int mult)
+{
+    const int all = grid_for(1);
+    const int sms = kp.grid_sms ? std::min((int)kp.grid_sms, all) : all;
+    return sms * mult;
+}
+
 cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, unsigned sort_passes,
                           cudaStream_t s, unsigned long long &nl)
 {
@@ -738,7 +745,7 @@ cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, u
         dh.bucket_start = b.bucket_start;
         dh.order = b.bucket_order;
     }
-    if (cudaError_t e_ = launch_pdl(k_decode, grid_for(DEC_BLOCKS_PER_SM), DEC_THREADS, smem, s, kp, t, b.ctrl, b.dec_status, b.rec[0],
+    if (cudaError_t e_ = launch_pdl(k_decode, grid_for(kp, DEC_BLOCKS_PER_SM), DEC_THREADS, smem, s, kp, t, b.ctrl, b.dec_status, b.rec[0],
                                     kp.spatial ? b.ring_pix : nullptr, dh)) return e_;
     return cudaGetLastError();
 }
@@ -753,11 +760,11 @@ cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsig
     const unsigned bucket_bits = kp.key_bits - kp.lb;
     const unsigned dbits = passes ? (bucket_bits + passes - 1) / passes : 1u;
     if (passes != 1)
-        if (cudaError_t e_ = launch_pdl(k_sort_hist, grid_for(2), 256, 0, s, b.ctrl, b.rec[0], passes, dbits, kp.lb,
+        if (cudaError_t e_ = launch_pdl(k_sort_hist, grid_for(kp, 2), 256, 0, s, b.ctrl, b.rec[0], passes, dbits, kp.lb,
                                         kp.nbuckets, b.sort_hist, b.sort_base, b.bucket_cnt, b.bucket_start))
             return e_;
     for (unsigned p = 0; p < passes; ++p) {
-        if (cudaError_t e_ = launch_pdl(k_sort_pass, grid_for(SORT_BLOCKS_PER_SM), SORT_THREADS, smem, s, b.ctrl, b.rec[p & 1],
+        if (cudaError_t e_ = launch_pdl(k_sort_pass, grid_for(kp, SORT_BLOCKS_PER_SM), SORT_THREADS, smem, s, b.ctrl, b.rec[p & 1],
                                         b.rec[(p + 1) & 1], p, dbits, kp.lb, epoch + p, b.sort_base, b.sort_rows,
                                         b.sort_rowflag, b.sort_gtot, b.sort_gflag, b.sort_gcount))
             return e_;

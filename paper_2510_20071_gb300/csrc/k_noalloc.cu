@@ -78,7 +78,7 @@ extern "C" int fibar_queue_counts_noalloc(fibar_t *h, uint32_t *cnt, int on_devi
     cudaStream_t s = (cudaStream_t)cuda_stream;
     e = cudaMemsetAsync(scratch, 0, npix * sizeof(unsigned), s);
     if (e == cudaSuccess && h->kp.spatial) {
-        k_queue_counts_scratch<<<grid_for(2), 256, 0, s>>>(h->kp, h->b.ctrl, h->b.ring_pix, scratch);
+        k_queue_counts_scratch<<<grid_for(h->kp, 2), 256, 0, s>>>(h->kp, h->b.ctrl, h->b.ring_pix, scratch);
         e = cudaGetLastError();
         h->launches += 1;
     }

@@ -192,7 +192,7 @@ cudaError_t launch_readout(const KParams &kp, const Bufs &b, float *out, cudaStr
         const bool aligned = ((uintptr_t)out & 15) == 0;
         if (aligned) {
             const size_t n4 = n / 4;
-            if (cudaError_t e_ = launch_pdl(k_copy, grid_for(4), 256, 0, s, (const float4 *)b.L, (float4 *)out, n4, b.L, out, n)) return e_;
+            if (cudaError_t e_ = launch_pdl(k_copy, grid_for(kp, 4), 256, 0, s, (const float4 *)b.L, (float4 *)out, n4, b.L, out, n)) return e_;
         } else {
             nl -= 1;
             return cudaMemcpyAsync(out, b.L, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
@@ -223,7 +223,7 @@ cudaError_t launch_debug_counts(const KParams &kp, const Bufs &b, unsigned int *
                                 unsigned long long &nl)
 {
     nl += 1;
-    if (cudaError_t e_ = launch_pdl(k_debug_counts, grid_for(2), 256, 0, s, kp, b.ctrl, b.ring_pix, cnt)) return e_;
+    if (cudaError_t e_ = launch_pdl(k_debug_counts, grid_for(kp, 2), 256, 0, s, kp, b.ctrl, b.ring_pix, cnt)) return e_;
     return cudaGetLastError();
 }
 

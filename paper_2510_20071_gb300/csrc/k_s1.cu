@@ -370,11 +370,11 @@ __global__ void __launch_bounds__(256) k_s1_apply(KParams kp, Bufs b)
 cudaError_t launch_s1(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl)
 {
     nl += 5;
-    if (cudaError_t e_ = launch_pdl(k_s1_pops, grid_for(4), 256, 0, s, kp, b)) return e_;
-    if (cudaError_t e_ = launch_pdl(k_s1_select, grid_for(2), SEL_THREADS, 0, s, kp, b)) return e_;
-    if (cudaError_t e_ = launch_pdl(k_s1_lb, grid_for(4), 256, 0, s, kp, b)) return e_;
-    if (cudaError_t e_ = launch_pdl(k_s1_blur, grid_for(4), 128, 0, s, kp, b)) return e_;
-    if (cudaError_t e_ = launch_pdl(k_s1_apply, grid_for(4), 256, 0, s, kp, b)) return e_;
+    if (cudaError_t e_ = launch_pdl(k_s1_pops, grid_for(kp, 4), 256, 0, s, kp, b)) return e_;
+    if (cudaError_t e_ = launch_pdl(k_s1_select, grid_for(kp, 2), SEL_THREADS, 0, s, kp, b)) return e_;
+    if (cudaError_t e_ = launch_pdl(k_s1_lb, grid_for(kp, 4), 256, 0, s, kp, b)) return e_;
+    if (cudaError_t e_ = launch_pdl(k_s1_blur, grid_for(kp, 4), 128, 0, s, kp, b)) return e_;
+    if (cudaError_t e_ = launch_pdl(k_s1_apply, grid_for(kp, 4), 256, 0, s, kp, b)) return e_;
     return cudaGetLastError();
 }
 

@@ -78,6 +78,64 @@ class _Stream:
     queue: list = field(default_factory=list)  # pending Requests, in arrival order
 
 
+class GridTuner:
+    """Chooses, per sensor shape, how many SMs a stream's kernels are sized for
+    (``fibar_set_grid_share``) when many streams are read out concurrently.
+
+    For a shape, ``tune`` reads out ``n_streams`` handles of that shape together
+    (``fibar_readout_batch``), each applying ``events_per_readout`` simulated events per
+    read-out, with every candidate share in turn, times the rounds with CUDA events and
+    keeps the share with the most events per second.  The choices are recorded in
+    ``table`` ((W, H) -> SMs, 0 = the whole device) and ``trials`` (the timings)."""
+
+    def __init__(self, candidates=None, rounds: int = 4, warm: int = 2, seed: int = 31):
+        import torch
+        self.torch = torch
+        self.sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        self.candidates = candidates or [0, self.sms // 2, self.sms // 4, self.sms // 8, self.sms // 16]
+        self.rounds, self.warm, self.seed = rounds, warm, seed
+        self.table: dict[tuple[int, int], int] = {}
+        self.trials: dict[tuple[int, int], list] = {}
+
+    def tune(self, W: int, H: int, n_streams: int, events_per_readout: int, **params) -> int:
+        import eventsim
+        torch = self.torch
+        per = max(1024, int(events_per_readout))
+        total = per * (self.warm + self.rounds) * len(self.candidates)
+        fibs = [Fibar(W, H, **params) for _ in range(n_streams)]
+        evs = [eventsim.simulate(W, H, total, scene="perlin", seed=self.seed + i, noise_frac=0.02, device="cuda")
+               for i in range(n_streams)]
+        stream = torch.cuda.current_stream()
+        trials = []
+        pos = 0
+        try:
+            for sms in self.candidates:
+                for f in fibs:
+                    f.set_grid_share(sms)
+                t0 = t1 = None
+                for r in range(self.warm + self.rounds):
+                    if r == self.warm:
+                        t0 = torch.cuda.Event(enable_timing=True)
+                        t0.record(stream)
+                    for f, ev in zip(fibs, evs):
+                        f.push(ev[pos:pos + per])
+                    readout_batch(fibs, [int(ev[pos + per - 1, 1]) for ev in evs], stream=stream)
+                    pos += per
+                t1 = torch.cuda.Event(enable_timing=True)
+                t1.record(stream)
+                t1.synchronize()
+                ms = t0.elapsed_time(t1)
+                trials.append({"sms": sms, "ms": round(ms, 4),
+                               "mev_s": round(n_streams * per * self.rounds / ms / 1e3, 2)})
+        finally:
+            for f in fibs:
+                f.close()
+        best = max(trials, key=lambda t: t["mev_s"])["sms"]
+        self.table[(W, H)] = best
+        self.trials[(W, H)] = trials
+        return best
+
+
 class Server:
     """Device-resident FIBAR streams behind one loop.
 
@@ -94,6 +152,7 @@ class Server:
         self.streams: dict[int, _Stream] = {}
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.batches = 0
+        self.grid_share: dict[tuple[int, int], int] = {}
 
     def admit(self, W: int, H: int, **params):
         """Create a stream's handle if its memory fits; returns its id or None."""
@@ -107,7 +166,17 @@ class Server:
             self.admission.refused += 1
             return None
         self.streams[sid] = _Stream(fib, W, H)
+        if (W, H) in self.grid_share:
+            fib.set_grid_share(self.grid_share[(W, H)])
         return sid
+
+    def set_grid_share(self, table: dict) -> None:
+        """Per sensor shape (W, H), the SMs its streams' kernels are sized for (see
+        :class:`GridTuner`); applies to admitted and future streams."""
+        self.grid_share.update(table)
+        for st in self.streams.values():
+            if (st.W, st.H) in table:
+                st.fib.set_grid_share(table[(st.W, st.H)])
 
     def release(self, sid: int) -> None:
         st = self.streams.pop(sid)

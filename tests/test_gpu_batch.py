@@ -24,8 +24,9 @@ def _streams(n, seconds, seed):
     return eventsim.mixed_streams(n, seconds, seed=seed, sensors=SENSORS, rate_lo=0.5e6, rate_hi=4e6)
 
 
-@pytest.mark.parametrize("mode", ["s2", "s1", "nsf"])
-def test_served_images_match_oracle_per_stream(oracle_mod, mode):
+@pytest.mark.parametrize("mode,sms", [("s2", 0), ("s1", 0), ("nsf", 0), ("s2", 1), ("s1", 3), ("nsf", 19)])
+def test_served_images_match_oracle_per_stream(oracle_mod, mode, sms):
+    """sms: the SMs every stream's grids are sized for (0: the whole device)."""
     from paper_2510_20071_gb300.serving import Server, latencies_ms
     params = dict(MODES[mode], c_on=0.2, c_off=0.2)
     streams = _streams(6, 0.008, seed=21)
@@ -33,6 +34,8 @@ def test_served_images_match_oracle_per_stream(oracle_mod, mode):
     sched = eventsim.serving_schedule(streams, reqs, tick_us=400)
     dev = [s["events"].cuda() for s in streams]
     srv = Server()
+    if sms:
+        srv.set_grid_share({(W, H): sms for W, H in SENSORS})
     sids = [srv.admit(s["W"], s["H"], **params) for s in streams]
     assert None not in sids
     steps = [[] for _ in streams]
@@ -67,6 +70,47 @@ def test_served_images_match_oracle_per_stream(oracle_mod, mode):
         assert st["events_applied"] == sum(s["events"].shape[0] for s in streams)
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("mode", ["s2", "s1", "nsf"])
+def test_grid_share_does_not_change_results(mode):
+    """Every stage's result is independent of its grid (grid-stride loops, work taken
+    from counters): a handle sized for 2 or 19 SMs gives the whole-device handle's
+    images and state bit for bit."""
+    from paper_2510_20071_gb300 import Fibar
+    W, H = 346, 260
+    ev = eventsim.simulate(W, H, 1_500_000, scene="perlin", seed=41, noise_frac=0.02)
+    cuts = [200_000, 700_000, 1_500_000]
+    params = dict(MODES[mode], c_on=0.2, c_off=0.2)
+    runs = []
+    for sms in (0, 2, 19):
+        f = Fibar(W, H, **params)
+        f.set_grid_share(sms)
+        imgs, lo = [], 0
+        try:
+            for hi in cuts:
+                f.push(ev[lo:hi].cuda())
+                imgs.append(f.readout(int(ev[hi - 1, 1])).cpu())
+                lo = hi
+            runs.append((imgs, f.state()))
+        finally:
+            f.close()
+    for imgs, state in runs[1:]:
+        for a, b in zip(runs[0][0], imgs):
+            assert torch.equal(a, b)
+        for k in runs[0][1]:
+            np.testing.assert_array_equal(np.asarray(runs[0][1][k]), np.asarray(state[k]), err_msg=k)
+
+
+def test_grid_share_tuner_records_a_choice_per_shape():
+    from paper_2510_20071_gb300.serving import GridTuner
+    t = GridTuner(candidates=[0, 8], rounds=2, warm=1)
+    for W, H in [(64, 48), (120, 90)]:
+        best = t.tune(W, H, 3, 20_000, c_on=0.2, c_off=0.2, spatial_filter=1, blur_mode=1)
+        assert best in (0, 8)
+        assert t.table[(W, H)] == best
+        assert [r["sms"] for r in t.trials[(W, H)]] == [0, 8]
+        assert all(r["ms"] > 0 and r["mev_s"] > 0 for r in t.trials[(W, H)])
 
 
 def _pushed_handles(streams, params):
