@@ -203,7 +203,8 @@ def run_batch(args, rank, world, local):
     # queue, and the timed ticks measure streams whose queues have filled
     w = min(max(args.warmup, 2 * len(sched) // 5), len(sched) - 1)
     t_sweep = sched[w][0] - 1
-    srv = Server()
+    use_graph = args.batch_path == "graph"
+    srv = Server(use_graph=use_graph)
     params = dict(c_on=0.2, c_off=0.2, spatial_filter=1, blur_mode=1)
     sids = [srv.admit(s["W"], s["H"], **params) for s in streams]
     if None in sids:
@@ -217,7 +218,7 @@ def run_batch(args, rank, world, local):
         # that shape as a batch holds on average are read out together, each at its
         # shape's mean events per read-out (100 Hz requests)
         from paper_2510_20071_gb300.serving import GridTuner
-        tuner = GridTuner()
+        tuner = GridTuner(use_graph=use_graph)
         shapes = {}
         for s in streams:
             shapes.setdefault((s["W"], s["H"]), []).append(s["events"].shape[0] / seconds)
@@ -233,8 +234,8 @@ def run_batch(args, rank, world, local):
         log(f"[rank {rank}] grid shares {tuning['sms']} ({tuning['seconds']} s)")
 
     def tick(T, pushes, reads):
-        for i, lo, hi in pushes:
-            srv.push(sids[i], streams[i]["events"][lo:hi])
+        # the tick's packet of every stream, in one library call
+        srv.push_ranges([(sids[i], streams[i]["events"], lo, hi) for i, lo, hi in pushes])
         rs = [srv.request(sids[i], t) for i, t in reads]
         srv.serve()
         return rs
@@ -269,8 +270,11 @@ def run_batch(args, rank, world, local):
     time.sleep(0.3)
     clocks = sampler.stop()
     st1 = srv.stats()
+    gstats = srv.group.stats() if srv.group is not None else None
     applied = st1["events_applied"] - st0["events_applied"]
     launches = st1["kernel_launches"] - st0["kernel_launches"]
+    if gstats:  # one k_group_begin per graph launch besides the members' chains
+        launches += st1["batches"] - st0["batches"]
     lat = sorted(latencies_ms(served))
     expect = sum(int((s["events"][:, 1] > t_sweep).sum().item()) for s in streams)
     if applied != expect:
@@ -306,6 +310,9 @@ def run_batch(args, rank, world, local):
                                "what": "device time from a batch's start to the request's image"},
         "host_ms": round(host_ms, 3),
         "grid_share_autotune": tuning,
+        "serving_path": (f"group graph: one launch per batch ({gstats['graph_kernels']} kernel nodes, "
+                         f"programmatic edges {'on' if gstats['programmatic_edges'] else 'off'}, "
+                         f"{gstats['builds']} capture(s))" if gstats else "fibar_readout_batch: host launches on 16 streams"),
         "batches": st1["batches"] - st0["batches"],
         "clocks": clocks,
         "gpu_launches": launches,
@@ -662,6 +669,8 @@ def main():
     ap.add_argument("--grid-share", type=int, default=None,
                     help="batch32: SMs every stream's grids are sized for (default: autotuned per shape)")
     ap.add_argument("--no-autotune", action="store_true", help="batch32: whole-device grids for every stream")
+    ap.add_argument("--batch-path", default="graph", choices=["graph", "streams"],
+                    help="batch32: one group-graph launch per batch, or host launches per stream")
     ap.add_argument("--calib-events", type=int, default=100_000_000,
                     help="calib: records in the recording (profiling runs use fewer)")
     args = ap.parse_args()

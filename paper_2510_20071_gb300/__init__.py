@@ -14,5 +14,6 @@ from .binding import (  # noqa: F401
     memory_bytes, readout_batch, relative_thresholds, fibar_relative_thresholds, fibar_set_pixel_gain,
     EXPORTED, STAGES, FibarStageTimes, FIBAR_FILL_NPARAMS, fill_forward, fibar_fill_set_weights,
     fibar_fill_features, fibar_fill_forward, fibar_fill_train_step, fibar_readout_host_async, fibar_wait,
-    fibar_set_grid_share,
+    fibar_set_grid_share, fibar_push_batch, push_batch, Group, FibarGroupStats, fibar_group_create,
+    fibar_group_readout, fibar_group_latency, fibar_group_stats, fibar_group_last_error, fibar_group_destroy,
 )

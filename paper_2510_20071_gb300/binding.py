@@ -27,7 +27,9 @@ EXPORTED = ["fibar_default_params", "fibar_create", "fibar_push_events", "fibar_
             "fibar_readout_batch", "fibar_memory_bytes", "fibar_relative_thresholds",
             "fibar_set_pixel_gain", "fibar_debug_wait_timeout", "fibar_push_events_many",
             "fibar_fill_set_weights", "fibar_fill_features", "fibar_fill_forward", "fibar_fill_train_step",
-            "fibar_readout_host_async", "fibar_wait", "fibar_set_grid_share"]
+            "fibar_readout_host_async", "fibar_wait", "fibar_set_grid_share", "fibar_push_batch",
+            "fibar_group_create", "fibar_group_readout", "fibar_group_latency", "fibar_group_stats",
+            "fibar_group_last_error", "fibar_group_destroy"]
 
 FIBAR_FILL_NPARAMS = 2769
 
@@ -56,6 +58,11 @@ class FibarStats(C.Structure):
                                           "detector_fix_steps", "s1_blurs", "detector_big_pops",
                                           "detector_ring_misses", "detector_recenters",
                                           "iir_walk_pieces", "iir_scan_pieces"]]
+
+
+class FibarGroupStats(C.Structure):
+    _fields_ = [("members", C.c_uint64), ("graph_launches", C.c_uint64), ("builds", C.c_uint64),
+                ("graph_kernels", C.c_uint64), ("programmatic_edges", C.c_int32)]
 
 
 class FibarStageTimes(C.Structure):
@@ -126,6 +133,20 @@ def load_library(build_if_missing: bool = True):
             lib.fibar_push_events_many.restype = C.c_int
             lib.fibar_set_grid_share.argtypes = [vp, C.c_uint32]
             lib.fibar_set_grid_share.restype = C.c_int
+            lib.fibar_push_batch.argtypes = [vp, vp, vp, C.c_size_t, C.c_int, vp, vp]
+            lib.fibar_push_batch.restype = C.c_int
+            lib.fibar_group_create.argtypes = [C.POINTER(vp), C.c_size_t, C.POINTER(vp)]
+            lib.fibar_group_create.restype = C.c_int
+            lib.fibar_group_readout.argtypes = [vp, vp, vp, vp, C.c_size_t, vp, vp, vp]
+            lib.fibar_group_readout.restype = C.c_int
+            lib.fibar_group_latency.argtypes = [vp, C.c_uint64, vp, C.c_size_t]
+            lib.fibar_group_latency.restype = C.c_int
+            lib.fibar_group_stats.argtypes = [vp, C.POINTER(FibarGroupStats)]
+            lib.fibar_group_stats.restype = C.c_int
+            lib.fibar_group_last_error.argtypes = [vp]
+            lib.fibar_group_last_error.restype = C.c_char_p
+            lib.fibar_group_destroy.argtypes = [vp]
+            lib.fibar_group_destroy.restype = None
             lib.fibar_readout_host_async.argtypes = [vp, C.c_uint64, vp, vp]
             lib.fibar_readout_host_async.restype = C.c_int
             lib.fibar_wait.argtypes = [vp, vp]
@@ -235,6 +256,41 @@ def fibar_debug_wait_timeout(h, max_spins: int, stream: int) -> int:
 
 def fibar_set_grid_share(h, sms: int) -> int:
     return load_library().fibar_set_grid_share(h, sms)
+
+
+def fibar_push_batch(hs_ptr: int, evs_ptr: int, ns_ptr: int, count: int, on_device: int, status_ptr,
+                     stream: int) -> int:
+    """Arrays by address: count handles, event-packet pointers (uint64) and sizes (size_t)."""
+    return load_library().fibar_push_batch(hs_ptr, evs_ptr, ns_ptr, count, on_device, status_ptr, stream)
+
+
+def fibar_group_create(hs):
+    g = C.c_void_p()
+    n = len(hs)
+    rc = load_library().fibar_group_create((C.c_void_p * n)(*hs), n, C.byref(g))
+    return rc, g
+
+
+def fibar_group_readout(g, members_ptr: int, t_ptr: int, outs_ptr: int, m: int, status_ptr, ticket_ptr,
+                        stream: int) -> int:
+    """Arrays by address: m uint32 member indices, uint64 times and image pointers."""
+    return load_library().fibar_group_readout(g, members_ptr, t_ptr, outs_ptr, m, status_ptr, ticket_ptr, stream)
+
+
+def fibar_group_latency(g, ticket: int, ms_ptr: int, m: int) -> int:
+    return load_library().fibar_group_latency(g, ticket, ms_ptr, m)
+
+
+def fibar_group_stats(g, st: FibarGroupStats) -> int:
+    return load_library().fibar_group_stats(g, C.byref(st))
+
+
+def fibar_group_last_error(g) -> str:
+    return load_library().fibar_group_last_error(g).decode()
+
+
+def fibar_group_destroy(g) -> None:
+    load_library().fibar_group_destroy(g)
 
 
 def fibar_readout_host_async(h, t_us: int, out_ptr: int, stream: int) -> int:
@@ -506,6 +562,111 @@ def readout_batch(fibars, t_us, outs=None, done_events=None, stream=None):
                 raise FibarError(status[i], f"handle {i}: {fibar_last_error(f.h)}")
         raise FibarError(rc, "fibar_readout_batch rejected the arguments")
     return outs
+
+
+def push_batch(fibars, packets, stream=None) -> None:
+    """Push device packets to several handles in one call (``fibar_push_batch``):
+    ``packets[k]`` (a contiguous CUDA (n, 2) int64 tensor) goes to ``fibars[k]``; a handle
+    may appear more than once (its packets in order)."""
+    import torch
+    n = len(fibars)
+    if len(packets) != n:
+        raise ValueError("one packet per entry")
+    hs = np.empty(n, np.uint64)
+    ptrs = np.empty(n, np.uint64)
+    ns = np.empty(n, np.uint64)
+    for k, (f, ev) in enumerate(zip(fibars, packets)):
+        if not ev.is_cuda or ev.dtype != torch.int64 or ev.dim() != 2 or ev.shape[1] != 2 or not ev.is_contiguous():
+            raise TypeError("packets must be contiguous CUDA (n, 2) int64 tensors")
+        hs[k] = f.h.value
+        ptrs[k] = ev.data_ptr()
+        ns[k] = ev.shape[0]
+    _push_arrays(fibars, packets, hs, ptrs, ns, stream)
+
+
+def _push_arrays(fibars, keep, hs, ptrs, ns, stream=None):
+    import torch
+    n = len(hs)
+    status = np.zeros(n, np.int32)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = fibar_push_batch(hs.ctypes.data, ptrs.ctypes.data, ns.ctypes.data, n, 1, status.ctypes.data, s.cuda_stream)
+    for f, ev in zip(fibars, keep):
+        f._keep.append(ev)
+    if rc != 0:
+        k = int(np.flatnonzero(status)[0]) if status.any() else 0
+        raise FibarError(rc, f"entry {k}: {fibar_last_error(fibars[k].h)}")
+
+
+class Group:
+    """A fixed set of :class:`Fibar` handles read out by one CUDA graph launch per call
+    (``fibar_group_*``).  Destroy (``close``) before the handles."""
+
+    def __init__(self, fibars):
+        if not fibars:
+            raise ValueError("a group needs at least one handle")
+        self.fibars = list(fibars)
+        rc, g = fibar_group_create([f.h.value for f in self.fibars])
+        if rc != 0:
+            raise FibarError(rc, "fibar_group_create failed")
+        self.g = g
+        self._tickets = {}
+
+    def _check(self, rc: int):
+        if rc != 0:
+            raise FibarError(rc, fibar_group_last_error(self.g))
+
+    def readout(self, members, t_us, outs, stream=None) -> int:
+        """Read out members (indices into the group) at t_us into outs (16-byte aligned
+        contiguous CUDA float32 tensors of each member's W*H); returns the launch's ticket."""
+        import torch
+        m = len(members)
+        if len(t_us) != m or len(outs) != m:
+            raise ValueError("one time and one output per member")
+        mem = np.asarray(members, dtype=np.uint32)
+        ts = np.asarray(t_us, dtype=np.uint64)
+        op = np.empty(m, np.uint64)
+        for k, (i, o) in enumerate(zip(members, outs)):
+            f = self.fibars[i]
+            if o.dtype != torch.float32 or not o.is_cuda or o.numel() != f.W * f.H or not o.is_contiguous():
+                raise TypeError("outs must be contiguous CUDA float32 tensors of W*H elements")
+            op[k] = o.data_ptr()
+        status = np.zeros(m, np.int32)
+        ticket = np.zeros(1, np.uint64)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rc = fibar_group_readout(self.g, mem.ctypes.data, ts.ctypes.data, op.ctypes.data, m, status.ctypes.data,
+                                 ticket.ctypes.data, s.cuda_stream)
+        if rc != 0:
+            bad = np.flatnonzero(status)
+            if bad.size:
+                i = int(members[int(bad[0])]) if int(bad[0]) < m else -1
+                detail = fibar_last_error(self.fibars[i].h) if 0 <= i < len(self.fibars) else ""
+                raise FibarError(rc, f"entry {int(bad[0])}: {fibar_group_last_error(self.g)} {detail}")
+            self._check(rc)
+        for i in members:
+            self.fibars[i]._rotate()
+        return int(ticket[0])
+
+    def latency_ms(self, ticket: int, m: int):
+        """Device ms from the launch's start to each of its m images (waits)."""
+        ms = np.zeros(m, np.float32)
+        self._check(fibar_group_latency(self.g, int(ticket), ms.ctypes.data, m))
+        return [float(x) for x in ms]
+
+    def stats(self) -> dict:
+        st = FibarGroupStats()
+        self._check(fibar_group_stats(self.g, st))
+        return {k: int(getattr(st, k)) for k, _ in st._fields_}
+
+    def close(self):
+        if getattr(self, "g", None):
+            fibar_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def relative_thresholds(ev, W: int, H: int, stream=None):

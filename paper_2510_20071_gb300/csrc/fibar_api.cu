@@ -338,7 +338,6 @@ extern "C" int fibar_create(uint32_t W, uint32_t H, const fibar_params_t *pp, fi
     h->commits = 0;
     h->pushed_since = 0;
     h->carry_slot = 0;
-    h->epoch = 1;
     h->have_readout = false;
     h->last_readout = 0;
     h->pushed = 0;
@@ -382,6 +381,7 @@ extern "C" int fibar_debug_wait_timeout(fibar_t *h, uint32_t max_spins, void *cu
 extern "C" int fibar_set_grid_share(fibar_t *h, uint32_t sms)
 {
     if (!h) return FIBAR_EINVAL;
+    if (h->kp.grid_sms != sms) h->config_version += 1;
     h->kp.grid_sms = sms;
     return FIBAR_OK;
 }
@@ -391,6 +391,7 @@ extern "C" int fibar_set_pixel_gain(fibar_t *h, const float *gain, int on_device
     if (!h) return FIBAR_EINVAL;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (!gain) {
+        if (h->b.gain) h->config_version += 1;
         h->b.gain = nullptr;
         return FIBAR_OK;
     }
@@ -414,6 +415,7 @@ extern "C" int fibar_set_pixel_gain(fibar_t *h, const float *gain, int on_device
                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_pixel_gain: copy");
+    if (h->b.gain != h->gain_buf) h->config_version += 1;
     h->b.gain = h->gain_buf;
     return FIBAR_OK;
 }
@@ -513,6 +515,20 @@ extern "C" int fibar_push_events(fibar_t *h, const fibar_event_t *ev, size_t n, 
     return FIBAR_OK;
 }
 
+extern "C" int fibar_push_batch(fibar_t *const *hs, const fibar_event_t *const *evs, const size_t *ns, size_t count,
+                                int on_device, int *status, void *cuda_stream)
+{
+    if (count == 0) return FIBAR_OK;
+    if (!hs || !evs || !ns) return FIBAR_EINVAL;
+    int first = FIBAR_OK;
+    for (size_t k = 0; k < count; ++k) {
+        const int rc = hs[k] ? fibar_push_events(hs[k], evs[k], ns[k], on_device, cuda_stream) : FIBAR_EINVAL;
+        if (status) status[k] = rc;
+        if (rc != FIBAR_OK && first == FIBAR_OK) first = rc;
+    }
+    return first;
+}
+
 extern "C" int fibar_push_events_many(fibar_t *h, const fibar_event_t *const *evs, const size_t *ns, size_t count,
                                       int on_device, void *cuda_stream)
 {
@@ -556,9 +572,9 @@ struct StageMarks {
     fibar_t *h;
     cudaStream_t s;
     cudaEvent_t *e;
-    explicit StageMarks(fibar_t *h_, cudaStream_t s_) : h(h_), s(s_), e(nullptr)
+    StageMarks(fibar_t *h_, cudaStream_t s_, bool on) : h(h_), s(s_), e(nullptr)
     {
-        if (!h->timing) return;
+        if (!on || !h->timing) return;
         if (h->ev_used == EV_SETS) fold_stage_events(h);
         e = &h->ev_pool[(size_t)h->ev_used * (FIBAR_NSTAGES + 1)];
         h->ev_used += 1;
@@ -569,12 +585,13 @@ struct StageMarks {
     }
 };
 
-// Enqueue the whole per-read-out pipeline.  out == nullptr: apply only (flush).
-int process(fibar_t *h, unsigned long long t_read, float *out, cudaStream_t s)
+}  // namespace
+
+namespace fibar {
+
+// The pending packets of the next read-out, as its decode takes them.
+void fill_segtable(const fibar_t *h, unsigned long long t_read, SegTable &T)
 {
-    const KParams &kp = h->kp;
-    const Bufs &b = h->b;
-    SegTable T;
     memset(&T, 0, sizeof(T));
     T.nseg = (unsigned)h->seg_ptr.size();
     for (unsigned i = 0; i < T.nseg; ++i) {
@@ -582,23 +599,29 @@ int process(fibar_t *h, unsigned long long t_read, float *out, cudaStream_t s)
         T.n[i] = h->seg_n[i];
     }
     T.carry_slot = (unsigned)h->carry_slot;
-    T.carry = b.carry[h->carry_slot];
-    T.carry_out = b.carry[1 - h->carry_slot];
+    T.carry = h->b.carry[h->carry_slot];
+    T.carry_out = h->b.carry[1 - h->carry_slot];
     T.t_read = t_read;
-    unsigned long long &nl = h->launches;
-    StageMarks mk(h, s);
+}
 
-    cudaError_t e = cudaSuccess;
-    if (h->copy_pending) {
-        // the read-out's host packets, copied on the internal stream
-        e = cudaEventRecord(h->ev_copied, h->copy_stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_copied, 0);
-        if (e != cudaSuccess) return cuda_fail(h, e, "wait for the host packets");
-    }
+// The kernels of one read-out, in order (out == nullptr: apply only, a flush).  With a
+// descriptor d (a chain captured into a group's graph) the decode, the image and the
+// commit take the read-out's table, image pointer and carry slot from device memory
+// instead of T and out; nothing else of a read-out changes from call to call.
+int enqueue_readout_chain(fibar_t *h, const SegTable &T, float *out, const ReadDesc *d, cudaStream_t s,
+                          bool stage_marks)
+{
+    const KParams &kp = h->kp;
+    const Bufs &b = h->b;
+    unsigned long long &nl = h->launches;
+    StageMarks mk(h, stage_marks ? s : nullptr, stage_marks);
+    const SegTable *tdev = d ? &d->t : nullptr;
+    float *const *outp = d ? &d->out : nullptr;
+
     mk.mark(FIBAR_STAGE_DECODE);
-    e = launch_decode(kp, b, T, h->sort_passes, s, nl);
+    cudaError_t e = launch_decode(kp, b, T, h->sort_passes, s, nl, tdev);
     if (e != cudaSuccess) return cuda_fail(h, e, "decode");
-    if (h->copy_pending) {
+    if (h->copy_pending && !d) {
         // the staging buffer is free again once the decode has run; the next host packets
         // go to the other one
         e = cudaEventRecord(h->ev_free[h->staging_cur], s);
@@ -607,8 +630,7 @@ int process(fibar_t *h, unsigned long long t_read, float *out, cudaStream_t s)
         h->copy_pending = false;
     }
     mk.mark(FIBAR_STAGE_SORT);
-    e = launch_sort(kp, b, h->sort_passes, h->epoch, s, nl);
-    h->epoch += SORT_MAX_PASSES;
+    e = launch_sort(kp, b, h->sort_passes, s, nl);
     if (e != cudaSuccess) return cuda_fail(h, e, "sort");
     const unsigned long long *sorted = b.rec[h->sort_passes & 1];
     mk.mark(FIBAR_STAGE_WALK);
@@ -629,23 +651,49 @@ int process(fibar_t *h, unsigned long long t_read, float *out, cudaStream_t s)
         if (e != cudaSuccess) return cuda_fail(h, e, "S1 blur");
     }
     mk.mark(FIBAR_STAGE_READOUT);
-    if (out) {
+    if (out || d) {
         if (kp.spatial && kp.blur_mode == 2 && h->fill)
-            e = launch_fill_readout(*h->fill, kp, b, out, s, nl);
+            e = launch_fill_readout(*h->fill, kp, b, out, s, nl, outp);
         else
-            e = launch_readout(kp, b, out, s, nl);
+            e = launch_readout(kp, b, out, s, nl, outp);
         if (e != cudaSuccess) return cuda_fail(h, e, "readout");
     }
     mk.mark(FIBAR_STAGE_COMMIT);
-    h->carry_slot = 1 - h->carry_slot;
-    e = launch_commit(kp, b, h->carry_slot, s, nl);
+    e = launch_commit(kp, b, 1 - (int)T.carry_slot, s, nl, d);
     if (e != cudaSuccess) return cuda_fail(h, e, "commit");
     mk.mark(FIBAR_NSTAGES);
+    return FIBAR_OK;
+}
+
+// Host bookkeeping once a read-out's (or flush's) kernels are enqueued.
+void readout_committed(fibar_t *h)
+{
+    h->carry_slot = 1 - h->carry_slot;
     h->seg_ptr.clear();
     h->seg_n.clear();
     h->staging_used = 0;
     h->commits += 1;
     h->pushed_since = 0;
+}
+
+}  // namespace fibar
+
+namespace {
+
+// Enqueue the whole per-read-out pipeline.  out == nullptr: apply only (flush).
+int process(fibar_t *h, unsigned long long t_read, float *out, cudaStream_t s)
+{
+    SegTable T;
+    fill_segtable(h, t_read, T);
+    if (h->copy_pending) {
+        // the read-out's host packets, copied on the internal stream
+        cudaError_t e = cudaEventRecord(h->ev_copied, h->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_copied, 0);
+        if (e != cudaSuccess) return cuda_fail(h, e, "wait for the host packets");
+    }
+    const int rc = enqueue_readout_chain(h, T, out, nullptr, s, true);
+    if (rc) return rc;
+    readout_committed(h);
     return FIBAR_OK;
 }
 

@@ -132,6 +132,14 @@ struct SegTable {
     unsigned long long t_read;
 };
 
+// One read-out of a handle as a captured read-out chain sees it: what changes from one
+// read-out to the next, in device memory, written before the chain runs.
+struct ReadDesc {
+    SegTable t;
+    float *out;                  // the image (16-byte aligned)
+    unsigned long long *stamp;   // if set: %globaltimer (ns) once the read-out has committed
+};
+
 struct Bufs {
     Ctrl *ctrl;
     float *pbar, *L;
@@ -224,7 +232,6 @@ struct fibar_s {
     unsigned long long commits;         // read-outs and flushes launched
     unsigned long long pushed_since;    // records pushed since the last read-out or flush
     int carry_slot;
-    unsigned int epoch;
     bool have_readout;
     unsigned long long last_readout;
     unsigned long long pushed, readouts;
@@ -237,6 +244,9 @@ struct fibar_s {
     unsigned ev_used;            // read-outs recorded in ev_pool
     double stage_ms[FIBAR_NSTAGES];
     unsigned long long stage_calls;
+    // bumped by every change of what a read-out chain launches (grid share, gains, fill
+    // weights), so that a group's captured chains can be rebuilt
+    unsigned long long config_version;
 };
 
 namespace fibar {
@@ -251,6 +261,10 @@ namespace fibar {
         asm volatile("griddepcontrol.launch_dependents;" :::);   \
     } while (0)
 
+// Launches of this thread carry the PDL attribute (cleared while a chain is captured
+// into a graph whose edges may not take it).
+inline thread_local bool pdl_enabled = true;
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args &&...args)
@@ -264,7 +278,7 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl_enabled ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
@@ -311,10 +325,11 @@ inline cudaError_t smem_attr_once(std::atomic<unsigned long long> &done, void (*
 cudaError_t launch_init(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
 cudaError_t launch_probe_wait(const Bufs &b, const unsigned *flag, unsigned max_spins, cudaStream_t s,
                               unsigned long long &nl);
+// tdev / outp / d (captured chains): the read-out's table, image pointer and descriptor
+// in device memory, used instead of t / out
 cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, unsigned sort_passes, cudaStream_t s,
-                          unsigned long long &nl);
-cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsigned epoch,
-                        cudaStream_t s, unsigned long long &nl);
+                          unsigned long long &nl, const SegTable *tdev = nullptr);
+cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, cudaStream_t s, unsigned long long &nl);
 cudaError_t launch_walk(const KParams &kp, const Bufs &b, const unsigned long long *sorted, unsigned sort_passes,
                         cudaStream_t s, unsigned long long &nl);
 cudaError_t launch_det_counts(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
@@ -322,9 +337,9 @@ cudaError_t launch_det_pass1(const KParams &kp, const Bufs &b, cudaStream_t s, u
 cudaError_t launch_det_pass2(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
 cudaError_t launch_det_fix(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
 cudaError_t launch_readout(const KParams &kp, const Bufs &b, float *out, cudaStream_t s,
-                           unsigned long long &nl);
+                           unsigned long long &nl, float *const *outp = nullptr);
 cudaError_t launch_commit(const KParams &kp, const Bufs &b, int next_carry_slot, cudaStream_t s,
-                          unsigned long long &nl);
+                          unsigned long long &nl, const ReadDesc *d = nullptr);
 cudaError_t launch_s1(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned long long &nl);
 cudaError_t launch_debug_counts(const KParams &kp, const Bufs &b, unsigned int *cnt,
                                 cudaStream_t s, unsigned long long &nl);
@@ -332,5 +347,10 @@ int grid_for(int sms_mult);
 int grid_for(const KParams &kp, int sms_mult);  // the handle's share of the SMs
 // learned fill read-out of a handle (k_fill.cu)
 cudaError_t launch_fill_readout(const FillParams &fp, const KParams &kp, const Bufs &b, float *out, cudaStream_t s,
-                                unsigned long long &nl);
+                                unsigned long long &nl, float *const *outp = nullptr);
+// the kernels of one read-out (fibar_api.cu); d != nullptr: a chain captured for a group
+int enqueue_readout_chain(fibar_t *h, const SegTable &T, float *out, const ReadDesc *d, cudaStream_t s,
+                          bool stage_marks);
+void fill_segtable(const fibar_t *h, unsigned long long t_read, SegTable &T);
+void readout_committed(fibar_t *h);
 }  // namespace fibar

@@ -84,6 +84,7 @@ struct FillIO {
     const float *x;                        // explicit: [2][H][W]
     const unsigned char *stale;            // explicit: [H][W] (1 = fill)
     float *out;                            // [H][W]
+    float *const *outp;                    // if set: where to find out (a captured chain's descriptor)
     unsigned *err;                         // error word (bit ERR_FILL_WAIT)
     unsigned W, H;
 };
@@ -192,6 +193,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1) k_fill(FillParams fp, FillIO io
     extern __shared__ __align__(1024) unsigned char fl_smem_raw[];
     FillSmem &S = *reinterpret_cast<FillSmem *>(fl_smem_raw);
     const int W = (int)io.W, H = (int)io.H;
+    float *const fout = io.outp ? *io.outp : io.out;
     const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nseg = (W + FL_OC - 1) / FL_OC, nstrip = (H + FL_R - 1) / FL_R;
     const int units = nseg * nstrip;
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(FL_THREADS, 1) k_fill(FillParams fp, FillIO io
             for (int o = (int)(warp >> 2); o < FL_R; o += FL_THREADS / 128) {
                 const float y = fl_tmem_ld1(tmem + ((32u * (warp & 3)) << 16) + FL_T3 + 16u * (o + 2)) + fp.b3;
                 const int gy = y0 + o;
-                if (px < FL_OC && gx < W && gy < H) io.out[(size_t)gy * W + gx] = S.stale[o][px] ? y : S.lout[o][px];
+                if (px < FL_OC && gx < W && gy < H) fout[(size_t)gy * W + gx] = S.stale[o][px] ? y : S.lout[o][px];
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -629,7 +631,7 @@ __global__ void k_fill_adam(float *theta, float *m, float *v, float *grad, const
 cudaError_t launch_fill(const FillParams &fp, const FillIO &io, cudaStream_t s, unsigned long long &nl, int max_ctas = 0);
 
 cudaError_t launch_fill_readout(const FillParams &fp, const KParams &kp, const Bufs &b, float *out, cudaStream_t s,
-                                unsigned long long &nl)
+                                unsigned long long &nl, float *const *outp)
 {
     FillIO io{};
     io.from_handle = 1;
@@ -637,6 +639,7 @@ cudaError_t launch_fill_readout(const FillParams &fp, const KParams &kp, const B
     io.L = b.L;
     io.last_pix = b.last_pix;
     io.out = out;
+    io.outp = outp;
     io.err = &b.ctrl->error;
     io.W = kp.W;
     io.H = kp.H;
@@ -708,6 +711,7 @@ int pack_fill_params(const float *theta, FillParams *fp)
 extern "C" int fibar_fill_set_weights(fibar_t *h, const float *theta, size_t n)
 {
     if (!h) return FIBAR_EINVAL;
+    h->config_version += 1;  // a captured read-out chain holds the weights by value
     if (!theta) {
         delete h->fill;
         h->fill = nullptr;

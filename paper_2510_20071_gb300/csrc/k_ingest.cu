@@ -134,33 +134,14 @@ __device__ __forceinline__ unsigned long long dpack(unsigned flag, DAgg a)
 }
 
 // Segment holding record pos (pos >= carry_n): the last segment starting at or before it.
-__device__ __forceinline__ int seg_of(const SegTable &T, const unsigned *s_start, unsigned pos)
+__device__ __forceinline__ int seg_of(unsigned nseg, const unsigned *s_start, unsigned pos)
 {
-    int lo = 0, hi = (int)T.nseg - 1;
+    int lo = 0, hi = (int)nseg - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (s_start[mid] <= pos) lo = mid; else hi = mid - 1;
     }
     return lo;
-}
-
-__device__ __forceinline__ int4 fetch_rec(const SegTable &T, const int4 *const *s_ptr,
-                                          const unsigned *s_start, unsigned carry_n, unsigned pos)
-{
-    if (pos < carry_n) return __ldg(T.carry + pos);
-    const int sg = seg_of(T, s_start, pos);
-    return __ldg(s_ptr[sg] + (pos - s_start[sg]));
-}
-
-// The same, starting the segment search from the segment of an earlier record of the
-// tile (a tile spans one or two packets almost always).
-__device__ __forceinline__ int4 fetch_rec_from(const SegTable &T, const int4 *const *s_ptr,
-                                               const unsigned *s_start, unsigned carry_n, unsigned pos,
-                                               int sg)
-{
-    if (pos < carry_n) return __ldg(T.carry + pos);
-    while (sg + 1 < (int)T.nseg && s_start[sg + 1] <= pos) ++sg;
-    return __ldg(s_ptr[sg] + (pos - s_start[sg]));
 }
 
 // Shared-memory index of tile position r: one word of padding per DEC_PER_THREAD, so that
@@ -178,10 +159,17 @@ struct DecHist {
 };
 
 __global__ void __launch_bounds__(DEC_THREADS)
-k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigned long long *rec_out,
-         unsigned *ring_pix, DecHist dh)
+k_decode(KParams kp, const __grid_constant__ SegTable T, const SegTable *Tdev, Ctrl *ctrl,
+         unsigned long long *status, unsigned long long *rec_out, unsigned *ring_pix, DecHist dh)
 {
     PDL_ENTRY();
+    // the read-out's packets: the launch's own table, or (a captured read-out chain) the
+    // table written to device memory before the chain runs
+    const SegTable &TS = Tdev ? *Tdev : T;
+    const unsigned nseg = TS.nseg, carry_slot = TS.carry_slot;
+    const int4 *const carry = TS.carry;
+    int4 *const carry_out = TS.carry_out;
+    const unsigned long long t_read = TS.t_read;
     extern __shared__ __align__(128) int4 s_rec[];  // the tile's records (DEC_TILE)
     __shared__ __align__(8) unsigned long long s_bar;
     __shared__ unsigned s_start[MAXSEG + 1];
@@ -194,20 +182,20 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
     __shared__ unsigned s_hb[RADIX];  // kept records per bucket (this tile)
     __shared__ bool s_hlast;
 
-    const unsigned carry_n = ctrl->carry_n[T.carry_slot];
+    const unsigned carry_n = ctrl->carry_n[carry_slot];
     if (threadIdx.x == 0) {
         unsigned acc = carry_n;
-        for (unsigned i = 0; i < T.nseg; ++i) {
+        for (unsigned i = 0; i < nseg; ++i) {
             s_start[i] = acc;
-            s_ptr[i] = T.ptr[i];
-            acc += T.n[i];
+            s_ptr[i] = TS.ptr[i];
+            acc += TS.n[i];
         }
-        s_start[T.nseg] = acc;
+        s_start[nseg] = acc;
         mbar_init(&s_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const unsigned total = s_start[T.nseg];
+    const unsigned total = s_start[nseg];
     const unsigned ntiles = (total + DEC_TILE - 1) / DEC_TILE;
     unsigned phase = 0;
     const bool hist = dh.ghist != nullptr;
@@ -279,13 +267,13 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
             unsigned p = pos0;
             if (p < carry_n) {
                 const unsigned e = min(pos1, carry_n);
-                bulk_g2s(s_rec, T.carry + p, (e - p) * 16u, &s_bar);
+                bulk_g2s(s_rec, carry + p, (e - p) * 16u, &s_bar);
                 p = e;
             }
             if (p < pos1) {
-                int sg = seg_of(T, s_start, p);
+                int sg = seg_of(nseg, s_start, p);
                 while (p < pos1) {
-                    while (sg + 1 < (int)T.nseg && s_start[sg + 1] <= p) ++sg;
+                    while (sg + 1 < (int)nseg && s_start[sg + 1] <= p) ++sg;
                     const unsigned e = min(pos1, s_start[sg + 1]);
                     bulk_g2s(s_rec + (p - pos0), s_ptr[sg] + (p - s_start[sg]), (e - p) * 16u, &s_bar);
                     p = e;
@@ -306,7 +294,7 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
                 const int p = (int)(signed char)(e.y & 0xFF);
                 const unsigned long long t =
                     ((unsigned long long)(unsigned)e.w << 32) | (unsigned)e.z;
-                if (t > T.t_read) vloc = min(vloc, r);
+                if (t > t_read) vloc = min(vloc, r);
                 const bool valid = x < kp.W && y < kp.H;
                 const unsigned tid_ = valid ? (y >> 1) * kp.tiles_w + (x >> 1) : 0u;
                 const unsigned sub = valid ? (((y & 1u) << 1) | (x & 1u)) : 0u;
@@ -374,7 +362,7 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
                     const unsigned s = inc.s == S_NONE ? total : inc.s;
                     ctrl->m = inc.c;
                     ctrl->consumed = s;
-                    ctrl->carry_n[1 - T.carry_slot] = total - s;
+                    ctrl->carry_n[1 - carry_slot] = total - s;
                 }
             }
         }
@@ -414,14 +402,14 @@ k_decode(KParams kp, SegTable T, Ctrl *ctrl, unsigned long long *status, unsigne
                 for (int i = 0; i < DEC_PER_THREAD; ++i) {
                     const unsigned r = i * DEC_THREADS + threadIdx.x;
                     const unsigned pos = pos0 + r;
-                    if (r >= vfirst && pos < total) T.carry_out[pos - s] = s_rec[r];
+                    if (r >= vfirst && pos < total) carry_out[pos - s] = s_rec[r];
                 }
             }
         } else {
             for (int i = 0; i < DEC_PER_THREAD; ++i) {
                 const unsigned r = i * DEC_THREADS + threadIdx.x;
                 const unsigned pos = pos0 + r;
-                if (pos < total) T.carry_out[pos - pre_s] = s_rec[r];
+                if (pos < total) carry_out[pos - pre_s] = s_rec[r];
             }
         }
         if (hist) {
@@ -555,10 +543,13 @@ struct SortSmem {
 
 __global__ void __launch_bounds__(SORT_THREADS)
 k_sort_pass(Ctrl *ctrl, const unsigned long long *in, unsigned long long *out, unsigned pass,
-            unsigned dbits, unsigned lb, unsigned epoch, const unsigned *gbase, unsigned *rows, unsigned *rowflag,
+            unsigned dbits, unsigned lb, const unsigned *gbase, unsigned *rows, unsigned *rowflag,
             unsigned *gtot, unsigned *gflag, unsigned *gcount)
 {
     PDL_ENTRY();
+    // flag value of this pass: distinct for every pass of every read-out (the commit
+    // counter starts at 1), so that no flag needs clearing between read-outs
+    const unsigned epoch = (ctrl->batch_no - 1u) * SORT_MAX_PASSES + 1u + pass;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem &S = *reinterpret_cast<SortSmem *>(smem_raw);
     const unsigned m = ctrl->m;
@@ -732,7 +723,7 @@ int grid_for(const KParams &kp, int mult)
 }
 
 cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, unsigned sort_passes,
-                          cudaStream_t s, unsigned long long &nl)
+                          cudaStream_t s, unsigned long long &nl, const SegTable *tdev)
 {
     nl += 1;
     static std::atomic<unsigned long long> attr_done{0};
@@ -745,13 +736,12 @@ cudaError_t launch_decode(const KParams &kp, const Bufs &b, const SegTable &t, u
         dh.bucket_start = b.bucket_start;
         dh.order = b.bucket_order;
     }
-    if (cudaError_t e_ = launch_pdl(k_decode, grid_for(kp, DEC_BLOCKS_PER_SM), DEC_THREADS, smem, s, kp, t, b.ctrl, b.dec_status, b.rec[0],
+    if (cudaError_t e_ = launch_pdl(k_decode, grid_for(kp, DEC_BLOCKS_PER_SM), DEC_THREADS, smem, s, kp, t, tdev, b.ctrl, b.dec_status, b.rec[0],
                                     kp.spatial ? b.ring_pix : nullptr, dh)) return e_;
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsigned epoch,
-                        cudaStream_t s, unsigned long long &nl)
+cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, cudaStream_t s, unsigned long long &nl)
 {
     nl += (passes == 1 ? 0 : 1) + passes;  // one pass: the decode counted the digits
     static std::atomic<unsigned long long> attr_done{0};
@@ -765,7 +755,7 @@ cudaError_t launch_sort(const KParams &kp, const Bufs &b, unsigned passes, unsig
             return e_;
     for (unsigned p = 0; p < passes; ++p) {
         if (cudaError_t e_ = launch_pdl(k_sort_pass, grid_for(kp, SORT_BLOCKS_PER_SM), SORT_THREADS, smem, s, b.ctrl, b.rec[p & 1],
-                                        b.rec[(p + 1) & 1], p, dbits, kp.lb, epoch + p, b.sort_base, b.sort_rows,
+                                        b.rec[(p + 1) & 1], p, dbits, kp.lb, b.sort_base, b.sort_rows,
                                         b.sort_rowflag, b.sort_gtot, b.sort_gflag, b.sort_gcount))
             return e_;
     }

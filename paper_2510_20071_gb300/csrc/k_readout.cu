@@ -16,9 +16,10 @@ constexpr int RB_TY = RB_Y * RB_ROWS;
 
 __global__ void __launch_bounds__(RB_X *RB_Y)
 k_readout_s2(KParams kp, const Ctrl *ctrl, const float *__restrict__ L,
-             const unsigned long long *__restrict__ last_pix, float *__restrict__ out)
+             const unsigned long long *__restrict__ last_pix, float *out_arg, float *const *outp)
 {
     PDL_ENTRY();
+    float *__restrict__ out = outp ? *outp : out_arg;  // outp: a captured chain's descriptor
     __shared__ float t[RB_TY + 2][RB_X + 2];
     __shared__ float hs[RB_TY + 2][RB_X];
     const int x0 = blockIdx.x * RB_X, y0 = blockIdx.y * RB_TY;
@@ -60,10 +61,12 @@ k_readout_s2(KParams kp, const Ctrl *ctrl, const float *__restrict__ L,
     }
 }
 
-__global__ void k_copy(const float4 *__restrict__ in, float4 *__restrict__ out, size_t n4,
-                       const float *__restrict__ in1, float *__restrict__ out1, size_t n)
+__global__ void k_copy(const float4 *__restrict__ in, float4 *out_arg, size_t n4,
+                       const float *__restrict__ in1, float *out1_arg, size_t n, float *const *outp)
 {
     PDL_ENTRY();
+    float4 *__restrict__ out = outp ? reinterpret_cast<float4 *>(*outp) : out_arg;
+    float *__restrict__ out1 = outp ? *outp : out1_arg;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
         out[i] = in[i];
     const size_t tail = n4 * 4;
@@ -72,9 +75,11 @@ __global__ void k_copy(const float4 *__restrict__ in, float4 *__restrict__ out, 
 
 // After the last kernel of a read-out: base += m, reset tickets and look-back status.
 __global__ void k_commit(Ctrl *ctrl, unsigned long long *dec_status, size_t n_status, int next_carry_slot,
-                         unsigned *snap)
+                         unsigned *snap, const ReadDesc *d)
 {
     PDL_ENTRY();
+    // a captured chain: the slot follows from the descriptor's table
+    if (d) next_carry_slot = 1 - (int)d->t.carry_slot;
     for (size_t i = threadIdx.x; i < n_status; i += blockDim.x) dec_status[i] = 0ull;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -107,6 +112,11 @@ __global__ void k_commit(Ctrl *ctrl, unsigned long long *dec_status, size_t n_st
         snap[2] = ctrl->error;
         __threadfence_system();
         *(volatile unsigned *)&snap[1] = ctrl->batch_no - 1u;
+        if (d && d->stamp) {
+            unsigned long long ns;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(ns));
+            *(volatile unsigned long long *)d->stamp = ns;
+        }
     }
 }
 
@@ -181,18 +191,22 @@ cudaError_t launch_init(const KParams &kp, const Bufs &b, cudaStream_t s, unsign
 }
 
 cudaError_t launch_readout(const KParams &kp, const Bufs &b, float *out, cudaStream_t s,
-                           unsigned long long &nl)
+                           unsigned long long &nl, float *const *outp)
 {
     nl += 1;
     if (kp.spatial && kp.blur_mode >= 1) {  // S2, and the learned fill's Gaussian fallback
         dim3 grid((kp.W + RB_X - 1) / RB_X, (kp.H + RB_TY - 1) / RB_TY);
-        if (cudaError_t e_ = launch_pdl(k_readout_s2, grid, RB_X * RB_Y, 0, s, kp, b.ctrl, b.L, b.last_pix, out)) return e_;
+        if (cudaError_t e_ = launch_pdl(k_readout_s2, grid, RB_X * RB_Y, 0, s, kp, b.ctrl, b.L, b.last_pix, out, outp))
+            return e_;
     } else {
         const size_t n = kp.npix;
-        const bool aligned = ((uintptr_t)out & 15) == 0;
+        // a captured chain's output (outp) is 16-byte aligned by contract
+        const bool aligned = outp || ((uintptr_t)out & 15) == 0;
         if (aligned) {
             const size_t n4 = n / 4;
-            if (cudaError_t e_ = launch_pdl(k_copy, grid_for(kp, 4), 256, 0, s, (const float4 *)b.L, (float4 *)out, n4, b.L, out, n)) return e_;
+            if (cudaError_t e_ = launch_pdl(k_copy, grid_for(kp, 4), 256, 0, s, (const float4 *)b.L, (float4 *)out, n4,
+                                            b.L, out, n, outp))
+                return e_;
         } else {
             nl -= 1;
             return cudaMemcpyAsync(out, b.L, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
@@ -210,12 +224,12 @@ cudaError_t launch_probe_wait(const Bufs &b, const unsigned *flag, unsigned max_
 }
 
 cudaError_t launch_commit(const KParams &kp, const Bufs &b, int next_carry_slot, cudaStream_t s,
-                          unsigned long long &nl)
+                          unsigned long long &nl, const ReadDesc *d)
 {
     nl += 1;
     (void)kp;
     if (cudaError_t e_ = launch_pdl(k_commit, 1, 256, 0, s, b.ctrl, b.dec_status, b.max_dec_tiles, next_carry_slot,
-                                    b.snap)) return e_;
+                                    b.snap, d)) return e_;
     return cudaGetLastError();
 }
 

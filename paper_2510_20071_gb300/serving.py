@@ -4,10 +4,13 @@ device memory, and read-out requests answered in concurrent batches.
 The paper reconstructs one camera and states that an image can be read out at any time
 (Sec. 1).  A server holds one library handle per admitted stream (its filter state, queue
 and rings stay in device memory between calls), pushes each stream's packets as they
-arrive, and answers read-out requests for arbitrary times: the requests that are due are
-issued together through ``fibar_readout_batch``, so the pipelines of different streams run
-side by side on the GPU.  Every request gets a CUDA event recorded when its image is
-complete; its latency is the device time from the batch's start to that event.
+arrive, and answers read-out requests for arbitrary times.  The requests that are due are
+served together: by default as one launch of a group graph (``fibar_group_readout``: every
+admitted stream's read-out chain captured once, the streams read out chosen per launch),
+else through ``fibar_readout_batch`` (each chain launched from the host onto a pool of
+streams).  Either way the pipelines of different streams run side by side on the GPU.  A
+request's latency is the device time from its batch's start to its image being complete
+(group: the kernels' own timer stamps; batch: CUDA events).
 
 :class:`Admission` is the memory accounting alone (host logic, no device), so that its
 rules can be checked without a GPU.
@@ -16,7 +19,9 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
-from .binding import Fibar, FibarError, memory_bytes, readout_batch
+import numpy as np
+
+from .binding import Fibar, FibarError, Group, _push_arrays, memory_bytes, readout_batch
 
 # per handle, on top of the library's count: the driver's allocation granularity
 HANDLE_SLACK_BYTES = 8 << 20
@@ -64,9 +69,13 @@ class Admission:
 class Request:
     sid: int
     t_us: int
-    image: object = None      # CUDA (H, W) float32 tensor, valid once `done` has completed
-    done: object = None       # torch.cuda.Event recorded when the image is complete
-    start: object = None      # torch.cuda.Event recorded before the batch that served it
+    image: object = None      # CUDA (H, W) float32 tensor, valid once its batch has run
+    done: object = None       # batch path: torch.cuda.Event recorded when the image is complete
+    start: object = None      # batch path: torch.cuda.Event recorded before the batch
+    group: object = None      # group path: the Group whose launch served it
+    ticket: int = -1          # group path: that launch's ticket
+    k: int = -1               # group path: this request's entry in that launch
+    m: int = 0                # group path: entries in that launch
 
 
 @dataclass
@@ -88,9 +97,10 @@ class GridTuner:
     keeps the share with the most events per second.  The choices are recorded in
     ``table`` ((W, H) -> SMs, 0 = the whole device) and ``trials`` (the timings)."""
 
-    def __init__(self, candidates=None, rounds: int = 4, warm: int = 2, seed: int = 31):
+    def __init__(self, candidates=None, rounds: int = 4, warm: int = 2, seed: int = 31, use_graph: bool = True):
         import torch
         self.torch = torch
+        self.use_graph = use_graph
         self.sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         self.candidates = candidates or [0, self.sms // 2, self.sms // 4, self.sms // 8, self.sms // 16]
         self.rounds, self.warm, self.seed = rounds, warm, seed
@@ -108,6 +118,10 @@ class GridTuner:
         stream = torch.cuda.current_stream()
         trials = []
         pos = 0
+        group = Group(fibs) if self.use_graph else None
+        outs = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in fibs]
+        tcols = [ev[:, 1].cpu() for ev in evs]
+        members = list(range(n_streams))
         try:
             for sms in self.candidates:
                 for f in fibs:
@@ -119,7 +133,11 @@ class GridTuner:
                         t0.record(stream)
                     for f, ev in zip(fibs, evs):
                         f.push(ev[pos:pos + per])
-                    readout_batch(fibs, [int(ev[pos + per - 1, 1]) for ev in evs], stream=stream)
+                    ts = [int(tc[pos + per - 1]) for tc in tcols]
+                    if group is not None:
+                        group.readout(members, ts, outs, stream=stream)
+                    else:
+                        readout_batch(fibs, ts, outs, stream=stream)
                     pos += per
                 t1 = torch.cuda.Event(enable_timing=True)
                 t1.record(stream)
@@ -128,6 +146,8 @@ class GridTuner:
                 trials.append({"sms": sms, "ms": round(ms, 4),
                                "mev_s": round(n_streams * per * self.rounds / ms / 1e3, 2)})
         finally:
+            if group is not None:
+                group.close()
             for f in fibs:
                 f.close()
         best = max(trials, key=lambda t: t["mev_s"])["sms"]
@@ -142,9 +162,13 @@ class Server:
     ``budget``: device bytes for stream state (default: the free memory reported by
     ``torch.cuda.mem_get_info`` minus ``reserve``)."""
 
-    def __init__(self, budget: int | None = None, reserve: int = 4 << 30, stream=None):
+    def __init__(self, budget: int | None = None, reserve: int = 4 << 30, stream=None, use_graph: bool = True):
         import torch
         self.torch = torch
+        self.use_graph = use_graph
+        self.group = None        # Group over the admitted streams (rebuilt after admit/release)
+        self._members = {}       # sid -> index in the group
+        self._old_groups = []    # replaced groups, kept for their tickets until close()
         if budget is None:
             free, _ = torch.cuda.mem_get_info()
             budget = max(0, free - reserve)
@@ -166,6 +190,7 @@ class Server:
             self.admission.refused += 1
             return None
         self.streams[sid] = _Stream(fib, W, H)
+        self._drop_group()
         if (W, H) in self.grid_share:
             fib.set_grid_share(self.grid_share[(W, H)])
         return sid
@@ -179,13 +204,53 @@ class Server:
                 st.fib.set_grid_share(table[(st.W, st.H)])
 
     def release(self, sid: int) -> None:
+        self._drop_group(close_all=True)
         st = self.streams.pop(sid)
         st.fib.close()
         self.admission.release(sid)
 
+    def _drop_group(self, close_all: bool = False) -> None:
+        if self.group is not None:
+            self._old_groups.append(self.group)
+            self.group = None
+        if close_all:  # a member is about to go: its groups must go first
+            for g in self._old_groups:
+                g.close()
+            self._old_groups = []
+
+    def _ensure_group(self) -> Group:
+        if self.group is None:
+            sids = list(self.streams)
+            self.group = Group([self.streams[i].fib for i in sids])
+            self._members = {sid: k for k, sid in enumerate(sids)}
+        return self.group
+
     def push(self, sid: int, packet) -> None:
         """Queue a packet (CUDA (n, 2) int64 event records) for the stream."""
         self.streams[sid].fib.push(packet)
+
+    def push_ranges(self, items) -> None:
+        """Queue several device packets in one library call: items of (sid, events, lo,
+        hi), the rows lo:hi of a contiguous CUDA (n, 2) int64 tensor ``events`` (which must
+        stay alive until the stream's read-out has run; the handle keeps a reference)."""
+        n = len(items)
+        if n == 0:
+            return
+        hs = np.empty(n, np.uint64)
+        ptrs = np.empty(n, np.uint64)
+        ns = np.empty(n, np.uint64)
+        fibs = []
+        keep = []
+        for k, (sid, ev, lo, hi) in enumerate(items):
+            f = self.streams[sid].fib
+            if not (0 <= lo <= hi <= ev.shape[0]):
+                raise ValueError("packet range outside the events")
+            fibs.append(f)
+            keep.append(ev)
+            hs[k] = f.h.value
+            ptrs[k] = ev.data_ptr() + 16 * lo
+            ns[k] = hi - lo
+        _push_arrays(fibs, keep, hs, ptrs, ns, self.stream)
 
     def request(self, sid: int, t_us: int) -> Request:
         """Ask for the stream's image at t_us (not earlier than its previous request)."""
@@ -210,14 +275,22 @@ class Server:
             if not batch:
                 return served
             reqs = [st.queue.pop(0) for _, st in batch]
-            start = torch.cuda.Event(enable_timing=True)
-            start.record(self.stream)
             for r, (_, st) in zip(reqs, batch):
                 r.image = torch.empty((st.H, st.W), dtype=torch.float32, device="cuda")
-                r.done = torch.cuda.Event(enable_timing=True)
-                r.start = start
-            readout_batch([st.fib for _, st in batch], [r.t_us for r in reqs],
-                          [r.image for r in reqs], [r.done for r in reqs], stream=self.stream)
+            if self.use_graph:
+                g = self._ensure_group()
+                ticket = g.readout([self._members[sid] for sid, _ in batch], [r.t_us for r in reqs],
+                                   [r.image for r in reqs], stream=self.stream)
+                for k, r in enumerate(reqs):
+                    r.group, r.ticket, r.k, r.m = g, ticket, k, len(reqs)
+            else:
+                start = torch.cuda.Event(enable_timing=True)
+                start.record(self.stream)
+                for r in reqs:
+                    r.done = torch.cuda.Event(enable_timing=True)
+                    r.start = start
+                readout_batch([st.fib for _, st in batch], [r.t_us for r in reqs],
+                              [r.image for r in reqs], [r.done for r in reqs], stream=self.stream)
             self.batches += 1
             served.extend(reqs)
 
@@ -232,14 +305,23 @@ class Server:
         return out
 
     def close(self) -> None:
+        self._drop_group(close_all=True)
         for sid in list(self.streams):
             self.release(sid)
 
 
 def latencies_ms(requests) -> list[float]:
-    """Device time from each request's batch start to its image (synchronises)."""
+    """Device time from each request's batch start to its image (synchronises).  Call
+    before the server that served them is closed."""
     out = []
+    cache = {}
     for r in requests:
-        r.done.synchronize()
-        out.append(r.start.elapsed_time(r.done))
+        if r.group is not None:
+            key = (id(r.group), r.ticket)
+            if key not in cache:
+                cache[key] = r.group.latency_ms(r.ticket, r.m)
+            out.append(cache[key][r.k])
+        else:
+            r.done.synchronize()
+            out.append(r.start.elapsed_time(r.done))
     return out

@@ -24,16 +24,18 @@ def _streams(n, seconds, seed):
     return eventsim.mixed_streams(n, seconds, seed=seed, sensors=SENSORS, rate_lo=0.5e6, rate_hi=4e6)
 
 
-@pytest.mark.parametrize("mode,sms", [("s2", 0), ("s1", 0), ("nsf", 0), ("s2", 1), ("s1", 3), ("nsf", 19)])
-def test_served_images_match_oracle_per_stream(oracle_mod, mode, sms):
-    """sms: the SMs every stream's grids are sized for (0: the whole device)."""
+@pytest.mark.parametrize("mode,sms,graph", [("s2", 0, True), ("s1", 0, True), ("nsf", 0, True), ("s2", 1, True),
+                                            ("s1", 3, False), ("nsf", 19, True), ("s2", 0, False)])
+def test_served_images_match_oracle_per_stream(oracle_mod, mode, sms, graph):
+    """sms: the SMs every stream's grids are sized for (0: the whole device); graph: one
+    group-graph launch per batch (else fibar_readout_batch)."""
     from paper_2510_20071_gb300.serving import Server, latencies_ms
     params = dict(MODES[mode], c_on=0.2, c_off=0.2)
     streams = _streams(6, 0.008, seed=21)
     reqs = eventsim.request_times(6, 0.008, rate_hz=2500, seed=22)
     sched = eventsim.serving_schedule(streams, reqs, tick_us=400)
     dev = [s["events"].cuda() for s in streams]
-    srv = Server()
+    srv = Server(use_graph=graph)
     if sms:
         srv.set_grid_share({(W, H): sms for W, H in SENSORS})
     sids = [srv.admit(s["W"], s["H"], **params) for s in streams]
@@ -42,8 +44,11 @@ def test_served_images_match_oracle_per_stream(oracle_mod, mode, sms):
     served = [[] for _ in streams]
     try:
         for T, pushes, reads in sched:
+            if graph:  # the tick's packets in one library call
+                srv.push_ranges([(sids[i], dev[i], lo, hi) for i, lo, hi in pushes])
             for i, lo, hi in pushes:
-                srv.push(sids[i], dev[i][lo:hi])
+                if not graph:
+                    srv.push(sids[i], dev[i][lo:hi])
                 steps[i].append(("push", lo, hi))
             for i, t in reads:
                 served[i].append(srv.request(sids[i], t))
