@@ -261,6 +261,7 @@ def run_batch(args, rank, world, local):
     served = []
     for T, pushes, reads in timed:
         served += tick(T, pushes, reads)
+    srv.join()  # group read-outs run on the streams' own CUDA streams
     e1.record(stream)
     host_ms = (time.perf_counter() - h0) * 1e3
     torch.cuda.synchronize()
@@ -310,9 +311,10 @@ def run_batch(args, rank, world, local):
                                "what": "device time from a batch's start to the request's image"},
         "host_ms": round(host_ms, 3),
         "grid_share_autotune": tuning,
-        "serving_path": (f"group graph: one launch per batch ({gstats['graph_kernels']} kernel nodes, "
-                         f"programmatic edges {'on' if gstats['programmatic_edges'] else 'off'}, "
-                         f"{gstats['builds']} capture(s))" if gstats else "fibar_readout_batch: host launches on 16 streams"),
+        "serving_path": (f"group: each stream's read-out chain captured once as a CUDA graph, one graph launch "
+                         f"per read-out on the stream's own CUDA stream ({gstats['graph_kernels']} kernel nodes in "
+                         f"all, programmatic edges {'on' if gstats['programmatic_edges'] else 'off'}, "
+                         f"{gstats['builds']} captures)" if gstats else "fibar_readout_batch: host launches on 16 streams"),
         "batches": st1["batches"] - st0["batches"],
         "clocks": clocks,
         "gpu_launches": launches,

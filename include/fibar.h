@@ -373,52 +373,61 @@ const char *fibar_last_error(fibar_t *h);
  * side instead of each one's grids filling the GPU in turn.  Errors: EINVAL. */
 int fibar_set_grid_share(fibar_t *h, uint32_t sms);
 
-/* ---- groups: read-outs of a fixed set of handles as one CUDA graph launch ----------
+/* ---- groups: read-outs of a fixed set of handles, one graph launch per member -------
  * The paper reconstructs one stream and has no counterpart.  A read-out is a chain of
  * about a dozen dependent kernels; issued one launch at a time (fibar_readout_batch),
- * the chains of many small streams leave the device waiting on the host.  A group
- * captures every member's chain once into one CUDA graph, under one conditional node per
- * member, the members side by side; what changes between read-outs (the packets pushed,
- * the read-out time, the image pointer, the carry slot) is read by the kernels from a
- * per-member descriptor in device memory.  A read-out of any subset of the members is
- * then one host-to-device copy of the descriptors and one graph launch.
+ * the chains of many small streams leave the device waiting on the host, and each short
+ * chain is bound by its own latency.  A group captures every member's chain once into a
+ * CUDA graph, and gives every member its own internal CUDA stream: what changes between
+ * read-outs (the packets pushed, the read-out time, the image pointer, the carry slot) is
+ * written by the host into a ring of descriptors in mapped page-locked memory, which the
+ * graph's first kernel copies to the device.  A read-out of a member is then one graph
+ * launch on its stream, and the chains of different members - of one call and of
+ * consecutive calls - run side by side, each member's read-outs in order.
  * Results are those of fibar_readout on each member (same kernels, same order per
  * member).  A member's change of grid share, pixel gains or fill weights is picked up by
- * re-capturing the graph at the group's next read-out.  A group's calls are not
- * thread-safe; destroy the group before its members.  Per-stage timing
- * (fibar_set_timing) does not cover group read-outs. */
+ * re-capturing its graph at its next group read-out.  A group's calls are not
+ * thread-safe; work on a member's own handle (push, fibar_readout, flush) must not be
+ * queued while its group read-outs are in flight (join first); destroy the group before
+ * its members.  Per-stage timing (fibar_set_timing) does not cover group read-outs. */
 typedef struct fibar_group_s fibar_group_t;
 
 typedef struct {
     uint64_t members;         /* handles in the group */
-    uint64_t graph_launches;  /* fibar_group_readout calls that launched the graph */
-    uint64_t builds;          /* captures of the graph (1 + re-captures) */
-    uint64_t graph_kernels;   /* kernel nodes in the graph (all members) */
-    int32_t programmatic_edges;  /* 1: chains captured with programmatic (early-launch)
-                                    edges; 0: plain edges (the driver refused them) */
+    uint64_t graph_launches;  /* fibar_group_readout calls that launched work */
+    uint64_t builds;          /* member graph captures (one per member + re-captures) */
+    uint64_t graph_kernels;   /* kernel nodes in the members' graphs (all members) */
+    int32_t programmatic_edges;  /* 1: every chain captured with programmatic
+                                    (early-launch) edges; 0: some with plain edges */
 } fibar_group_stats_t;
 
 /* Create a group over hs[0..n) (n <= 1024, distinct handles of the current device) and
- * capture its graph.  *out receives the group.  Errors: EINVAL, ENOMEM, ECUDA. */
+ * capture each member's graph.  *out receives the group.  Errors: EINVAL, ENOMEM, ECUDA. */
 int fibar_group_create(fibar_t *const *hs, size_t n, fibar_group_t **out);
 
 /* Read out members[k] (indices into the group's hs, distinct) at t_us[k] into outs[k]
- * (device images of W*H floats, 16-byte aligned), k < m, with one graph launch on
- * cuda_stream; what fibar_readout(hs[members[k]], t_us[k], outs[k], 1, ...) does for
- * each.  The launch starts after the work already queued on cuda_stream (and after the
- * group's previous launch, on whatever stream), and later work on cuda_stream starts
- * after it.  ticket: NULL, or receives the launch's number for fibar_group_latency.
- * status: NULL, or m ints with each entry's check result.  Every entry is checked before
- * anything is queued: if one fails (EINVAL: index out of range or repeated, output NULL
- * or misaligned; EORDER: time earlier than the member's previous read-out), nothing is
+ * (device images of W*H floats, 16-byte aligned), k < m: what fibar_readout(hs[members[k]],
+ * t_us[k], outs[k], 1, ...) does for each, as one graph launch per member on the member's
+ * own stream.  The launches start after the work already queued on cuda_stream (the
+ * packets); work queued on cuda_stream later does NOT wait for them: call
+ * fibar_group_join (or fibar_group_latency, which waits) before using the images there.
+ * ticket: NULL, or receives the call's number for fibar_group_latency.  status: NULL, or
+ * m ints with each entry's check result.  Every entry is checked before anything is
+ * queued: if one fails (EINVAL: index out of range or repeated, output NULL or
+ * misaligned; EORDER: time earlier than the member's previous read-out), nothing is
  * queued and the first failing code is returned.  Errors also: ECUDA. */
 int fibar_group_readout(fibar_group_t *g, const uint32_t *members, const uint64_t *t_us, float *const *outs,
                         size_t m, int *status, uint64_t *ticket, void *cuda_stream);
 
-/* Device time in ms from the start of launch `ticket` to each of its images being
- * complete (its member's read-out committed), ms[k] for the k-th entry of that call;
- * m must equal that call's m.  Waits for the launch.  Tickets of the last 256 launches
- * are kept.  Errors: EINVAL (unknown or expired ticket, m mismatch), ECUDA. */
+/* Make work queued on cuda_stream from now on wait for every group read-out queued so
+ * far.  Errors: EINVAL, ECUDA. */
+int fibar_group_join(fibar_group_t *g, void *cuda_stream);
+
+/* Device time in ms from the start of call `ticket` (the first of its members' chains to
+ * start) to each of its images being complete (that member's read-out committed),
+ * ms[k] for the k-th entry of that call; m must equal that call's m.  Waits for the
+ * call's members.  Tickets of the last 4096 calls are kept.  Errors: EINVAL (unknown or
+ * expired ticket, m mismatch), ECUDA. */
 int fibar_group_latency(fibar_group_t *g, uint64_t ticket, float *ms, size_t m);
 
 /* Counters of the group.  Errors: EINVAL. */
@@ -427,7 +436,7 @@ int fibar_group_stats(fibar_group_t *g, fibar_group_stats_t *st);
 /* Message of the last failed group call ("" if none).  Owned by the group. */
 const char *fibar_group_last_error(fibar_group_t *g);
 
-/* Release the group (waits for its launches in flight); its members stay valid. */
+/* Release the group (waits for its work in flight); its members stay valid. */
 void fibar_group_destroy(fibar_group_t *g);
 
 /* Release the handle and its device memory (waits for its outstanding work). */

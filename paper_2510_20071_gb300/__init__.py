@@ -16,4 +16,5 @@ from .binding import (  # noqa: F401
     fibar_fill_features, fibar_fill_forward, fibar_fill_train_step, fibar_readout_host_async, fibar_wait,
     fibar_set_grid_share, fibar_push_batch, push_batch, Group, FibarGroupStats, fibar_group_create,
     fibar_group_readout, fibar_group_latency, fibar_group_stats, fibar_group_last_error, fibar_group_destroy,
+    fibar_group_join,
 )

@@ -29,7 +29,7 @@ EXPORTED = ["fibar_default_params", "fibar_create", "fibar_push_events", "fibar_
             "fibar_fill_set_weights", "fibar_fill_features", "fibar_fill_forward", "fibar_fill_train_step",
             "fibar_readout_host_async", "fibar_wait", "fibar_set_grid_share", "fibar_push_batch",
             "fibar_group_create", "fibar_group_readout", "fibar_group_latency", "fibar_group_stats",
-            "fibar_group_last_error", "fibar_group_destroy"]
+            "fibar_group_last_error", "fibar_group_destroy", "fibar_group_join"]
 
 FIBAR_FILL_NPARAMS = 2769
 
@@ -139,6 +139,8 @@ def load_library(build_if_missing: bool = True):
             lib.fibar_group_create.restype = C.c_int
             lib.fibar_group_readout.argtypes = [vp, vp, vp, vp, C.c_size_t, vp, vp, vp]
             lib.fibar_group_readout.restype = C.c_int
+            lib.fibar_group_join.argtypes = [vp, vp]
+            lib.fibar_group_join.restype = C.c_int
             lib.fibar_group_latency.argtypes = [vp, C.c_uint64, vp, C.c_size_t]
             lib.fibar_group_latency.restype = C.c_int
             lib.fibar_group_stats.argtypes = [vp, C.POINTER(FibarGroupStats)]
@@ -275,6 +277,10 @@ def fibar_group_readout(g, members_ptr: int, t_ptr: int, outs_ptr: int, m: int, 
                         stream: int) -> int:
     """Arrays by address: m uint32 member indices, uint64 times and image pointers."""
     return load_library().fibar_group_readout(g, members_ptr, t_ptr, outs_ptr, m, status_ptr, ticket_ptr, stream)
+
+
+def fibar_group_join(g, stream: int) -> int:
+    return load_library().fibar_group_join(g, stream)
 
 
 def fibar_group_latency(g, ticket: int, ms_ptr: int, m: int) -> int:
@@ -598,8 +604,10 @@ def _push_arrays(fibars, keep, hs, ptrs, ns, stream=None):
 
 
 class Group:
-    """A fixed set of :class:`Fibar` handles read out by one CUDA graph launch per call
-    (``fibar_group_*``).  Destroy (``close``) before the handles."""
+    """A fixed set of :class:`Fibar` handles, each member's read-out one launch of its
+    captured graph on the member's own stream (``fibar_group_*``).  Images are complete
+    once ``join`` has ordered a stream after them (or ``latency_ms`` has waited).  Destroy
+    (``close``) before the handles."""
 
     def __init__(self, fibars):
         if not fibars:
@@ -645,6 +653,13 @@ class Group:
         for i in members:
             self.fibars[i]._rotate()
         return int(ticket[0])
+
+    def join(self, stream=None) -> None:
+        """Make later work on ``stream`` (default: the current stream) wait for every read-out
+        queued so far."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self._check(fibar_group_join(self.g, s.cuda_stream))
 
     def latency_ms(self, ticket: int, m: int):
         """Device ms from the launch's start to each of its m images (waits)."""

@@ -1,22 +1,26 @@
-// fibar_group: read-outs of a fixed set of handles as one CUDA graph launch.
+// fibar_group: read-outs of a fixed set of handles, each member's read-out one launch of
+// a CUDA graph captured once.
 //
 // A handle's read-out is a chain of about a dozen dependent kernels (decode, sort, walk,
 // detector, blur, image, commit).  Issued from the host one launch at a time, the chains
-// of many small streams leave the GPU waiting on the host's launch calls.  A group
-// captures each member's chain once into one graph, with the parts that change between
-// read-outs - the packets to decode (its segment table), the image pointer and the carry
-// slot - read by the kernels from a per-member descriptor in device memory:
+// of many small streams leave the GPU waiting on the host's launch calls, and chains
+// that each take a short batch are bound by their own latency, not by the device.  A
+// group therefore
+//   - captures each member's chain once into a graph, with the parts that change between
+//     read-outs (the packets to decode, the read-out time, the image pointer, the carry
+//     slot) read by the kernels from the member's descriptor in device memory;
+//   - gives each member its own CUDA stream, so that the chains of different members -
+//     of the same call and of consecutive calls - run side by side, while one member's
+//     read-outs stay in order.
+// The descriptor of a member's c-th commit (read-out or flush) is written by the host
+// into slot c mod DESC_RING of a ring in mapped page-locked memory; the chain's first
+// kernel (k_desc_fetch) copies slot (commits so far) mod DESC_RING, which the device
+// knows from its own commit counter, into device memory.  A call costs the host one
+// graph launch and one stream wait per member, whatever the chain's length.
 //
-//   k_group_begin -> IF(active[0]) { chain of member 0 }
-//                 -> IF(active[1]) { chain of member 1 }
-//                 -> ...                                   (all side by side)
-//
-// One conditional node per member.  A read-out of any subset of the members is then one
-// host-to-device copy of the descriptors (from a ring of pinned host slots) and one graph
-// launch; k_group_begin sets each member's condition from the copied flags, and the
-// chains of the members read out run concurrently.  Each chain's commit kernel stamps
-// the GPU's global timer into mapped host memory, which gives every image's latency
-// from the launch's start without an event per member.
+// Latency: k_desc_fetch and the commit kernel stamp the GPU's global timer into mapped
+// memory; an image's latency is its commit stamp minus the earliest fetch stamp of its
+// call.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -29,53 +33,56 @@ using namespace fibar;
 
 namespace {
 
-constexpr unsigned GROUP_RING = 8;       // pinned descriptor slots (copies in flight)
-constexpr unsigned GROUP_TICKETS = 256;  // launches whose latency stamps are kept
+constexpr unsigned DESC_RING = 16;        // descriptor slots per member
+constexpr unsigned GROUP_TICKETS = 4096;  // calls whose latency stamps are kept
 constexpr size_t GROUP_MAX = 1024;
 
-struct GroupHead {
-    unsigned long long *start_stamp;  // %globaltimer at the launch's start
-    unsigned n;
-    unsigned pad;
-};
-
-__global__ void k_group_begin(const GroupHead *head, const unsigned *active,
-                              const cudaGraphConditionalHandle *cond, unsigned n)
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    if (threadIdx.x == 0) {
-        unsigned long long ns;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(ns));
-        *(volatile unsigned long long *)head->start_stamp = ns;
-    }
-    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) cudaGraphSetConditional(cond[i], active[i] ? 1u : 0u);
+    unsigned long long ns;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(ns));
+    return ns;
 }
 
-size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+// Copy the descriptor of this read-out (the slot of the handle's commit number) from the
+// mapped host ring into device memory, and stamp the chain's start.
+__global__ void __launch_bounds__(256) k_desc_fetch(const Ctrl *ctrl, const ReadDesc *ring, ReadDesc *dst)
+{
+    const unsigned slot = (ctrl->batch_no - 1u) % DESC_RING;
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(ring + slot);
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(dst);
+    constexpr unsigned WORDS = sizeof(ReadDesc) / 8;
+    for (unsigned i = threadIdx.x; i < WORDS; i += blockDim.x) d[i] = src[i];
+    if (threadIdx.x == 0) {
+        unsigned long long *b = ring[slot].stamp_begin;
+        if (b) *(volatile unsigned long long *)b = global_ns();
+    }
+}
+static_assert(sizeof(ReadDesc) % 8 == 0, "descriptor copied in 8-byte words");
+
+struct Member {
+    fibar_t *h = nullptr;
+    cudaStream_t s = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long version = 0;
+    unsigned long long chain_launches = 0;  // kernels per read-out (k_desc_fetch included)
+    bool pdl = false;                       // captured with programmatic edges
+    bool used_since_join = false;
+};
 
 }  // namespace
 
 struct fibar_group_s {
-    std::vector<fibar_t *> hs;
-    std::vector<unsigned long long> versions;        // members' config_version at capture
-    std::vector<unsigned long long> chain_launches;  // kernels in each member's chain
+    std::vector<Member> mem;
     int device = -1;
-    size_t off_active = 0, off_desc = 0, blk_bytes = 0;
-    unsigned char *d_blk = nullptr;   // descriptors on the device
-    unsigned char *h_ring = nullptr;  // GROUP_RING pinned slots of blk_bytes
-    cudaEvent_t ev_slot[GROUP_RING] = {};
-    unsigned long long slot_uses = 0;
-    cudaGraphConditionalHandle *d_cond = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaStream_t cap = nullptr;
-    bool pdl = false;                   // chains captured with programmatic edges
-    unsigned long long *h_stamps = nullptr, *d_stamps = nullptr;  // GROUP_TICKETS x (1 + n)
-    cudaEvent_t ev_ticket[GROUP_TICKETS] = {};
+    ReadDesc *d_desc = nullptr;                      // one device descriptor per member
+    ReadDesc *h_ring = nullptr, *hd_ring = nullptr;  // n x DESC_RING, host / device view
+    unsigned long long *h_stamps = nullptr, *d_stamps = nullptr;  // GROUP_TICKETS x n x 2
     std::vector<std::vector<uint32_t>> ticket_members;
     unsigned long long next_ticket = 0;
-    cudaStream_t last_stream = nullptr;
-    bool have_last = false;
-    unsigned long long launches = 0, rebuilds = 0, kernels = 0;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
+    unsigned long long launches = 0, builds = 0;
     std::string err;
 };
 
@@ -94,86 +101,60 @@ int gcuda(fibar_group_t *g, cudaError_t e, const char *where)
     return FIBAR_ECUDA;
 }
 
-void drop_graph(fibar_group_t *g)
+// Capture member i's chain (k_desc_fetch, then the read-out's kernels) into a graph.
+int capture_member(fibar_group_t *g, size_t i, bool pdl, cudaGraphExec_t *exec_out, unsigned long long *nk_out)
 {
-    if (g->exec) cudaGraphExecDestroy(g->exec);
-    if (g->graph) cudaGraphDestroy(g->graph);
-    g->exec = nullptr;
-    g->graph = nullptr;
-}
-
-// Capture every member's chain under one conditional node each and instantiate.
-int build_graph(fibar_group_t *g, bool pdl)
-{
-    drop_graph(g);
-    const size_t n = g->hs.size();
-    cudaError_t e = cudaGraphCreate(&g->graph, 0);
-    if (e != cudaSuccess) return gcuda(g, e, "group: graph");
-    std::vector<cudaGraphConditionalHandle> cond(n);
-    for (size_t i = 0; i < n && e == cudaSuccess; ++i)
-        e = cudaGraphConditionalHandleCreate(&cond[i], g->graph, 0, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(g->d_cond, cond.data(), n * sizeof(cudaGraphConditionalHandle), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return gcuda(g, e, "group: conditional handles");
-
-    const GroupHead *head = reinterpret_cast<const GroupHead *>(g->d_blk);
-    const unsigned *active = reinterpret_cast<const unsigned *>(g->d_blk + g->off_active);
-    const cudaGraphConditionalHandle *dc = g->d_cond;
-    unsigned nn = (unsigned)n;
-    void *args[] = {(void *)&head, (void *)&active, (void *)&dc, (void *)&nn};
-    cudaKernelNodeParams kn = {};
-    kn.func = (void *)k_group_begin;
-    kn.gridDim = dim3(1);
-    kn.blockDim = dim3(256);
-    kn.kernelParams = args;
-    cudaGraphNode_t root = nullptr;
-    e = cudaGraphAddKernelNode(&root, g->graph, nullptr, 0, &kn);
-    if (e != cudaSuccess) return gcuda(g, e, "group: root node");
-
-    ReadDesc *desc = reinterpret_cast<ReadDesc *>(g->d_blk + g->off_desc);
+    Member &mb = g->mem[i];
+    fibar_t *h = mb.h;
+    cudaStream_t cap = mb.s;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return gcuda(g, e, "group: begin capture");
+    const unsigned long long l0 = h->launches;
+    k_desc_fetch<<<1, 256, 0, cap>>>(h->b.ctrl, g->hd_ring + i * DESC_RING, g->d_desc + i);
+    e = cudaGetLastError();
     SegTable dummy;
     memset(&dummy, 0, sizeof(dummy));
-    g->kernels = 1;
-    for (size_t i = 0; i < n; ++i) {
-        fibar_t *h = g->hs[i];
-        cudaGraphNodeParams np = {};
-        np.type = cudaGraphNodeTypeConditional;
-        np.conditional.handle = cond[i];
-        np.conditional.type = cudaGraphCondTypeIf;
-        np.conditional.size = 1;
-        cudaGraphNode_t node = nullptr;
-        e = cudaGraphAddNode(&node, g->graph, &root, nullptr, 1, &np);
-        if (e != cudaSuccess) return gcuda(g, e, "group: conditional node");
-        cudaGraph_t body = np.conditional.phGraph_out[0];
-        e = cudaStreamBeginCaptureToGraph(g->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-        if (e != cudaSuccess) return gcuda(g, e, "group: begin capture");
-        const unsigned long long l0 = h->launches;
-        pdl_enabled = pdl;
-        const int rc = enqueue_readout_chain(h, dummy, nullptr, desc + i, g->cap, false);
-        pdl_enabled = true;
-        g->chain_launches[i] = h->launches - l0;
-        h->launches = l0;
-        cudaGraph_t got = nullptr;
-        const cudaError_t ee = cudaStreamEndCapture(g->cap, &got);
+    pdl_enabled = pdl;
+    const int rc = e == cudaSuccess ? enqueue_readout_chain(h, dummy, nullptr, g->d_desc + i, cap, false) : FIBAR_OK;
+    pdl_enabled = true;
+    *nk_out = h->launches - l0 + 1;
+    h->launches = l0;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cap, &graph);
+    if (e != cudaSuccess || rc != FIBAR_OK || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return gcuda(g, e, "group: descriptor fetch");
         if (rc != FIBAR_OK) return gfail(g, rc, "group: capturing member " + std::to_string(i) + ": " + h->err);
-        if (ee != cudaSuccess) return gcuda(g, ee, "group: end capture");
-        g->kernels += g->chain_launches[i];
-        g->versions[i] = h->config_version;
+        return gcuda(g, ee, "group: end capture");
     }
-    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    e = cudaGraphInstantiate(exec_out, graph, 0);
+    cudaGraphDestroy(graph);
     if (e != cudaSuccess) return gcuda(g, e, "group: instantiate");
-    g->pdl = pdl;
     return FIBAR_OK;
 }
 
-// Programmatic edges first; a driver that refuses them inside conditional bodies gets
-// plain edges.
-int build(fibar_group_t *g)
+// (Re)build member i's graph.  Launches of the previous graph still queued on the
+// member's stream keep it alive until they complete.  Programmatic edges first, plain
+// edges if the driver refuses them.
+int build_member(fibar_group_t *g, size_t i)
 {
-    int rc = build_graph(g, true);
-    if (rc != FIBAR_OK) rc = build_graph(g, false);
-    if (rc == FIBAR_OK) g->rebuilds += 1;
-    return rc;
+    Member &mb = g->mem[i];
+    cudaGraphExec_t ex = nullptr;
+    unsigned long long nk = 0;
+    bool pdl = true;
+    int rc = capture_member(g, i, true, &ex, &nk);
+    if (rc != FIBAR_OK) {
+        pdl = false;
+        rc = capture_member(g, i, false, &ex, &nk);
+    }
+    if (rc != FIBAR_OK) return rc;
+    if (mb.exec) cudaGraphExecDestroy(mb.exec);
+    mb.exec = ex;
+    mb.chain_launches = nk;
+    mb.pdl = pdl;
+    mb.version = mb.h->config_version;
+    g->builds += 1;
+    return FIBAR_OK;
 }
 
 }  // namespace
@@ -182,15 +163,15 @@ extern "C" void fibar_group_destroy(fibar_group_t *g)
 {
     if (!g) return;
     if (g->device >= 0) cudaSetDevice(g->device);
-    // a launch still in flight keeps its graph alive until it completes
-    drop_graph(g);
-    for (cudaEvent_t &ev : g->ev_slot)
-        if (ev) cudaEventSynchronize(ev), cudaEventDestroy(ev);
-    for (cudaEvent_t &ev : g->ev_ticket)
-        if (ev) cudaEventSynchronize(ev), cudaEventDestroy(ev);
-    if (g->cap) cudaStreamDestroy(g->cap);
-    if (g->d_blk) cudaFree(g->d_blk);
-    if (g->d_cond) cudaFree(g->d_cond);
+    for (Member &mb : g->mem) {
+        if (mb.s) cudaStreamSynchronize(mb.s);
+        if (mb.exec) cudaGraphExecDestroy(mb.exec);
+        if (mb.s) cudaStreamDestroy(mb.s);
+    }
+    for (cudaEvent_t ev : g->ev_join)
+        if (ev) cudaEventDestroy(ev);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->d_desc) cudaFree(g->d_desc);
     if (g->h_ring) cudaFreeHost(g->h_ring);
     if (g->h_stamps) cudaFreeHost(g->h_stamps);
     delete g;
@@ -211,38 +192,36 @@ extern "C" int fibar_group_create(fibar_t *const *hs, size_t n, fibar_group_t **
 
     fibar_group_t *g = new (std::nothrow) fibar_group_s();
     if (!g) return FIBAR_ENOMEM;
-    g->hs.assign(hs, hs + n);
-    g->versions.assign(n, 0);
-    g->chain_launches.assign(n, 0);
+    g->mem.resize(n);
+    g->ev_join.assign(n, nullptr);
     g->ticket_members.resize(GROUP_TICKETS);
     g->device = dev;
-    g->off_active = align16(sizeof(GroupHead));
-    g->off_desc = g->off_active + align16(n * sizeof(unsigned));
-    g->blk_bytes = g->off_desc + n * sizeof(ReadDesc);
-    cudaError_t e = cudaMalloc((void **)&g->d_blk, g->blk_bytes);
-    if (e == cudaSuccess) e = cudaMemset(g->d_blk, 0, g->blk_bytes);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&g->d_cond, n * sizeof(cudaGraphConditionalHandle));
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&g->h_ring, GROUP_RING * g->blk_bytes, cudaHostAllocDefault);
-    if (e == cudaSuccess)
-        e = cudaHostAlloc((void **)&g->h_stamps, GROUP_TICKETS * (n + 1) * sizeof(unsigned long long),
-                          cudaHostAllocMapped);
+    const size_t ring_bytes = n * DESC_RING * sizeof(ReadDesc);
+    const size_t stamp_bytes = (size_t)GROUP_TICKETS * n * 2 * sizeof(unsigned long long);
+    cudaError_t e = cudaMalloc((void **)&g->d_desc, n * sizeof(ReadDesc));
+    if (e == cudaSuccess) e = cudaMemset(g->d_desc, 0, n * sizeof(ReadDesc));
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&g->h_ring, ring_bytes, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&g->hd_ring, g->h_ring, 0);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&g->h_stamps, stamp_bytes, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&g->d_stamps, g->h_stamps, 0);
-    for (unsigned i = 0; i < GROUP_RING && e == cudaSuccess; ++i)
-        e = cudaEventCreateWithFlags(&g->ev_slot[i], cudaEventDisableTiming);
-    for (unsigned i = 0; i < GROUP_TICKETS && e == cudaSuccess; ++i)
-        e = cudaEventCreateWithFlags(&g->ev_ticket[i], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming);
+    for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+        g->mem[i].h = hs[i];
+        e = cudaStreamCreateWithFlags(&g->mem[i].s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_join[i], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         fibar_group_destroy(g);
         return e == cudaErrorMemoryAllocation ? FIBAR_ENOMEM : FIBAR_ECUDA;
     }
-    memset(g->h_ring, 0, GROUP_RING * g->blk_bytes);
-    memset(g->h_stamps, 0, GROUP_TICKETS * (n + 1) * sizeof(unsigned long long));
-    if (build(g) != FIBAR_OK) {
-        fibar_group_destroy(g);
-        return FIBAR_ECUDA;
-    }
+    memset(g->h_ring, 0, ring_bytes);
+    memset(g->h_stamps, 0, stamp_bytes);
+    for (size_t i = 0; i < n; ++i)
+        if (build_member(g, i) != FIBAR_OK) {
+            fibar_group_destroy(g);
+            return FIBAR_ECUDA;
+        }
     *out = g;
     return FIBAR_OK;
 }
@@ -252,7 +231,7 @@ extern "C" int fibar_group_readout(fibar_group_t *g, const uint32_t *members, co
 {
     if (!g) return FIBAR_EINVAL;
     if (m == 0) return FIBAR_OK;
-    const size_t n = g->hs.size();
+    const size_t n = g->mem.size();
     if (!members || !t_us || !outs || m > n) return gfail(g, FIBAR_EINVAL, "group_readout: bad arguments");
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != g->device)
@@ -267,7 +246,7 @@ extern "C" int fibar_group_readout(fibar_group_t *g, const uint32_t *members, co
             rc = FIBAR_EINVAL;
         } else {
             seen[i] = 1;
-            fibar_t *h = g->hs[i];
+            fibar_t *h = g->mem[i].h;
             if (!outs[k] || ((uintptr_t)outs[k] & 15) != 0)
                 rc = FIBAR_EINVAL, h->err = "group_readout: output null or not 16-byte aligned";
             else if (h->have_readout && t_us[k] < h->last_readout)
@@ -277,77 +256,78 @@ extern "C" int fibar_group_readout(fibar_group_t *g, const uint32_t *members, co
         if (rc != FIBAR_OK && first == FIBAR_OK) first = rc;
     }
     if (first != FIBAR_OK) return gfail(g, first, "group_readout: an entry failed its checks (see status)");
-
-    for (size_t i = 0; i < n; ++i)
-        if (g->hs[i]->config_version != g->versions[i]) {
-            const int rc = build(g);
-            if (rc != FIBAR_OK) return rc;
-            break;
-        }
-
-    cudaStream_t s = (cudaStream_t)cuda_stream;
-    cudaError_t e = cudaSuccess;
-    // the previous launch read the device descriptors: order after it
-    const unsigned long long tk = g->next_ticket;
-    if (g->have_last && g->last_stream != s)
-        e = cudaStreamWaitEvent(s, g->ev_ticket[(tk + GROUP_TICKETS - 1) % GROUP_TICKETS], 0);
-    if (e != cudaSuccess) return gcuda(g, e, "group_readout: order after the previous launch");
-
-    const unsigned j = (unsigned)(g->slot_uses % GROUP_RING);
-    e = cudaEventSynchronize(g->ev_slot[j]);  // the copy out of this slot has run
-    if (e != cudaSuccess) return gcuda(g, e, "group_readout: descriptor slot");
-    unsigned char *blk = g->h_ring + (size_t)j * g->blk_bytes;
-    const unsigned ts = (unsigned)(tk % GROUP_TICKETS);
-    unsigned long long *stamps = g->d_stamps + (size_t)ts * (n + 1);
-    GroupHead *head = reinterpret_cast<GroupHead *>(blk);
-    head->start_stamp = stamps;
-    head->n = (unsigned)n;
-    unsigned *active = reinterpret_cast<unsigned *>(blk + g->off_active);
-    memset(active, 0, n * sizeof(unsigned));
-    ReadDesc *desc = reinterpret_cast<ReadDesc *>(blk + g->off_desc);
-    size_t top = 0;
     for (size_t k = 0; k < m; ++k) {
         const uint32_t i = members[k];
-        fibar_t *h = g->hs[i];
-        active[i] = 1;
-        fill_segtable(h, t_us[k], desc[i].t);
-        desc[i].out = outs[k];
-        desc[i].stamp = stamps + 1 + i;
-        top = std::max(top, (size_t)i + 1);
-        if (h->copy_pending) {
-            // host packets of this member: the copy stream's work comes first
-            e = cudaEventRecord(h->ev_copied, h->copy_stream);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_copied, 0);
-            if (e != cudaSuccess) return gcuda(g, e, "group_readout: wait for host packets");
+        if (g->mem[i].h->config_version != g->mem[i].version) {
+            const int rc = build_member(g, i);
+            if (rc != FIBAR_OK) return rc;
         }
     }
-    e = cudaMemcpyAsync(g->d_blk, blk, g->off_desc + top * sizeof(ReadDesc), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaEventRecord(g->ev_slot[j], s);
-    g->slot_uses += 1;
-    if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, s);
-    if (e == cudaSuccess) e = cudaEventRecord(g->ev_ticket[ts], s);
-    if (e != cudaSuccess) return gcuda(g, e, "group_readout: launch");
-    g->next_ticket = tk + 1;
-    g->have_last = true;
-    g->last_stream = s;
-    g->launches += 1;
-    g->ticket_members[ts].assign(members, members + m);
+
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // the members' work starts after what the caller queued so far (its packets)
+    cudaError_t e = cudaEventRecord(g->ev_fork, s);
+    if (e != cudaSuccess) return gcuda(g, e, "group_readout: fork event");
+    const unsigned long long tk = g->next_ticket;
+    const unsigned ts = (unsigned)(tk % GROUP_TICKETS);
+    unsigned long long *stamps = g->d_stamps + (size_t)ts * n * 2;
     for (size_t k = 0; k < m; ++k) {
-        fibar_t *h = g->hs[members[k]];
-        if (h->copy_pending) {
-            // the staging buffer is free once this launch has run
-            e = cudaEventRecord(h->ev_free[h->staging_cur], s);
-            if (e != cudaSuccess) return gcuda(g, e, "group_readout: staging event");
+        const uint32_t i = members[k];
+        Member &mb = g->mem[i];
+        fibar_t *h = mb.h;
+        // this commit's descriptor slot was last read by commit c - DESC_RING
+        const unsigned long long c = h->commits;
+        if (c >= DESC_RING &&
+            (unsigned long long)__atomic_load_n(&h->snap_host[1], __ATOMIC_ACQUIRE) + DESC_RING < c + 1) {
+            e = cudaStreamSynchronize(mb.s);
+            if (e != cudaSuccess) return gcuda(g, e, "group_readout: descriptor ring");
+        }
+        ReadDesc &d = g->h_ring[i * DESC_RING + c % DESC_RING];
+        fill_segtable(h, t_us[k], d.t);
+        d.out = outs[k];
+        d.stamp_begin = stamps + 2 * i;
+        d.stamp = stamps + 2 * i + 1;
+        e = cudaStreamWaitEvent(mb.s, g->ev_fork, 0);
+        const bool host_packets = h->copy_pending;
+        if (e == cudaSuccess && host_packets) {
+            // host packets of this member: the copy stream's work comes first
+            e = cudaEventRecord(h->ev_copied, h->copy_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(mb.s, h->ev_copied, 0);
+        }
+        if (e == cudaSuccess) e = cudaGraphLaunch(mb.exec, mb.s);
+        if (e == cudaSuccess && host_packets) {
+            // the staging buffer is free once this read-out has run
+            e = cudaEventRecord(h->ev_free[h->staging_cur], mb.s);
             h->staging_cur ^= 1;
             h->copy_pending = false;
         }
+        if (e != cudaSuccess) return gcuda(g, e, "group_readout: launch");
+        mb.used_since_join = true;
         readout_committed(h);
         h->have_readout = true;
         h->last_readout = t_us[k];
         h->readouts += 1;
-        h->launches += g->chain_launches[members[k]];
+        h->launches += mb.chain_launches;
     }
+    g->next_ticket = tk + 1;
+    g->launches += 1;
+    g->ticket_members[ts].assign(members, members + m);
     if (ticket) *ticket = tk;
+    return FIBAR_OK;
+}
+
+extern "C" int fibar_group_join(fibar_group_t *g, void *cuda_stream)
+{
+    if (!g) return FIBAR_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    for (size_t i = 0; i < g->mem.size(); ++i) {
+        Member &mb = g->mem[i];
+        if (!mb.used_since_join) continue;
+        cudaError_t e = cudaEventRecord(g->ev_join[i], mb.s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, g->ev_join[i], 0);
+        if (e != cudaSuccess) return gcuda(g, e, "group_join");
+        mb.used_since_join = false;
+    }
     return FIBAR_OK;
 }
 
@@ -359,13 +339,16 @@ extern "C" int fibar_group_latency(fibar_group_t *g, uint64_t ticket, float *ms,
     const unsigned ts = (unsigned)(ticket % GROUP_TICKETS);
     const std::vector<uint32_t> &mem = g->ticket_members[ts];
     if (!ms || m != mem.size()) return gfail(g, FIBAR_EINVAL, "group_latency: one value per member read out");
-    const cudaError_t e = cudaEventSynchronize(g->ev_ticket[ts]);
-    if (e != cudaSuccess) return gcuda(g, e, "group_latency: sync");
-    const size_t n = g->hs.size();
-    const volatile unsigned long long *st = g->h_stamps + (size_t)ts * (n + 1);
-    const unsigned long long t0 = st[0];
+    for (uint32_t i : mem) {
+        const cudaError_t e = cudaStreamSynchronize(g->mem[i].s);
+        if (e != cudaSuccess) return gcuda(g, e, "group_latency: sync");
+    }
+    const size_t n = g->mem.size();
+    const volatile unsigned long long *st = g->h_stamps + (size_t)ts * n * 2;
+    unsigned long long t0 = ~0ull;
+    for (uint32_t i : mem) t0 = std::min(t0, (unsigned long long)st[2 * i]);
     for (size_t k = 0; k < m; ++k) {
-        const unsigned long long t1 = st[1 + mem[k]];
+        const unsigned long long t1 = st[2 * mem[k] + 1];
         ms[k] = t1 >= t0 ? (float)((double)(t1 - t0) * 1e-6) : 0.f;
     }
     return FIBAR_OK;
@@ -374,11 +357,17 @@ extern "C" int fibar_group_latency(fibar_group_t *g, uint64_t ticket, float *ms,
 extern "C" int fibar_group_stats(fibar_group_t *g, fibar_group_stats_t *st)
 {
     if (!g || !st) return FIBAR_EINVAL;
-    st->members = g->hs.size();
+    st->members = g->mem.size();
     st->graph_launches = g->launches;
-    st->builds = g->rebuilds;
-    st->graph_kernels = g->kernels;
-    st->programmatic_edges = g->pdl ? 1 : 0;
+    st->builds = g->builds;
+    unsigned long long k = 0;
+    int pdl = 1;
+    for (const Member &mb : g->mem) {
+        k += mb.chain_launches;
+        pdl &= mb.pdl ? 1 : 0;
+    }
+    st->graph_kernels = k;
+    st->programmatic_edges = pdl;
     return FIBAR_OK;
 }
 

@@ -136,8 +136,9 @@ struct SegTable {
 // read-out to the next, in device memory, written before the chain runs.
 struct ReadDesc {
     SegTable t;
-    float *out;                  // the image (16-byte aligned)
-    unsigned long long *stamp;   // if set: %globaltimer (ns) once the read-out has committed
+    float *out;                        // the image (16-byte aligned)
+    unsigned long long *stamp_begin;   // if set: %globaltimer (ns) when the chain starts
+    unsigned long long *stamp;         // if set: %globaltimer (ns) once the read-out has committed
 };
 
 struct Bufs {

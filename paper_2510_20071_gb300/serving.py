@@ -139,6 +139,8 @@ class GridTuner:
                     else:
                         readout_batch(fibs, ts, outs, stream=stream)
                     pos += per
+                if group is not None:
+                    group.join(stream)
                 t1 = torch.cuda.Event(enable_timing=True)
                 t1.record(stream)
                 t1.synchronize()
@@ -210,6 +212,7 @@ class Server:
         self.admission.release(sid)
 
     def _drop_group(self, close_all: bool = False) -> None:
+        self.join()
         if self.group is not None:
             self._old_groups.append(self.group)
             self.group = None
@@ -294,7 +297,16 @@ class Server:
             self.batches += 1
             served.extend(reqs)
 
+    def join(self) -> None:
+        """Make later work on the server's stream wait for every read-out served so far
+        (group read-outs run on the members' own streams)."""
+        if self.group is not None:
+            self.group.join(self.stream)
+        for g in self._old_groups:
+            g.join(self.stream)
+
     def stats(self) -> dict:
+        self.join()
         out = {"streams": len(self.streams), "bytes_held": self.admission.used,
                "budget": self.admission.budget, "refused": self.admission.refused,
                "batches": self.batches, "kernel_launches": 0, "events_applied": 0}
