@@ -214,23 +214,21 @@ def run_batch(args, rank, world, local):
         srv.set_grid_share({(s["W"], s["H"]): args.grid_share for s in streams})
         tuning = {"fixed_sms": args.grid_share}
     elif not args.no_autotune:
-        # per sensor shape: the SM share with the most events/s when as many streams of
-        # that shape as a batch holds on average are read out together, each at its
-        # shape's mean events per read-out (100 Hz requests)
+        # per sensor shape: the SM share with the most events/s when that shape's streams
+        # are read out together, round after round without waiting (their read-outs
+        # overlap as in serving), each at its shape's mean events per read-out (100 Hz)
         from paper_2510_20071_gb300.serving import GridTuner
         tuner = GridTuner(use_graph=use_graph)
         shapes = {}
         for s in streams:
             shapes.setdefault((s["W"], s["H"]), []).append(s["events"].shape[0] / seconds)
-        sizes = [len(reads) for _, _, reads in sched if reads]
-        per_batch = max(1, round(sum(sizes) / max(len(sizes), 1)))
         t_tune = time.time()
         for (w_, h_), rates in shapes.items():
-            tuner.tune(w_, h_, per_batch, int(sum(rates) / len(rates) / 100.0), **params)
+            tuner.tune(w_, h_, len(rates), int(sum(rates) / len(rates) / 100.0), **params)
         srv.set_grid_share(tuner.table)
         tuning = {"sms": {f"{w_}x{h_}": v for (w_, h_), v in tuner.table.items()},
                   "trials": {f"{w_}x{h_}": v for (w_, h_), v in tuner.trials.items()},
-                  "streams_per_trial": per_batch, "seconds": round(time.time() - t_tune, 2)}
+                  "seconds": round(time.time() - t_tune, 2)}
         log(f"[rank {rank}] grid shares {tuning['sms']} ({tuning['seconds']} s)")
 
     def tick(T, pushes, reads):
@@ -672,7 +670,8 @@ def main():
                     help="batch32: SMs every stream's grids are sized for (default: autotuned per shape)")
     ap.add_argument("--no-autotune", action="store_true", help="batch32: whole-device grids for every stream")
     ap.add_argument("--batch-path", default="graph", choices=["graph", "streams"],
-                    help="batch32: one group-graph launch per batch, or host launches per stream")
+                    help="batch32: group read-outs (one captured graph per stream, launched on the "
+                         "stream's own CUDA stream), or fibar_readout_batch's host launches")
     ap.add_argument("--calib-events", type=int, default=100_000_000,
                     help="calib: records in the recording (profiling runs use fewer)")
     args = ap.parse_args()
@@ -683,9 +682,9 @@ def main():
         return run_reference(args, rank, world)
 
     if args.workload == "batch32":
-        # hardware work queues for the library's 16 internal streams (read by CUDA when the
-        # context is created; the default of 8 would make pairs of streams share one)
-        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "16")
+        # hardware work queues for the streams' own CUDA streams (read by CUDA when the
+        # context is created; the default of 8 would make groups of streams share one)
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
     import torch.distributed as dist
     torch.cuda.set_device(local)

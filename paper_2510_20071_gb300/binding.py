@@ -6,6 +6,7 @@ only) and raises :class:`FibarError` on any non-zero status.
 """
 from __future__ import annotations
 
+import array
 import ctypes as C
 import os
 import threading
@@ -591,15 +592,25 @@ def push_batch(fibars, packets, stream=None) -> None:
 
 
 def _push_arrays(fibars, keep, hs, ptrs, ns, stream=None):
+    _push_lists(fibars, keep, hs.tolist(), ptrs.tolist(), ns.tolist(), stream)
+
+
+def _push_lists(fibars, keep, hs, ptrs, ns, stream=None):
+    """fibar_push_batch of device packets given as lists of handle integers, packet
+    addresses and sizes; keeps each packet's tensor (``keep``) with its handle."""
     import torch
     n = len(hs)
-    status = np.zeros(n, np.int32)
+    a_h, a_p, a_n = array.array("Q", hs), array.array("Q", ptrs), array.array("Q", ns)
+    status = array.array("i", bytes(4 * n))
     s = stream if stream is not None else torch.cuda.current_stream()
-    rc = fibar_push_batch(hs.ctypes.data, ptrs.ctypes.data, ns.ctypes.data, n, 1, status.ctypes.data, s.cuda_stream)
+    rc = fibar_push_batch(a_h.buffer_info()[0], a_p.buffer_info()[0], a_n.buffer_info()[0], n, 1,
+                          status.buffer_info()[0], s.cuda_stream)
     for f, ev in zip(fibars, keep):
-        f._keep.append(ev)
+        k = f._keep
+        if not k or k[-1] is not ev:
+            k.append(ev)
     if rc != 0:
-        k = int(np.flatnonzero(status)[0]) if status.any() else 0
+        k = next((i for i in range(n) if status[i] != 0), 0)
         raise FibarError(rc, f"entry {k}: {fibar_last_error(fibars[k].h)}")
 
 
@@ -625,34 +636,41 @@ class Group:
 
     def readout(self, members, t_us, outs, stream=None) -> int:
         """Read out members (indices into the group) at t_us into outs (16-byte aligned
-        contiguous CUDA float32 tensors of each member's W*H); returns the launch's ticket."""
+        contiguous CUDA float32 tensors of each member's W*H); returns the call's ticket."""
         import torch
         m = len(members)
         if len(t_us) != m or len(outs) != m:
             raise ValueError("one time and one output per member")
-        mem = np.asarray(members, dtype=np.uint32)
-        ts = np.asarray(t_us, dtype=np.uint64)
-        op = np.empty(m, np.uint64)
-        for k, (i, o) in enumerate(zip(members, outs)):
+        for i, o in zip(members, outs):
             f = self.fibars[i]
             if o.dtype != torch.float32 or not o.is_cuda or o.numel() != f.W * f.H or not o.is_contiguous():
                 raise TypeError("outs must be contiguous CUDA float32 tensors of W*H elements")
-            op[k] = o.data_ptr()
-        status = np.zeros(m, np.int32)
-        ticket = np.zeros(1, np.uint64)
         s = stream if stream is not None else torch.cuda.current_stream()
-        rc = fibar_group_readout(self.g, mem.ctypes.data, ts.ctypes.data, op.ctypes.data, m, status.ctypes.data,
-                                 ticket.ctypes.data, s.cuda_stream)
+        return self.readout_ptrs(members, t_us, [o.data_ptr() for o in outs], s.cuda_stream)
+
+    def readout_ptrs(self, members, t_us, out_ptrs, cuda_stream: int) -> int:
+        """``readout`` with the images as device addresses (each W*H floats of its member)
+        and the stream as a raw handle: no tensor checks, for callers that made the
+        images themselves."""
+        m = len(members)
+        mem = array.array("I", members)
+        ts = array.array("Q", t_us)
+        op = array.array("Q", out_ptrs)
+        status = array.array("i", bytes(4 * m))
+        ticket = array.array("Q", [0])
+        rc = fibar_group_readout(self.g, mem.buffer_info()[0], ts.buffer_info()[0], op.buffer_info()[0], m,
+                                 status.buffer_info()[0], ticket.buffer_info()[0], cuda_stream)
         if rc != 0:
-            bad = np.flatnonzero(status)
-            if bad.size:
-                i = int(members[int(bad[0])]) if int(bad[0]) < m else -1
+            bad = [k for k in range(m) if status[k] != 0]
+            if bad:
+                i = int(members[bad[0]])
                 detail = fibar_last_error(self.fibars[i].h) if 0 <= i < len(self.fibars) else ""
-                raise FibarError(rc, f"entry {int(bad[0])}: {fibar_group_last_error(self.g)} {detail}")
+                raise FibarError(rc, f"entry {bad[0]}: {fibar_group_last_error(self.g)} {detail}")
             self._check(rc)
+        fibars = self.fibars
         for i in members:
-            self.fibars[i]._rotate()
-        return int(ticket[0])
+            fibars[i]._rotate()
+        return ticket[0]
 
     def join(self, stream=None) -> None:
         """Make later work on ``stream`` (default: the current stream) wait for every read-out

@@ -21,7 +21,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .binding import Fibar, FibarError, Group, _push_arrays, memory_bytes, readout_batch
+from .binding import Fibar, FibarError, Group, _push_lists, memory_bytes, readout_batch
 
 # per handle, on top of the library's count: the driver's allocation granularity
 HANDLE_SLACK_BYTES = 8 << 20
@@ -85,6 +85,7 @@ class _Stream:
     H: int
     last_t: int = -1
     queue: list = field(default_factory=list)  # pending Requests, in arrival order
+    hval: int = 0                               # the library handle, as an integer
 
 
 class GridTuner:
@@ -97,7 +98,7 @@ class GridTuner:
     keeps the share with the most events per second.  The choices are recorded in
     ``table`` ((W, H) -> SMs, 0 = the whole device) and ``trials`` (the timings)."""
 
-    def __init__(self, candidates=None, rounds: int = 4, warm: int = 2, seed: int = 31, use_graph: bool = True):
+    def __init__(self, candidates=None, rounds: int = 3, warm: int = 1, seed: int = 31, use_graph: bool = True):
         import torch
         self.torch = torch
         self.use_graph = use_graph
@@ -171,6 +172,7 @@ class Server:
         self.group = None        # Group over the admitted streams (rebuilt after admit/release)
         self._members = {}       # sid -> index in the group
         self._old_groups = []    # replaced groups, kept for their tickets until close()
+        self._ev_cache = {}      # id(events tensor) -> (tensor, data_ptr, rows), for push_ranges
         if budget is None:
             free, _ = torch.cuda.mem_get_info()
             budget = max(0, free - reserve)
@@ -191,7 +193,7 @@ class Server:
             self.admission.release(sid)
             self.admission.refused += 1
             return None
-        self.streams[sid] = _Stream(fib, W, H)
+        self.streams[sid] = _Stream(fib, W, H, hval=fib.h.value)
         self._drop_group()
         if (W, H) in self.grid_share:
             fib.set_grid_share(self.grid_share[(W, H)])
@@ -239,21 +241,27 @@ class Server:
         n = len(items)
         if n == 0:
             return
-        hs = np.empty(n, np.uint64)
-        ptrs = np.empty(n, np.uint64)
-        ns = np.empty(n, np.uint64)
-        fibs = []
-        keep = []
-        for k, (sid, ev, lo, hi) in enumerate(items):
-            f = self.streams[sid].fib
-            if not (0 <= lo <= hi <= ev.shape[0]):
+        cache = self._ev_cache
+        streams = self.streams
+        hs, ptrs, ns, fibs, keep = [], [], [], [], []
+        for sid, ev, lo, hi in items:
+            st = streams[sid]
+            c = cache.get(id(ev))
+            if c is None or c[0] is not ev:
+                if (not ev.is_cuda or ev.dtype != self.torch.int64 or ev.dim() != 2 or ev.shape[1] != 2
+                        or not ev.is_contiguous()):
+                    raise TypeError("events must be a contiguous CUDA (n, 2) int64 tensor")
+                if len(cache) > 4096:
+                    cache.clear()
+                c = cache[id(ev)] = (ev, ev.data_ptr(), ev.shape[0])
+            if not 0 <= lo <= hi <= c[2]:
                 raise ValueError("packet range outside the events")
-            fibs.append(f)
+            hs.append(st.hval)
+            ptrs.append(c[1] + 16 * lo)
+            ns.append(hi - lo)
+            fibs.append(st.fib)
             keep.append(ev)
-            hs[k] = f.h.value
-            ptrs[k] = ev.data_ptr() + 16 * lo
-            ns[k] = hi - lo
-        _push_arrays(fibs, keep, hs, ptrs, ns, self.stream)
+        _push_lists(fibs, keep, hs, ptrs, ns, self.stream)
 
     def request(self, sid: int, t_us: int) -> Request:
         """Ask for the stream's image at t_us (not earlier than its previous request)."""
@@ -282,10 +290,12 @@ class Server:
                 r.image = torch.empty((st.H, st.W), dtype=torch.float32, device="cuda")
             if self.use_graph:
                 g = self._ensure_group()
-                ticket = g.readout([self._members[sid] for sid, _ in batch], [r.t_us for r in reqs],
-                                   [r.image for r in reqs], stream=self.stream)
+                members = self._members
+                ticket = g.readout_ptrs([members[sid] for sid, _ in batch], [r.t_us for r in reqs],
+                                        [r.image.data_ptr() for r in reqs], self.stream.cuda_stream)
+                m = len(reqs)
                 for k, r in enumerate(reqs):
-                    r.group, r.ticket, r.k, r.m = g, ticket, k, len(reqs)
+                    r.group, r.ticket, r.k, r.m = g, ticket, k, m
             else:
                 start = torch.cuda.Event(enable_timing=True)
                 start.record(self.stream)
