@@ -50,6 +50,19 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64b(const unsigned lon
     return v;
 }
 
+// a published blur value: tag and value in one 64-bit word, so a relaxed load suffices
+__device__ __forceinline__ unsigned long long ld_relaxed_u64b(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64b(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ void st_release_u64b(unsigned long long *p, unsigned long long v)
 {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -298,24 +311,57 @@ __global__ void __launch_bounds__(128) k_s1_blur(KParams kp, Bufs b)
         bool done = !active;
         unsigned spins = 0;
         float dv[9];  // published D of each tap's blur (the value and its flag in one word)
+        float cm[9];  // beta^m of each tap's blur, ready before the wait
         unsigned pending = 0;  // taps whose blur has not been seen published yet
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
             dv[t] = 0.f;
-            if (tp[t].bl != NOBLUR) pending |= 1u << t;
+            cm[t] = 0.f;
+            if (active && tp[t].bl != NOBLUR) {  // (the taps of a lane without a blur are unset)
+                pending |= 1u << t;
+                cm[t] = beta_pow(kp, b.beta_pow, tp[t].m);
+            }
         }
+        // the pending tap whose blur comes last in list order (the one most likely to be
+        // published last): while it is pending only it is polled, then the others once
+        auto key_of = [&](unsigned pend) {
+            int key = -1;
+            unsigned best = 0;
+#pragma unroll
+            for (int t = 0; t < 9; ++t)
+                if ((pend >> t & 1u) && (key < 0 || tp[t].bl > best)) { key = t; best = tp[t].bl; }
+            return key;
+        };
+        int key = key_of(pending);
         while (__any_sync(0xFFFFFFFFu, !done)) {
             if (!done) {
-                // poll only the taps still pending: a published value never changes
+                // a published value never changes
+                if (key >= 0) {
+                    unsigned bl = 0;
 #pragma unroll
-                for (int t = 0; t < 9; ++t)
-                    if (pending >> t & 1u) {
-                        const unsigned long long v = ld_acquire_u64b(&b.bval[tp[t].bl]);
-                        if ((unsigned)(v >> 32) == g.batch_no) {
-                            dv[t] = __uint_as_float((unsigned)v);
-                            pending &= ~(1u << t);
-                        }
+                    for (int t = 0; t < 9; ++t)
+                        if (t == key) bl = tp[t].bl;
+                    const unsigned long long v = ld_relaxed_u64b(&b.bval[bl]);
+                    if ((unsigned)(v >> 32) == g.batch_no) {
+#pragma unroll
+                        for (int t = 0; t < 9; ++t)
+                            if (t == key) dv[t] = __uint_as_float((unsigned)v);
+                        pending &= ~(1u << key);
+                        key = -1;
                     }
+                }
+                if (key < 0 && pending) {
+#pragma unroll
+                    for (int t = 0; t < 9; ++t)
+                        if (pending >> t & 1u) {
+                            const unsigned long long v = ld_relaxed_u64b(&b.bval[tp[t].bl]);
+                            if ((unsigned)(v >> 32) == g.batch_no) {
+                                dv[t] = __uint_as_float((unsigned)v);
+                                pending &= ~(1u << t);
+                            }
+                        }
+                    key = key_of(pending);
+                }
                 const bool ready = pending == 0;
                 if (ready) {
                     float acc = 0.f;
@@ -324,11 +370,13 @@ __global__ void __launch_bounds__(128) k_s1_blur(KParams kp, Bufs b)
                         const int dx = t % 3 - 1, dy = t / 3 - 1;
                         // taps outside the sensor hold lnb = 0 and no blur: they add 0
                         float v = tp[t].lnb;
-                        if (tp[t].bl != NOBLUR) v += beta_pow(kp, b.beta_pow, tp[t].m) * dv[t];
+                        if (tp[t].bl != NOBLUR) v += cm[t] * dv[t];
                         acc += wt[dx + 1] * wt[dy + 1] * v;
                     }
                     const float D = acc / wsum - lself;
-                    st_release_u64b(&b.bval[s], ((unsigned long long)g.batch_no << 32) | __float_as_uint(D));
+                    // the word is the whole message (readers take tag and value from it):
+                    // no ordering with other stores is needed
+                    st_relaxed_u64b(&b.bval[s], ((unsigned long long)g.batch_no << 32) | __float_as_uint(D));
                     done = true;
                 } else if (++spins > SPIN_LIMIT) {
                     atomicOr(&ctrl->error, ERR_S1_WAIT);
