@@ -31,26 +31,8 @@ __device__ __forceinline__ float beta_pow(const KParams &kp, const float *tab, i
     return exp2f(kp.log2b * (float)m);
 }
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64b(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// a published blur value: tag and value in one 64-bit word, so a relaxed load suffices
+// Words that carry their whole message (a tag and a value or count in 64 bits): relaxed
+// single-copy-atomic loads and stores suffice, no ordering with other memory is needed.
 __device__ __forceinline__ unsigned long long ld_relaxed_u64b(const unsigned long long *p)
 {
     unsigned long long v;
@@ -61,11 +43,6 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64b(const unsigned lon
 __device__ __forceinline__ void st_relaxed_u64b(unsigned long long *p, unsigned long long v)
 {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ void st_release_u64b(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 struct S1Geo {
@@ -150,15 +127,16 @@ __global__ void __launch_bounds__(SEL_THREADS) k_s1_select(KParams kp, Bufs b)
         const unsigned tile_cnt = s_warp[15];
         // publish this tile's count; sum all predecessors' counts (no look-back chain)
         unsigned long long *st = b.sel_status;
-        if (threadIdx.x == 0) st_release_u64b(&st[tile], tag | (1ull << 30) | tile_cnt);
+        // (the status word is the whole message: tag, flag and count)
+        if (threadIdx.x == 0) st_relaxed_u64b(&st[tile], tag | (1ull << 30) | tile_cnt);
         unsigned part = 0;
         for (unsigned tp = threadIdx.x; tp < tile; tp += SEL_THREADS) {
-            unsigned long long v = ld_acquire_u64b(&st[tp]);
+            unsigned long long v = ld_relaxed_u64b(&st[tp]);
             unsigned spins = 0;
             while ((v >> 32) != (tag >> 32) || ((v >> 30) & 3ull) == 0ull) {
                 if (++spins > SPIN_LIMIT) { atomicOr(&ctrl->error, ERR_SORT_WAIT); break; }
                 __nanosleep(64);
-                v = ld_acquire_u64b(&st[tp]);
+                v = ld_relaxed_u64b(&st[tp]);
             }
             part += (unsigned)v & 0x3FFFFFFFu;
         }
@@ -322,46 +300,19 @@ __global__ void __launch_bounds__(128) k_s1_blur(KParams kp, Bufs b)
                 cm[t] = beta_pow(kp, b.beta_pow, tp[t].m);
             }
         }
-        // the pending tap whose blur comes last in list order (the one most likely to be
-        // published last): while it is pending only it is polled, then the others once
-        auto key_of = [&](unsigned pend) {
-            int key = -1;
-            unsigned best = 0;
-#pragma unroll
-            for (int t = 0; t < 9; ++t)
-                if ((pend >> t & 1u) && (key < 0 || tp[t].bl > best)) { key = t; best = tp[t].bl; }
-            return key;
-        };
-        int key = key_of(pending);
         while (__any_sync(0xFFFFFFFFu, !done)) {
             if (!done) {
-                // a published value never changes
-                if (key >= 0) {
-                    unsigned bl = 0;
+                // every pending tap at once (independent relaxed loads, one round trip):
+                // a published word holds its tag and its value and never changes
 #pragma unroll
-                    for (int t = 0; t < 9; ++t)
-                        if (t == key) bl = tp[t].bl;
-                    const unsigned long long v = ld_relaxed_u64b(&b.bval[bl]);
-                    if ((unsigned)(v >> 32) == g.batch_no) {
-#pragma unroll
-                        for (int t = 0; t < 9; ++t)
-                            if (t == key) dv[t] = __uint_as_float((unsigned)v);
-                        pending &= ~(1u << key);
-                        key = -1;
-                    }
-                }
-                if (key < 0 && pending) {
-#pragma unroll
-                    for (int t = 0; t < 9; ++t)
-                        if (pending >> t & 1u) {
-                            const unsigned long long v = ld_relaxed_u64b(&b.bval[tp[t].bl]);
-                            if ((unsigned)(v >> 32) == g.batch_no) {
-                                dv[t] = __uint_as_float((unsigned)v);
-                                pending &= ~(1u << t);
-                            }
+                for (int t = 0; t < 9; ++t)
+                    if (pending >> t & 1u) {
+                        const unsigned long long v = ld_relaxed_u64b(&b.bval[tp[t].bl]);
+                        if ((unsigned)(v >> 32) == g.batch_no) {
+                            dv[t] = __uint_as_float((unsigned)v);
+                            pending &= ~(1u << t);
                         }
-                    key = key_of(pending);
-                }
+                    }
                 const bool ready = pending == 0;
                 if (ready) {
                     float acc = 0.f;
@@ -421,7 +372,8 @@ cudaError_t launch_s1(const KParams &kp, const Bufs &b, cudaStream_t s, unsigned
     if (cudaError_t e_ = launch_pdl(k_s1_pops, grid_for(kp, 4), 256, 0, s, kp, b)) return e_;
     if (cudaError_t e_ = launch_pdl(k_s1_select, grid_for(kp, 2), SEL_THREADS, 0, s, kp, b)) return e_;
     if (cudaError_t e_ = launch_pdl(k_s1_lb, grid_for(kp, 4), 256, 0, s, kp, b)) return e_;
-    if (cudaError_t e_ = launch_pdl(k_s1_blur, grid_for(kp, 4), 128, 0, s, kp, b)) return e_;
+    // as many blur warps as 64 registers a thread allow (32 per SM): more blurs in flight
+    if (cudaError_t e_ = launch_pdl(k_s1_blur, grid_for(kp, 8), 128, 0, s, kp, b)) return e_;
     if (cudaError_t e_ = launch_pdl(k_s1_apply, grid_for(kp, 4), 256, 0, s, kp, b)) return e_;
     return cudaGetLastError();
 }
