@@ -52,7 +52,7 @@ void free_all(fibar_t *h)
     void *ptrs[] = {b.ctrl, b.pbar, b.L, b.last_pix, b.last_tile, b.staging, b.carry[0], b.carry[1],
                     b.dec_status, b.rec[0], b.rec[1], b.sort_hist, b.sort_base, b.sort_rows, b.sort_rowflag, b.sort_gtot, b.sort_gflag, b.sort_gcount,
                     b.qout, b.ring4, b.ring_pix, b.bucket_start, b.bucket_cnt, b.bucket_order, b.dMt, b.det_base, b.det_prof, b.band_ctr, b.E0, b.E1, b.E2, b.p2_ids, b.merged, b.unm_bits,
-                    b.out_staging, b.dbg_cnt, b.plist, b.plnb, b.epos, b.lbl, b.s1_info, b.s1_linit,
+                    b.out_staging, b.dbg_cnt, b.plist, b.plnb, b.lbl, b.lbo, b.s1_info, b.s1_linit,
                     b.popk, b.blur_ord, b.bk, b.bpix, b.bj, b.bval, b.sel_status, b.beta_pow};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -216,8 +216,8 @@ void for_each_buffer(const Layout &lo, Bufs &b, F &&f)
     if (lo.p.spatial_filter && lo.p.blur_mode == 0) {
         f(b.plist, maxp);
         f(b.plnb, maxp);
-        f(b.epos, maxp);
         f(b.lbl, maxp);
+        f(b.lbo, maxp);
         f(b.s1_info, npix);
         f(b.s1_linit, npix);
         f(b.popk, b.max_pops);

@@ -176,8 +176,8 @@ struct Bufs {
     // S1 (blur in place when a pixel goes stale)
     unsigned int *plist;         // [maxp] batch events grouped by pixel (tile-major), in order
     float *plnb;                 // [maxp] L without this batch's blurs after that event
-    unsigned int *epos;          // [maxp] ordinal of batch event k within its pixel's list
     unsigned int *lbl;           // [maxp] latest blur attached to the pixel's events <= position
+    int *lbo;                    // [maxp] ordinal of that blur's event in the pixel's list (-1: before the batch)
     int4 *s1_info;               // [npix] {batch_no, list start, list length, previous event - base}
     float *s1_linit;             // [npix] L at the batch start (pixels with batch events)
     unsigned int *popk;          // [maxp + npix] pop step | stale << 31 of each popped event

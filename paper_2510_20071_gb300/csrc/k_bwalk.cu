@@ -431,7 +431,6 @@ k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
                             if (qq == sp) { os = ord[qq]; ps0 = soff[qq]; }
                         b.plist[ps0 + os] = k;
                         b.plnb[ps0 + os] = lvs;
-                        b.epos[k] = os;
 #pragma unroll
                         for (int qq = 0; qq < 4; ++qq) ord[qq] += (qq == sp);
                     }
@@ -533,7 +532,6 @@ k_bwalk(KParams kp, Bufs b, const unsigned long long *srt)
                         const unsigned rk = e - S.tstart[d] - sub16(S.subofs[d], sp);
                         b.plist[T.lbase[sl] + rk] = k;
                         b.plnb[T.lbase[sl] + rk] = cur.u2;
-                        b.epos[k] = T.ord[sl] + rk;
                     }
                     // the last event of each pixel's run stores the pixel's new state
                     bool last = e + 1 >= n;

@@ -190,10 +190,15 @@ __global__ void __launch_bounds__(256) k_s1_lb(KParams kp, Bufs b)
         const int4 info = b.s1_info[pix];
         if ((unsigned)info.y != p) continue;
         unsigned run = info.w > -0x40000000 ? blur_of(b, g, info.w) : NOBLUR;
+        int run_ord = -1;  // the blur of the event before the batch
         for (int q = info.y; q < info.y + info.z; ++q) {
             const unsigned bo = blur_of(b, g, (long long)b.plist[q]);
-            if (bo != NOBLUR) run = bo;
+            if (bo != NOBLUR) {
+                run = bo;
+                run_ord = q - info.y;
+            }
             b.lbl[q] = run;
+            b.lbo[q] = run_ord;
         }
     }
 }
@@ -211,6 +216,7 @@ __device__ __forceinline__ Tap resolve(const KParams &kp, const Bufs &b, const S
     t.bl = NOBLUR;
     t.m = 0;
     int ord_e = -1;
+    int ord_b = -1;  // ordinal of the tap's blur event in its pixel's list (-1: before the batch)
     long long prev;
     const int4 info = b.s1_info[n];
     bool found = false;
@@ -229,9 +235,15 @@ __device__ __forceinline__ Tap resolve(const KParams &kp, const Bufs &b, const S
             t.lnb = b.plnb[p];
             ord_e = f;
             const unsigned own = blur_of(b, g, e);
-            if (own != NOBLUR && own < s) t.bl = own;
-            else if (f > 0) t.bl = b.lbl[p - 1];
-            else t.bl = prev > -0x40000000 ? blur_of(b, g, prev) : NOBLUR;
+            if (own != NOBLUR && own < s) {
+                t.bl = own;
+                ord_b = f;
+            } else if (f > 0) {
+                t.bl = b.lbl[p - 1];
+                ord_b = b.lbo[p - 1];
+            } else {
+                t.bl = prev > -0x40000000 ? blur_of(b, g, prev) : NOBLUR;
+            }
         } else {
             t.lnb = b.s1_linit[n];
         }
@@ -244,11 +256,7 @@ __device__ __forceinline__ Tap resolve(const KParams &kp, const Bufs &b, const S
         const unsigned own = blur_of(b, g, prev);
         if (own != NOBLUR && own < s) t.bl = own;
     }
-    if (t.bl != NOBLUR) {
-        const int jb = b.bj[t.bl];
-        const int ord_b = jb >= 0 ? (int)b.epos[jb] : -1;
-        t.m = ord_e - ord_b;
-    }
+    if (t.bl != NOBLUR) t.m = ord_e - ord_b;
     return t;
 }
 
@@ -353,8 +361,7 @@ __global__ void __launch_bounds__(256) k_s1_apply(KParams kp, Bufs b)
         const int last = info.y + info.z - 1;
         const unsigned bl = b.lbl[last];
         if (bl == NOBLUR) continue;
-        const int jb = b.bj[bl];
-        const int ord_b = jb >= 0 ? (int)b.epos[jb] : -1;
+        const int ord_b = b.lbo[last];
         b.L[pix] = b.plnb[last] + beta_pow(kp, b.beta_pow, info.z - 1 - ord_b) * __uint_as_float((unsigned)__ldcg(&b.bval[bl]));
     }
     // pixels without events in this batch whose previous event was popped (and blurred) now
