@@ -272,8 +272,6 @@ def run_batch(args, rank, world, local):
     gstats = srv.group.stats() if srv.group is not None else None
     applied = st1["events_applied"] - st0["events_applied"]
     launches = st1["kernel_launches"] - st0["kernel_launches"]
-    if gstats:  # one k_group_begin per graph launch besides the members' chains
-        launches += st1["batches"] - st0["batches"]
     lat = sorted(latencies_ms(served))
     expect = sum(int((s["events"][:, 1] > t_sweep).sum().item()) for s in streams)
     if applied != expect:
@@ -306,7 +304,7 @@ def run_batch(args, rank, world, local):
                      "peak_kind": peak_kind,
                      "alg_bytes": "16 B per event read + 8 B per pixel per image (L read, image written)"},
         "readout_latency_ms": {"p50": pct(50), "p99": pct(99), "max": pct(100), "samples": len(lat),
-                               "what": "device time from a batch's start to the request's image"},
+                               "what": "device time from the start of the request's batch (its first chain) to the request's image, queueing behind the stream's earlier read-outs included"},
         "host_ms": round(host_ms, 3),
         "grid_share_autotune": tuning,
         "serving_path": (f"group: each stream's read-out chain captured once as a CUDA graph, one graph launch "
