@@ -777,6 +777,27 @@ def main():
     f.set_timing(False)
     stage_pass_ms = s0.elapsed_time(s1) / max(n_stage, 1)
 
+    # the other spatial-filter modes on the same stream and steps (a fresh handle each):
+    # the paper's in-place blur (S1) and no spatial filter (NSF), timed like `value`
+    modes = {}
+    if args.mode == "s2":
+        k_modes = min(args.steps, 20)
+        for m in ("s1", "nsf"):
+            fm = Fibar(W, H, stream=stream, c_on=0.2, c_off=0.2, **MODE_PARAMS[m])
+            run_steps(fm, ev, plan[:w0], out)
+            a0 = fm.stats()["events_applied"]
+            torch.cuda.synchronize()
+            m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            m0.record(stream)
+            run_steps(fm, ev, plan[w0:w0 + k_modes], out)
+            m1.record(stream)
+            torch.cuda.synchronize()
+            mms = m0.elapsed_time(m1)
+            ma = fm.stats()["events_applied"] - a0
+            modes[m] = {"name": MODE_NAMES[m], "value": round(ma / (mms / 1e3) / 1e6, 3),
+                        "ms_per_step": round(mms / k_modes, 5), "steps": k_modes, "unit": UNIT}
+            fm.close()
+
     ms_max, total_events, value = whole_job(ms, float(applied), world)  # Mevents/s, whole job
 
     # roofline of the dominant kernel stage, from its CUDA-event time in the stage pass
@@ -826,6 +847,7 @@ def main():
                      "alg_bytes_per_event": B_ev},
         "readout_latency_ms": {"p50": pct(50), "p99": pct(99), "max": pct(100), "samples": len(lat),
                                "what": "device time of one read-out (1 M pending events + image)"},
+        "modes": modes or None,
         "stages_ms_per_step": {k: round(v / max(stages["calls"], 1), 5) for k, v in stage_ms.items()},
         "stage_pass_ms_per_step": round(stage_pass_ms, 5),
         "clocks": clocks,

@@ -103,7 +103,9 @@ class GridTuner:
         self.torch = torch
         self.use_graph = use_graph
         self.sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-        self.candidates = candidates or [0, self.sms // 2, self.sms // 4, self.sms // 8, self.sms // 16]
+        # the whole device, then a quarter down to a twelfth (on the 32-stream workload a
+        # quarter or an eighth won on every sensor; half of the device never did)
+        self.candidates = candidates or [0, self.sms // 4, self.sms // 6, self.sms // 8, self.sms // 12]
         self.rounds, self.warm, self.seed = rounds, warm, seed
         self.table: dict[tuple[int, int], int] = {}
         self.trials: dict[tuple[int, int], list] = {}
