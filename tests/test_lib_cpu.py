@@ -77,3 +77,52 @@ def test_binding_refuses_without_cuda():
     import paper_2510_20071_gb300 as fb
     with pytest.raises(fb.FibarError):
         fb.Fibar(8, 8)
+
+
+def test_group_and_batch_entry_points_reject_bad_arguments_without_a_device():
+    """The serving entry points check their arguments before any CUDA call."""
+    import array
+    import paper_2510_20071_gb300 as fb
+    lib = fb.load_library()
+    rc, g = fb.fibar_group_create([])
+    assert rc == fb.FIBAR_EINVAL and not g.value
+    out = C.c_void_p()
+    assert lib.fibar_group_create(None, 1, C.byref(out)) == fb.FIBAR_EINVAL
+    assert lib.fibar_group_create((C.c_void_p * 1)(None), 1025, C.byref(out)) == fb.FIBAR_EINVAL
+    assert lib.fibar_group_create((C.c_void_p * 1)(None), 1, None) == fb.FIBAR_EINVAL
+    assert fb.fibar_group_readout(None, 0, 0, 0, 1, None, None, 0) == fb.FIBAR_EINVAL
+    assert fb.fibar_group_join(None, 0) == fb.FIBAR_EINVAL
+    assert fb.fibar_group_latency(None, 0, 0, 0) == fb.FIBAR_EINVAL
+    assert fb.fibar_group_stats(None, fb.FibarGroupStats()) == fb.FIBAR_EINVAL
+    assert fb.fibar_group_last_error(None) == "null group"
+    fb.fibar_group_destroy(None)
+    assert fb.fibar_set_grid_share(None, 8) == fb.FIBAR_EINVAL
+    # batched pushes: nothing to do, missing arrays, and a NULL handle per entry
+    assert fb.fibar_push_batch(0, 0, 0, 0, 1, None, 0) == fb.FIBAR_OK
+    assert fb.fibar_push_batch(0, 0, 0, 2, 1, None, 0) == fb.FIBAR_EINVAL
+    hs, ptrs, ns = array.array("Q", [0, 0]), array.array("Q", [16, 32]), array.array("Q", [1, 1])
+    status = array.array("i", [7, 7])
+    rc = fb.fibar_push_batch(hs.buffer_info()[0], ptrs.buffer_info()[0], ns.buffer_info()[0], 2, 1,
+                             status.buffer_info()[0], 0)
+    assert rc == fb.FIBAR_EINVAL and list(status) == [fb.FIBAR_EINVAL, fb.FIBAR_EINVAL]
+    # batched read-outs: nothing to do, then missing arrays
+    assert fb.fibar_readout_batch([], [], [], None, None, 0) == fb.FIBAR_OK
+    assert lib.fibar_readout_batch(None, None, None, 1, None, None, None) == fb.FIBAR_EINVAL
+
+
+def test_group_stats_layout_matches_header(tmp_path):
+    from paper_2510_20071_gb300 import FibarGroupStats
+    prog = tmp_path / "gl.c"
+    prog.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "fibar.h"
+int main(void) {
+  printf("%zu %zu\\n", sizeof(fibar_group_stats_t), offsetof(fibar_group_stats_t, programmatic_edges));
+  return 0;
+}
+""")
+    exe = tmp_path / "gl"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    vals = list(map(int, subprocess.check_output([str(exe)]).split()))
+    assert vals == [C.sizeof(FibarGroupStats), FibarGroupStats.programmatic_edges.offset]
