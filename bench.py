@@ -43,7 +43,9 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 DRAM_TRAFFIC = {
     "s2": {"decode": 16.80e6, "sort": 8.03e6, "walk": 65.51e6, "det_counts": 41.01e6, "det_pass1": 16.97e6,
            "det_pass2": 11.67e6, "det_fix": 0.02e6, "readout": 11.07e6, "commit": 0.01e6},
-    "s1": {"walk": 86.84e6, "s1_blur": 159.54e6},
+    # S1 runs the same decode, sort and detector kernels on the same stream as S2
+    "s1": {"decode": 16.80e6, "sort": 8.03e6, "walk": 86.84e6, "det_counts": 41.01e6, "det_pass1": 16.97e6,
+           "det_pass2": 11.67e6, "det_fix": 0.02e6, "s1_blur": 159.54e6, "commit": 0.01e6},
 }
 
 
