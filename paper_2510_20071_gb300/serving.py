@@ -253,7 +253,7 @@ class Server:
                 if (not ev.is_cuda or ev.dtype != self.torch.int64 or ev.dim() != 2 or ev.shape[1] != 2
                         or not ev.is_contiguous()):
                     raise TypeError("events must be a contiguous CUDA (n, 2) int64 tensor")
-                if len(cache) > 4096:
+                if len(cache) >= 256:  # bounded: it holds its tensors alive
                     cache.clear()
                 c = cache[id(ev)] = (ev, ev.data_ptr(), ev.shape[0])
             if not 0 <= lo <= hi <= c[2]:
