@@ -1,5 +1,5 @@
 """Host-side logic of batched serving (no GPU): memory accounting, the library's memory
-query, and the seeded mixed-stream inputs."""
+query, the seeded mixed-stream inputs, and the marshalling of batched pushes."""
 import numpy as np
 import pytest
 
@@ -76,3 +76,65 @@ def test_serving_schedule_covers_every_event_once():
             reads[i].append(t)
     assert all(np.all(x == 1) for x in seen)
     assert reads == r
+
+
+class _FakeEvents:
+    """Stands in for a contiguous CUDA (n, 2) int64 tensor (host logic only)."""
+
+    def __init__(self, n, addr):
+        import torch
+        self.shape = (n, 2)
+        self.is_cuda = True
+        self.dtype = torch.int64
+        self._addr = addr
+
+    def dim(self):
+        return 2
+
+    def is_contiguous(self):
+        return True
+
+    def data_ptr(self):
+        return self._addr
+
+
+def test_push_ranges_marshals_addresses_and_keeps_packets(monkeypatch):
+    import torch
+    from paper_2510_20071_gb300 import serving
+
+    class Fib:
+        def __init__(self, hval):
+            self.h = type("H", (), {"value": hval})()
+            self._keep = []
+
+    calls = []
+
+    def fake_push(fibs, keep, hs, ptrs, ns, stream):
+        calls.append((list(hs), list(ptrs), list(ns)))
+        for f, ev in zip(fibs, keep):
+            if not f._keep or f._keep[-1] is not ev:
+                f._keep.append(ev)
+
+    monkeypatch.setattr(serving, "_push_lists", fake_push)
+    srv = serving.Server.__new__(serving.Server)
+    srv.torch = torch
+    srv.stream = None
+    srv._ev_cache = {}
+    srv.streams = {7: serving._Stream(Fib(1000), 4, 4, hval=1000), 9: serving._Stream(Fib(2000), 4, 4, hval=2000)}
+    a, b = _FakeEvents(100, 1 << 20), _FakeEvents(50, 1 << 24)
+    srv.push_ranges([(7, a, 10, 30), (9, b, 0, 50), (7, a, 30, 31)])
+    hs, ptrs, ns = calls[-1]
+    assert hs == [1000, 2000, 1000]
+    assert ptrs == [(1 << 20) + 16 * 10, 1 << 24, (1 << 20) + 16 * 30]   # 16-byte records
+    assert ns == [20, 50, 1]
+    assert srv.streams[7].fib._keep == [a] and srv.streams[9].fib._keep == [b]
+    srv.push_ranges([])                      # nothing to do: no library call
+    assert len(calls) == 1
+    with pytest.raises(ValueError):
+        srv.push_ranges([(7, a, 90, 101)])   # past the end of the events
+    with pytest.raises(ValueError):
+        srv.push_ranges([(7, a, 5, 4)])
+    # the address cache stays bounded however many packet tensors go through
+    for i in range(600):
+        srv.push_ranges([(9, _FakeEvents(8, (i + 1) << 12), 0, 8)])
+    assert len(srv._ev_cache) <= 256
