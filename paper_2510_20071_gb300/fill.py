@@ -91,7 +91,7 @@ def collect_frames(W: int, H: int, n_events: int, *, seed: int, scene: str = "pe
                 continue
             x, st = f.fill_features()
             I = truth(t_read)
-            active = (x[1] < 2.0) & (st == 0)   # had an event (age < 4) and still queued
+            active = (x[1] < 2.0) & (st == 0)   # had an event (age below the cap of 4) and still queued
             Xs.append(x)
             Ts.append(affine_target(x[0], I, active))
             Ss.append(st)
