@@ -280,7 +280,9 @@ class Server:
 
     def serve(self) -> list[Request]:
         """Answer every queued request: each batch takes the oldest request of every stream
-        that has one, so a stream's requests are served in order.  Returns them."""
+        that has one, so a stream's requests are served in order.  Returns them.  With group
+        read-outs an image is complete once `join()` (or `latencies_ms`) has waited for it;
+        keep each Request (it holds its image) until then."""
         torch = self.torch
         served = []
         while True:
